@@ -1,0 +1,181 @@
+/*
+ * msd.h -- C ABI of libmsd: the multi-Slater-determinant AFQMC hot path on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * For a batch of walkers |phi> (one complex M x N_s orbital matrix per spin s)
+ * and a CI trial |Psi_T> = sum_I c_I |D_I> whose determinants share one
+ * orthonormal orbital set (Sec. II B), the library evaluates
+ *
+ *   overlap      O_T = <Psi_T|phi>                                (Sec. II A-B)
+ *   force bias   vbias_g = <Psi_T| L_g-hat |phi> / <Psi_T|phi>,
+ *                L_g-hat = sum_{pq,s} L^g_pq a+_ps a_qs             (Eq. 8)
+ *   local energy E_L = <Psi_T|H|phi> / <Psi_T|phi>                (Sec. II A, III)
+ *
+ * for H = e0 + sum_{pq,s} h^s_pq a+_ps a_qs
+ *         + 1/2 sum_g sum_{pqrs,st} L^g_pq L^g_rs a+_ps a+_rt a_st a_qs,
+ * the Cholesky form of Eq. 2-3 with (pq|rs) = sum_g L^g_pq L^g_rs and the
+ * bare one-body matrix h (not h' = h - 1/2 sum_r (pr|rq), which only the
+ * propagator uses).
+ *
+ * Method (Sec. III "Implementation", and the Wick-theorem approach the paper
+ * adopts in Sec. III): every trial determinant is an excitation of the
+ * reference D_0 (trial determinant 0). Per walker and spin the library forms
+ * Theta = phi (D_0^dag phi)^-1 and the reference Green's function
+ * G0 = Theta D_0^dag; the overlap ratio of a determinant with holes h_1..h_k
+ * and particles p_1..p_k is sign * det A with A[i][j] = G[h_i][p_j] (a k x k
+ * minor of G = G0^T), its Green's function is a rank-k update of G, and the
+ * energy follows from contractions of the Cholesky vectors with G. Spin
+ * sectors are handled separately; only the energy and the ratio weights
+ * couple them.
+ *
+ * Conventions
+ *   - Complex numbers are interleaved (re, im) pairs of doubles.
+ *   - phi_s: [n_w][M][N_s] row-major (walker, orbital, electron).
+ *   - |D_I> = prod_{p in occ_a(I), ascending} a+_{p alpha}
+ *             prod_{p in occ_b(I), ascending} a+_{p beta} |0>;
+ *     the walker's creation operators are ordered the same way (alpha
+ *     columns, then beta columns), so <D_I|phi> = det(phi_a[occ_a]) *
+ *     det(phi_b[occ_b]).
+ *   - Walker and output pointers may be device memory (the fast path) or host
+ *     memory; host buffers are staged through device memory owned by the
+ *     context, and a call with any host buffer synchronises the stream before
+ *     it returns. The library never frees caller memory.
+ *   - Every entry point returns MSD_OK (0) or a negative error code; the
+ *     message of the last error is available from msd_last_error().
+ *   - A context belongs to one device and is not thread-safe: calls on one
+ *     context must not overlap.
+ */
+#ifndef MSD_H
+#define MSD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MSD_OK                0
+#define MSD_ERR_ARG          -1   /* null pointer or value out of range          */
+#define MSD_ERR_SHAPE        -2   /* sizes inconsistent or beyond built limits   */
+#define MSD_ERR_CUDA         -3   /* a CUDA runtime call failed                  */
+#define MSD_ERR_TIMEOUT      -4   /* a bounded device-side wait expired          */
+#define MSD_ERR_REF_SINGULAR -5   /* D_0^dag phi singular for some walker         */
+#define MSD_ERR_STATE        -6   /* Hamiltonian or trial not set yet            */
+#define MSD_ERR_NOMEM        -7   /* device or host allocation failed            */
+
+/* Arithmetic of the Cholesky-vector contractions and per-determinant energy
+   terms. The reference inverse (D_0^dag phi)^-1, the k x k minor
+   determinants and the final reductions are FP64 in both modes. */
+#define MSD_FP64  0
+#define MSD_MIXED 1
+
+/* Built limits. */
+#define MSD_MAX_ELECTRONS   64   /* N_s per spin                                 */
+#define MSD_MAX_LEVEL        6   /* excitation level per spin of any determinant */
+#define MSD_MAX_ACTIVE     112   /* n_h * n_p per spin (see msd_info)            */
+
+typedef struct msd_ctx msd_ctx;
+
+/* Create a context for M orbitals and n_alpha, n_beta electrons on CUDA
+   device `device`, with precision MSD_FP64 or MSD_MIXED.
+   *out receives the context (NULL on failure). */
+int msd_create(msd_ctx** out, int M, int n_alpha, int n_beta, int precision, int device);
+
+/* Release the context and all device memory it owns. NULL is a no-op. */
+void msd_destroy(msd_ctx* ctx);
+
+/* Message of the last error on this context (or of the last failed
+   msd_create when ctx is NULL). Valid until the next call on ctx. */
+const char* msd_last_error(const msd_ctx* ctx);
+
+/* Hamiltonian (Eq. 2-3). Host pointers; the data are copied.
+     h1 [2][M][M]       one-body matrix per spin, symmetric
+     e0                 constant energy
+     L  [n_chol][M][M]  Cholesky vectors, each symmetric
+   May be called again to replace the Hamiltonian. */
+int msd_set_hamiltonian(msd_ctx* ctx, const double* h1, double e0, int n_chol,
+                        const double* L);
+
+/* CI trial (Sec. II B). Host pointers; the data are copied.
+     coeff [n_det]           real CI coefficients c_I
+     occ_a [n_det][n_alpha]  occupied alpha orbitals of D_I, strictly ascending
+     occ_b [n_det][n_beta]   occupied beta orbitals, strictly ascending
+   Determinant 0 is the reference D_0; every determinant must differ from it
+   by at most MSD_MAX_LEVEL orbitals per spin. Errors: MSD_ERR_ARG for
+   unsorted, repeated or out-of-range orbitals, MSD_ERR_SHAPE for a level
+   above MSD_MAX_LEVEL or an active block above MSD_MAX_ACTIVE. */
+int msd_set_trial(msd_ctx* ctx, int n_det, const double* coeff, const int32_t* occ_a,
+                  const int32_t* occ_b);
+
+/* Select MSD_FP64 or MSD_MIXED for subsequent calls. */
+int msd_set_precision(msd_ctx* ctx, int precision);
+
+/* Trial overlap of n_w walkers (Sec. II A-B, overlap).
+     phi_a [n_w][M][n_alpha], phi_b [n_w][M][n_beta]   complex, host or device
+     ovlp      [n_w]  O_T = <Psi_T|phi> = O_0 * sum_I c_I r_I, complex
+     ratio_sum [n_w]  sum_I c_I r_I with r_I = <D_I|phi>/<D_0|phi> (may be NULL)
+   stream: a cudaStream_t (NULL = legacy default stream). */
+int msd_overlap(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b,
+                double* ovlp, double* ratio_sum, void* stream);
+
+/* Overlap ratio of every trial determinant (the get_dets quantity of the
+   paper's Sec. III "Implementation"):
+     ratios [n_w][n_det]  r_I = <D_I|phi> / <D_0|phi>, complex
+     ref_ovlp [n_w]       <D_0|phi>, complex (may be NULL) */
+int msd_det_ratios(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b,
+                   double* ratios, double* ref_ovlp, void* stream);
+
+/* Force-bias numerators (Eq. 8 without its -sqrt(dt) prefactor, which the
+   propagator applies):
+     vbias [n_w][n_chol]  sum_s tr(L_g G_T^s), complex, where G_T^s is the
+                          mixed Green's function <Psi_T|a+_ps a_qs|phi>/O_T
+     ovlp  [n_w]          O_T (may be NULL) */
+int msd_force_bias(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b,
+                   double* vbias, double* ovlp, void* stream);
+
+/* Mixed-estimator local energy (Sec. III, energy estimator):
+     e_loc [n_w]  E_L = <Psi_T|H|phi> / <Psi_T|phi>, complex
+     ovlp  [n_w]  O_T (may be NULL) */
+int msd_local_energy(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b,
+                     double* e_loc, double* ovlp, void* stream);
+
+/* Introspection. Keys: */
+#define MSD_INFO_N_DET          1
+#define MSD_INFO_N_CHOL         2
+#define MSD_INFO_N_STRINGS_A    3   /* distinct alpha excitation strings        */
+#define MSD_INFO_N_STRINGS_B    4
+#define MSD_INFO_N_HOLES_A      5   /* n_h: orbitals of D_0 that are ever holes */
+#define MSD_INFO_N_PARTS_A      6   /* n_p: orbitals that are ever particles    */
+#define MSD_INFO_N_HOLES_B      7
+#define MSD_INFO_N_PARTS_B      8
+#define MSD_INFO_WORKSPACE_BYTES 9  /* device workspace currently held          */
+#define MSD_INFO_WALKER_CHUNK  10   /* walkers per internal pass                */
+int msd_info(const msd_ctx* ctx, int key, long long* value);
+
+/* Per-kernel timing with CUDA events on the launching stream. When enabled,
+   every kernel launch is bracketed by events; msd_kernel_stat synchronises
+   on them and reports, per kernel name, the launch count and total device
+   milliseconds since the last msd_reset_stats. */
+int msd_set_timing(msd_ctx* ctx, int enable);
+int msd_reset_stats(msd_ctx* ctx);
+int msd_kernel_count(const msd_ctx* ctx);
+int msd_kernel_stat(msd_ctx* ctx, int index, const char** name, long long* launches,
+                    double* total_ms);
+
+/* Limit the device workspace (bytes) the context may hold; larger walker
+   batches are processed in chunks. 0 restores the default (4 GiB). */
+int msd_set_workspace_limit(msd_ctx* ctx, size_t bytes);
+
+/* With sync = 1 (the default) every call synchronises its stream before
+   returning and reports device-side errors (a singular reference, an
+   expired wait) in its return code. With sync = 0 calls on device buffers
+   return as soon as the work is queued; device-side errors are then
+   reported by the next synchronising call. */
+int msd_set_sync(msd_ctx* ctx, int sync);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSD_H */

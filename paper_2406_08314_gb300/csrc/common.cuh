@@ -1,0 +1,98 @@
+// Shared device helpers and the internal launch interface of libmsd.
+// Internal to the CUDA library; nothing outside csrc/ includes it.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#define MSD_KMAX 6          // highest excitation level per spin
+#define MSD_NMAX 64         // electrons per spin
+#define MSD_XMAX 112        // n_h * n_p per spin (active hole x particle block)
+
+// ---------------------------------------------------------------- complex
+__host__ __device__ __forceinline__ double2 cz(double r, double i) { return make_double2(r, i); }
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+// a + b * c
+__host__ __device__ __forceinline__ double2 cfma(double2 b, double2 c, double2 a) {
+    return make_double2(fma(b.x, c.x, fma(-b.y, c.y, a.x)), fma(b.x, c.y, fma(b.y, c.x, a.y)));
+}
+// a - b * c
+__host__ __device__ __forceinline__ double2 cfms(double2 b, double2 c, double2 a) {
+    return make_double2(fma(-b.x, c.x, fma(b.y, c.y, a.x)), fma(-b.x, c.y, fma(-b.y, c.x, a.y)));
+}
+__host__ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+    // Smith's algorithm
+    if (fabs(b.x) >= fabs(b.y)) {
+        double r = b.y / b.x, d = b.x + b.y * r;
+        return make_double2((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+    }
+    double r = b.x / b.y, d = b.x * r + b.y;
+    return make_double2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+}
+__host__ __device__ __forceinline__ double cabs1(double2 a) { return fabs(a.x) + fabs(a.y); }
+
+__host__ __device__ __forceinline__ float2 fz(float r, float i) { return make_float2(r, i); }
+__host__ __device__ __forceinline__ float2 fadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 fmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 ffma(float2 b, float2 c, float2 a) {
+    return make_float2(fmaf(b.x, c.x, fmaf(-b.y, c.y, a.x)), fmaf(b.x, c.y, fmaf(b.y, c.x, a.y)));
+}
+
+// ------------------------------------------------------------ device state
+// Error word bits set by kernels (read back by the host after a call).
+#define MSD_DEV_ERR_SINGULAR 1u
+#define MSD_DEV_ERR_TIMEOUT  2u
+#define MSD_DEV_ERR_BOUNDS   4u
+
+// Per-spin trial tables on the device.
+struct SpinTables {
+    int N;              // electrons
+    int nh, np;         // active holes (orbitals of D0 ever vacated) / particles
+    int n_str;          // distinct excitation strings, reference string first
+    int bucket[MSD_KMAX + 2];   // strings of level k: [bucket[k], bucket[k+1])
+    const int* occ0;    // [N]
+    const int* hole_pos;   // [nh] position in occ0 of each hole orbital
+    const int* part_orb;   // [np] orbital of each particle
+    const uint8_t* str_h;  // [n_str][KMAX] hole indices (0..nh-1), ascending
+    const uint8_t* str_p;  // [n_str][KMAX] particle indices (0..np-1), ascending
+    const int8_t* str_sign;    // [n_str] parity of the in-place -> sorted reordering
+    const int* csr_off;    // [n_str+1] determinants containing each string
+    const int* csr_other;  // [nnz] string of the opposite spin in that determinant
+    const double* csr_c;   // [nnz] CI coefficient of that determinant
+    long long b_off[MSD_KMAX + 2];  // per-walker offset (complex units) of each bucket's B block
+    long long b_per_walker;         // sum_k k^2 * (strings of level k)
+};
+
+// Pair (determinant) tables for the opposite-spin cross term.
+struct PairTables {
+    int n_det;
+    int bucket[(MSD_KMAX + 1) * (MSD_KMAX + 1) + 1];  // by (ka, kb): index ka*(KMAX+1)+kb
+    const int* a;       // [n_det] alpha string
+    const int* b;       // [n_det] beta string
+    const double* c;    // [n_det] coefficient
+    const int* det_index;  // [n_det] original position in the trial list
+};
+
+// Workspace pointers for one chunk of walkers (nw walkers).
+struct Work {
+    int nw;             // walkers in this chunk
+    int M;
+    double2* Gr[2];     // [nw][N][M]     G[occ0_j][r] = Theta[r][j]
+    double2* O0[2];     // [nw]           det(D0^dag phi)
+    double2* Gact[2];   // [nw][nh][np]   G[h][p]
+    double2* r[2];      // [nw][n_str]    ratio per string
+    double2* B[2];      // [nw * b_per_walker] inverse minors (bucket-major, SoA within bucket)
+    float2* Bf[2];      // FP32 copy for the mixed path (same layout)
+    double2* wts[2];    // [nw][n_str]    sum over dets containing the string of c * r_other
+    double2* part;      // [nw][nslot]    per-block partial sums
+    int nslot;
+    unsigned* err;      // device error word
+};

@@ -1,0 +1,445 @@
+// Reference inverse, excitation-string minors and CI weights: the overlap
+// part of the generalized-Wick evaluation (Sec. III "Implementation":
+// get_dets), plus the cofactor accumulation behind the mixed Green's
+// function (reduce_CI) and its rank-n_p update.
+#include "common.cuh"
+#include "kernels.h"
+
+// ------------------------------------------------------------------------
+// Reference determinant per (walker, spin): S = D0^dag phi = phi[occ0, :]
+// (Sec. II A overlap of two determinants). LU with partial pivoting in
+// FP64 gives O0 = det S and S^-1; then
+//   Gr[j][r]  = (phi S^-1)[r][j] = G[occ0_j][r]   (G = G0^T, G0 = Theta D0^dag)
+//   Gact[h][p] = G[H_h][P_p]                       (active hole x particle block)
+// One block per walker. A walker whose |det S| falls below 1e-14 times the
+// product of the column norms of S is flagged singular.
+__global__ void __launch_bounds__(256)
+k_ref(const double2* __restrict__ phi, int M, int N, const int* __restrict__ occ0,
+      const int* __restrict__ hole_pos, int nh, const int* __restrict__ part_orb, int np,
+      double2* __restrict__ Gr, double2* __restrict__ O0, double2* __restrict__ Gact,
+      unsigned* err)
+{
+    extern __shared__ double2 sm[];
+    double2* S = sm;              // [N][N] LU in place
+    double2* Si = S + N * N;      // [N][N] inverse
+    __shared__ int piv[MSD_NMAX];
+    __shared__ double cn[MSD_NMAX];
+    __shared__ int singular;
+    const int w = blockIdx.x;
+    const int t = threadIdx.x, nt = blockDim.x;
+    const double2* ph = phi + (size_t)w * M * N;
+
+    for (int e = t; e < N * N; e += nt) S[e] = ph[(size_t)occ0[e / N] * N + e % N];
+    if (t == 0) singular = 0;
+    __syncthreads();
+    for (int j = t; j < N; j += nt) {
+        double a = 0;
+        for (int i = 0; i < N; ++i) a += S[i * N + j].x * S[i * N + j].x + S[i * N + j].y * S[i * N + j].y;
+        cn[j] = sqrt(a);
+    }
+    for (int k = 0; k < N; ++k) {
+        if (t < 32) {
+            double best = -1; int bi = k;
+            for (int i = k + t; i < N; i += 32) {
+                double v = S[i * N + k].x * S[i * N + k].x + S[i * N + k].y * S[i * N + k].y;
+                if (v > best) { best = v; bi = i; }
+            }
+            for (int o = 16; o; o >>= 1) {
+                double ob = __shfl_down_sync(0xffffffffu, best, o);
+                int oi = __shfl_down_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (t == 0) { piv[k] = bi; if (best == 0.0) singular = 1; }
+        }
+        __syncthreads();
+        if (singular) break;
+        const int p = piv[k];
+        if (p != k)
+            for (int j = t; j < N; j += nt) { double2 a = S[k * N + j]; S[k * N + j] = S[p * N + j]; S[p * N + j] = a; }
+        __syncthreads();
+        for (int i = k + 1 + t; i < N; i += nt) S[i * N + k] = cdiv(S[i * N + k], S[k * N + k]);
+        __syncthreads();
+        const int m = N - k - 1;
+        for (int e = t; e < m * m; e += nt) {
+            int i = k + 1 + e / m, j = k + 1 + e % m;
+            S[i * N + j] = cfms(S[i * N + k], S[k * N + j], S[i * N + j]);
+        }
+        __syncthreads();
+    }
+    __shared__ double2 det;
+    if (t == 0) {
+        double2 d = cz(1, 0);
+        double nrm = 1;
+        if (!singular) {
+            for (int k = 0; k < N; ++k) { d = cmul(d, S[k * N + k]); if (piv[k] != k) d = cz(-d.x, -d.y); nrm *= cn[k]; }
+            if (!(sqrt(d.x * d.x + d.y * d.y) > 1e-14 * nrm)) singular = 1;
+        }
+        if (singular) { d = cz(0, 0); atomicOr(err, MSD_DEV_ERR_SINGULAR); }
+        det = d;
+        O0[w] = d;
+    }
+    __syncthreads();
+    if (singular) {
+        for (int e = t; e < N * M; e += nt) Gr[(size_t)w * N * M + e] = cz(0, 0);
+        for (int e = t; e < nh * np; e += nt) Gact[(size_t)w * nh * np + e] = cz(0, 0);
+        return;
+    }
+    // S^-1 column c: solve L U x = P e_c
+    for (int c = t; c < N; c += nt) {
+        double2 x[MSD_NMAX];
+        for (int i = 0; i < N; ++i) x[i] = cz(i == c ? 1 : 0, 0);
+        for (int k = 0; k < N; ++k) { int p = piv[k]; if (p != k) { double2 a = x[k]; x[k] = x[p]; x[p] = a; } }
+        for (int i = 0; i < N; ++i)
+            for (int k = 0; k < i; ++k) x[i] = cfms(S[i * N + k], x[k], x[i]);
+        for (int i = N - 1; i >= 0; --i) {
+            for (int k = i + 1; k < N; ++k) x[i] = cfms(S[i * N + k], x[k], x[i]);
+            x[i] = cdiv(x[i], S[i * N + i]);
+        }
+        for (int i = 0; i < N; ++i) Si[i * N + c] = x[i];
+    }
+    __syncthreads();
+    double2* gr = Gr + (size_t)w * N * M;
+    for (int e = t; e < N * M; e += nt) {
+        const int j = e / M, r = e % M;
+        const double2* pr = ph + (size_t)r * N;
+        double2 a = cz(0, 0);
+        for (int k = 0; k < N; ++k) a = cfma(pr[k], Si[k * N + j], a);
+        gr[e] = a;
+    }
+    for (int e = t; e < nh * np; e += nt) {
+        const int h = e / np, p = e % np;
+        const double2* pr = ph + (size_t)part_orb[p] * N;
+        const int j = hole_pos[h];
+        double2 a = cz(0, 0);
+        for (int k = 0; k < N; ++k) a = cfma(pr[k], Si[k * N + j], a);
+        Gact[(size_t)w * nh * np + e] = a;
+    }
+}
+
+void launch_ref(const double2* phi, int nw, int M, int N, const SpinTables& T, double2* Gr,
+                double2* O0, double2* Gact, unsigned* err, cudaStream_t st)
+{
+    size_t smem = sizeof(double2) * 2 * N * N;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_ref, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_ref<<<nw, 256, smem, st>>>(phi, M, N, T.occ0, T.hole_pos, T.nh, T.part_orb, T.np, Gr, O0,
+                                 Gact, err);
+}
+
+// ------------------------------------------------------------------------
+// Excitation strings of level K for one spin (get_dets / build_det_matrix):
+// A[i][j] = G[h_i][p_j] (a K x K minor of G), pivoted LU in FP64 gives
+// r = sign * det A, the overlap ratio <D_s|phi>/<D_0|phi> of the string's
+// spin sector; B = A^-1 (precision T: double in FP64 mode, float in mixed
+// mode) is stored for the Green's-function and energy terms.
+// One thread per (walker, string); the walker's active block lives in
+// shared memory.
+template <int K, typename T>
+__global__ void __launch_bounds__(128)
+k_strings(SpinTables tb, int nw, const double2* __restrict__ Gact, double2* __restrict__ r,
+          void* __restrict__ Bout, int want_b)
+{
+    __shared__ double2 g[MSD_XMAX];
+    const int w = blockIdx.y;
+    const int X = tb.nh * tb.np;
+    for (int e = threadIdx.x; e < X; e += blockDim.x) g[e] = Gact[(size_t)w * X + e];
+    __syncthreads();
+    const int ns = tb.bucket[K + 1] - tb.bucket[K];
+    const int sl = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sl >= ns) return;
+    const int s = tb.bucket[K] + sl;
+    int hh[K], pp[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) { hh[i] = tb.str_h[(size_t)s * MSD_KMAX + i]; pp[i] = tb.str_p[(size_t)s * MSD_KMAX + i]; }
+    double2 a[K][K];
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+#pragma unroll
+        for (int j = 0; j < K; ++j) a[i][j] = g[hh[i] * tb.np + pp[j]];
+    int perm[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) perm[i] = i;
+    double2 det = cz(tb.str_sign[s], 0);
+    bool sing = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        int p = k;
+        double best = a[k][k].x * a[k][k].x + a[k][k].y * a[k][k].y;
+#pragma unroll
+        for (int i = k + 1; i < K; ++i) {
+            double v = a[i][k].x * a[i][k].x + a[i][k].y * a[i][k].y;
+            if (v > best) { best = v; p = i; }
+        }
+        if (best == 0.0) sing = true;
+#pragma unroll
+        for (int i = k + 1; i < K; ++i) {
+            if (i == p) {
+#pragma unroll
+                for (int j = 0; j < K; ++j) { double2 tt = a[k][j]; a[k][j] = a[i][j]; a[i][j] = tt; }
+                int tp = perm[k]; perm[k] = perm[i]; perm[i] = tp;
+                det = cz(-det.x, -det.y);
+            }
+        }
+        det = cmul(det, a[k][k]);
+        if (!sing) {
+            const double2 inv = cdiv(cz(1, 0), a[k][k]);
+#pragma unroll
+            for (int i = k + 1; i < K; ++i) {
+                const double2 f = cmul(a[i][k], inv);
+                a[i][k] = f;
+#pragma unroll
+                for (int j = k + 1; j < K; ++j) a[i][j] = cfms(f, a[k][j], a[i][j]);
+            }
+        }
+    }
+    if (sing) det = cz(0, 0);
+    r[(size_t)w * tb.n_str + s] = det;
+    if (!want_b) return;
+    // B = A^-1 from P A = L U: column c solves L U x = P e_c.
+    T* B = reinterpret_cast<T*>(Bout) + 2 * (size_t)(tb.b_off[K] + (long long)w * K * K * ns);
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+        double2 x[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) x[i] = cz(perm[i] == c ? 1 : 0, 0);
+#pragma unroll
+        for (int i = 0; i < K; ++i)
+#pragma unroll
+            for (int k = 0; k < i; ++k) x[i] = cfms(a[i][k], x[k], x[i]);
+#pragma unroll
+        for (int i = K - 1; i >= 0; --i) {
+#pragma unroll
+            for (int k = i + 1; k < K; ++k) x[i] = cfms(a[i][k], x[k], x[i]);
+            x[i] = sing ? cz(0, 0) : cdiv(x[i], a[i][i]);
+        }
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            const size_t e = (size_t)(i * K + c) * ns + sl;
+            B[2 * e] = (T)x[i].x;
+            B[2 * e + 1] = (T)x[i].y;
+        }
+    }
+}
+
+template <int K>
+static void launch_strings_k(const SpinTables& tb, int nw, const double2* Gact, double2* r, void* B,
+                             bool fp32, int want_b, cudaStream_t st)
+{
+    const int ns = tb.bucket[K + 1] - tb.bucket[K];
+    if (ns <= 0) return;
+    dim3 grid((ns + 127) / 128, nw);
+    if (fp32) k_strings<K, float><<<grid, 128, 0, st>>>(tb, nw, Gact, r, B, want_b);
+    else k_strings<K, double><<<grid, 128, 0, st>>>(tb, nw, Gact, r, B, want_b);
+}
+
+// Reference string (level 0): ratio 1.
+__global__ void k_ref_string(int nw, int n_str, double2* r)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w < nw) r[(size_t)w * n_str] = cz(1, 0);
+}
+
+void launch_strings(const SpinTables& tb, int nw, const double2* Gact, double2* r, void* B,
+                    bool fp32, bool want_b, cudaStream_t st, const TimerHook& th)
+{
+    if (tb.bucket[1] > tb.bucket[0]) {
+        th.begin("k_ref_string", st);
+        k_ref_string<<<(nw + 127) / 128, 128, 0, st>>>(nw, tb.n_str, r);
+        th.end(st);
+    }
+    th.begin("k_strings", st);
+    launch_strings_k<1>(tb, nw, Gact, r, B, fp32, want_b, st);
+    launch_strings_k<2>(tb, nw, Gact, r, B, fp32, want_b, st);
+    launch_strings_k<3>(tb, nw, Gact, r, B, fp32, want_b, st);
+    launch_strings_k<4>(tb, nw, Gact, r, B, fp32, want_b, st);
+    launch_strings_k<5>(tb, nw, Gact, r, B, fp32, want_b, st);
+    launch_strings_k<6>(tb, nw, Gact, r, B, fp32, want_b, st);
+    th.end(st);
+}
+
+// ------------------------------------------------------------------------
+// CI weights per string: w_s = sum over determinants I containing string s
+// of c_I * r_other(I), so that sum_I c_I r_a r_b = sum_a r_a w_a. For spin
+// alpha the block also reduces r_s * w_s into per-walker partial sums.
+__global__ void __launch_bounds__(256)
+k_weights(SpinTables tb, const double2* __restrict__ r_self, const double2* __restrict__ r_other,
+          int n_other, double2* __restrict__ wts, double2* __restrict__ part, int nslot,
+          int slot0)
+{
+    const int w = blockIdx.y;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    double2 rw = cz(0, 0);
+    if (s < tb.n_str) {
+        double2 acc = cz(0, 0);
+        const double2* ro = r_other + (size_t)w * n_other;
+        for (int e = tb.csr_off[s]; e < tb.csr_off[s + 1]; ++e)
+            acc = cadd(acc, cscale(ro[tb.csr_other[e]], tb.csr_c[e]));
+        wts[(size_t)w * tb.n_str + s] = acc;
+        rw = cmul(r_self[(size_t)w * tb.n_str + s], acc);
+    }
+    if (part) {
+        __shared__ double2 red[256];
+        red[threadIdx.x] = rw;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o; o >>= 1) {
+            if (threadIdx.x < o) red[threadIdx.x] = cadd(red[threadIdx.x], red[threadIdx.x + o]);
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) part[(size_t)w * nslot + slot0 + blockIdx.x] = red[0];
+    }
+}
+
+int weights_blocks(const SpinTables& tb) { return (tb.n_str + 255) / 256; }
+
+void launch_weights(const SpinTables& tb, int nw, const double2* r_self, const double2* r_other,
+                    int n_other, double2* wts, double2* part, int nslot, int slot0, cudaStream_t st)
+{
+    dim3 grid(weights_blocks(tb), nw);
+    k_weights<<<grid, 256, 0, st>>>(tb, r_self, r_other, n_other, wts, part, nslot, slot0);
+}
+
+// ------------------------------------------------------------------------
+// Per-determinant ratios r_I = r_a(I) * r_b(I) in the caller's order.
+__global__ void k_det_ratios(PairTables pt, int n_str_a, int n_str_b, const double2* __restrict__ ra,
+                             const double2* __restrict__ rb, double2* __restrict__ out)
+{
+    const int w = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= pt.n_det) return;
+    out[(size_t)w * pt.n_det + pt.det_index[i]] =
+        cmul(ra[(size_t)w * n_str_a + pt.a[i]], rb[(size_t)w * n_str_b + pt.b[i]]);
+}
+
+void launch_det_ratios(const PairTables& pt, int nw, int n_str_a, int n_str_b, const double2* ra,
+                       const double2* rb, double2* out, cudaStream_t st)
+{
+    dim3 grid((pt.n_det + 255) / 256, nw);
+    k_det_ratios<<<grid, 256, 0, st>>>(pt, n_str_a, n_str_b, ra, rb, out);
+}
+
+// Sum of partial slots [slot0, slot0 + n) per walker -> out[w] (and
+// O_T = O0a * O0b * sum when ovlp is given).
+__global__ void k_sum_slots(int nw, const double2* __restrict__ part, int nslot, int slot0, int n,
+                            double2* __restrict__ out, const double2* __restrict__ O0a,
+                            const double2* __restrict__ O0b, double2* __restrict__ ovlp)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nw) return;
+    double2 a = cz(0, 0);
+    for (int i = 0; i < n; ++i) a = cadd(a, part[(size_t)w * nslot + slot0 + i]);
+    if (out) out[w] = a;
+    if (ovlp) ovlp[w] = cmul(cmul(O0a[w], O0b[w]), a);
+}
+
+void launch_sum_slots(int nw, const double2* part, int nslot, int slot0, int n, double2* out,
+                      const double2* O0a, const double2* O0b, double2* ovlp, cudaStream_t st)
+{
+    k_sum_slots<<<(nw + 127) / 128, 128, 0, st>>>(nw, part, nslot, slot0, n, out, O0a, O0b, ovlp);
+}
+
+// ------------------------------------------------------------------------
+// Cofactor accumulation (reduce_CI): per (walker, spin)
+//   Cm[p][h] = sum_s w_s r_s B_s[i][j]  at (p_i, h_j),
+// so that G_T - G = (E_P - G[:, P]) Cm G[H, :] / R. Shared-memory
+// accumulation per walker replaces global atomics.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_cmat(SpinTables tb, const double2* __restrict__ r, const double2* __restrict__ wts,
+       const void* __restrict__ Bin, double2* __restrict__ Cm)
+{
+    __shared__ double acc[2 * MSD_XMAX];
+    const int w = blockIdx.x;
+    const int X = tb.nh * tb.np;
+    for (int e = threadIdx.x; e < 2 * X; e += blockDim.x) acc[e] = 0;
+    __syncthreads();
+    const T* Bb = reinterpret_cast<const T*>(Bin);
+    for (int s = tb.bucket[1] + threadIdx.x; s < tb.n_str; s += blockDim.x) {
+        int k = 1;
+        while (s >= tb.bucket[k + 1]) ++k;
+        const int ns = tb.bucket[k + 1] - tb.bucket[k], sl = s - tb.bucket[k];
+        const double2 f = cmul(r[(size_t)w * tb.n_str + s], wts[(size_t)w * tb.n_str + s]);
+        const T* B = Bb + 2 * (size_t)(tb.b_off[k] + (long long)w * k * k * ns);
+        for (int i = 0; i < k; ++i)
+            for (int j = 0; j < k; ++j) {
+                const size_t e = (size_t)(i * k + j) * ns + sl;
+                const double2 b = cz((double)B[2 * e], (double)B[2 * e + 1]);
+                const double2 v = cmul(f, b);
+                const int pi = tb.str_p[(size_t)s * MSD_KMAX + i], hj = tb.str_h[(size_t)s * MSD_KMAX + j];
+                atomicAdd(&acc[2 * (pi * tb.nh + hj)], v.x);
+                atomicAdd(&acc[2 * (pi * tb.nh + hj) + 1], v.y);
+            }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < X; e += blockDim.x) Cm[(size_t)w * X + e] = cz(acc[2 * e], acc[2 * e + 1]);
+}
+
+void launch_cmat(const SpinTables& tb, int nw, const double2* r, const double2* wts, const void* B,
+                 bool fp32, double2* Cm, cudaStream_t st)
+{
+    if (fp32) k_cmat<float><<<nw, 256, 0, st>>>(tb, r, wts, B, Cm);
+    else k_cmat<double><<<nw, 256, 0, st>>>(tb, r, wts, B, Cm);
+}
+
+// ------------------------------------------------------------------------
+// Rows of the mixed Green's function G_T (Eq. 8 numerator), per (walker,
+// spin), restricted to the rows that can be non-zero (occ0 then P):
+//   Y[p][c] = sum_h Cm[p][h] G[H_h][c]
+//   G_T[occ0_l][c] = G[occ0_l][c] - sum_p G[occ0_l][P_p] Y[p][c] / R
+//   G_T[P_p][c]    = Y[p][c] / R
+// Written to GT[w][row][c] with row stride M, at column offset `off` of a
+// row of length ld (both spins are concatenated per walker).
+__global__ void __launch_bounds__(256)
+k_gt(SpinTables tb, int M, const double2* __restrict__ Gr, const double2* __restrict__ Cm,
+     const double2* __restrict__ Rsum, double2* __restrict__ GT, long long ld, long long off)
+{
+    __shared__ double2 cm[MSD_XMAX];
+    __shared__ double2 y[MSD_XMAX * 8];   // [np][8 columns]
+    const int w = blockIdx.y;
+    const int c0 = blockIdx.x * 8;
+    const int N = tb.N, nh = tb.nh, np = tb.np;
+    const double2* gr = Gr + (size_t)w * N * M;
+    for (int e = threadIdx.x; e < nh * np; e += blockDim.x) cm[e] = Cm[(size_t)w * nh * np + e];
+    __syncthreads();
+    const double2 R = Rsum[w];
+    const double2 iR = cdiv(cz(1, 0), R);
+    for (int e = threadIdx.x; e < np * 8; e += blockDim.x) {
+        const int p = e / 8, c = c0 + e % 8;
+        double2 a = cz(0, 0);
+        if (c < M)
+            for (int h = 0; h < nh; ++h) a = cfma(cm[p * nh + h], gr[(size_t)tb.hole_pos[h] * M + c], a);
+        y[e] = cmul(a, iR);
+    }
+    __syncthreads();
+    double2* out = GT + (size_t)w * ld + off;
+    for (int e = threadIdx.x; e < (N + np) * 8; e += blockDim.x) {
+        const int x = e / 8, c = c0 + e % 8;
+        if (c >= M) continue;
+        double2 v;
+        if (x < N) {
+            v = gr[(size_t)x * M + c];
+            for (int p = 0; p < np; ++p) v = cfms(gr[(size_t)x * M + tb.part_orb[p]], y[p * 8 + e % 8], v);
+        } else {
+            v = y[(x - N) * 8 + e % 8];
+        }
+        out[(size_t)x * M + c] = v;
+    }
+}
+
+void launch_gt(const SpinTables& tb, int nw, int M, const double2* Gr, const double2* Cm,
+               const double2* R, double2* GT, long long ld, long long off, cudaStream_t st)
+{
+    dim3 grid((M + 7) / 8, nw);
+    k_gt<<<grid, 256, 0, st>>>(tb, M, Gr, Cm, R, GT, ld, off);
+}
+
+// <D_0|phi> = det(D0^dag phi_a) det(D0^dag phi_b) per walker.
+__global__ void k_ref_ovlp(int nw, const double2* __restrict__ O0a, const double2* __restrict__ O0b,
+                           double2* __restrict__ out)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w < nw) out[w] = cmul(O0a[w], O0b[w]);
+}
+
+void launch_ref_ovlp(int nw, const double2* O0a, const double2* O0b, double2* out, cudaStream_t st)
+{
+    k_ref_ovlp<<<(nw + 127) / 128, 128, 0, st>>>(nw, O0a, O0b, out);
+}

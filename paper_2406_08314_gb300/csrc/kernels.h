@@ -1,0 +1,60 @@
+// Host-side launchers of the libmsd kernels (internal to csrc/).
+#pragma once
+
+#include "common.cuh"
+
+// Optional per-kernel event timing, supplied by the context.
+struct TimerHook {
+    void* self = nullptr;
+    void (*begin_fn)(void*, const char*, cudaStream_t) = nullptr;
+    void (*end_fn)(void*, cudaStream_t) = nullptr;
+    void begin(const char* name, cudaStream_t st) const { if (begin_fn) begin_fn(self, name, st); }
+    void end(cudaStream_t st) const { if (end_fn) end_fn(self, st); }
+};
+
+// k_wick.cu
+void launch_ref(const double2* phi, int nw, int M, int N, const SpinTables& T, double2* Gr,
+                double2* O0, double2* Gact, unsigned* err, cudaStream_t st);
+void launch_strings(const SpinTables& tb, int nw, const double2* Gact, double2* r, void* B,
+                    bool fp32, bool want_b, cudaStream_t st, const TimerHook& th);
+int weights_blocks(const SpinTables& tb);
+void launch_weights(const SpinTables& tb, int nw, const double2* r_self, const double2* r_other,
+                    int n_other, double2* wts, double2* part, int nslot, int slot0, cudaStream_t st);
+void launch_det_ratios(const PairTables& pt, int nw, int n_str_a, int n_str_b, const double2* ra,
+                       const double2* rb, double2* out, cudaStream_t st);
+void launch_sum_slots(int nw, const double2* part, int nslot, int slot0, int n, double2* out,
+                      const double2* O0a, const double2* O0b, double2* ovlp, cudaStream_t st);
+void launch_ref_ovlp(int nw, const double2* O0a, const double2* O0b, double2* out, cudaStream_t st);
+void launch_cmat(const SpinTables& tb, int nw, const double2* r, const double2* wts, const void* B,
+                 bool fp32, double2* Cm, cudaStream_t st);
+void launch_gt(const SpinTables& tb, int nw, int M, const double2* Gr, const double2* Cm,
+               const double2* R, double2* GT, long long ld, long long off, cudaStream_t st);
+
+// k_energy.cu
+void launch_gemm_zd(int Mr, int Nc, int K, const double2* A, long long lda, const double* B,
+                    long long ldb, double2* C, long long ldc, cudaStream_t st);
+size_t fepi_smem(const SpinTables& tb);
+void launch_fepi(const SpinTables& tb, int nw, int M, int n_chol, const double2* F, long long ldf,
+                 const double2* Gr, double2* v0, double2* xx, double2* Lact, double2* Xic,
+                 cudaStream_t st);
+void launch_onebody(const SpinTables& tb, int nw, int M, const double* h1, const double2* Gr,
+                    double2* e1, double2* Lh, cudaStream_t st);
+void launch_gamma_reduce(int nw, int X, int n_chol, int spin, const double2* v0a, const double2* v0b,
+                         const double2* xx, const double2* Lact, const double2* Xic,
+                         const double2* Lh, void* Y, bool fp32, double2* scal, cudaStream_t st);
+void launch_gram(int nw, int Xp, int Xq, int n_chol, const double2* P, const double2* Q, void* K,
+                 bool fp32, cudaStream_t st);
+int string_energy_blocks(const SpinTables& tb, int k);
+size_t string_energy_smem(const SpinTables& tb, bool fp32);
+int string_energy_slots(const SpinTables& tb);
+void launch_string_energy(const SpinTables& tb, int nw, const double2* r, const double2* wts,
+                          const void* B, const void* K, const void* Y, bool fp32, double2* part,
+                          int nslot, int slot0, cudaStream_t st);
+int pair_cross_slots(const PairTables& pt);
+void launch_pair_cross(const SpinTables& ta, const SpinTables& tb, const PairTables& pt, int nw,
+                       const double2* ra, const double2* rb, const void* Ba, const void* Bb,
+                       const void* K, bool fp32, double2* part, int nslot, int slot0,
+                       cudaStream_t st);
+void launch_final(int nw, const double2* part, int nslot, int nR, double e0, const double2* e1a,
+                  const double2* e1b, const double2* scal, const double2* O0a, const double2* O0b,
+                  double2* eloc, double2* ovlp, cudaStream_t st);

@@ -1,0 +1,986 @@
+// C-ABI entry points of libmsd (declared in include/msd.h): context, trial
+// preprocessing, workspace management and the orchestration of the
+// kernels for overlap, per-determinant ratios, force bias and local energy.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/msd.h"
+#include "common.cuh"
+#include "kernels.h"
+
+namespace {
+
+std::string g_create_error;
+
+struct SpinHost {
+    int N = 0, nh = 0, np = 0, n_str = 0;
+    std::vector<int> occ0, hole_pos, part_orb, hole_orb;
+    std::vector<uint8_t> str_h, str_p;
+    std::vector<int8_t> str_sign;
+    std::vector<int> str_k;
+    std::vector<int> csr_off, csr_other;
+    std::vector<double> csr_c;
+    int bucket[MSD_KMAX + 2] = {0};
+    long long b_per_walker = 0;
+    // device copies
+    int *d_occ0 = nullptr, *d_hole_pos = nullptr, *d_part_orb = nullptr;
+    uint8_t *d_str_h = nullptr, *d_str_p = nullptr;
+    int8_t* d_str_sign = nullptr;
+    int *d_csr_off = nullptr, *d_csr_other = nullptr;
+    double* d_csr_c = nullptr;
+    double* d_Lh = nullptr;   // [n_chol][N + np][M]
+};
+
+struct PairHost {
+    int n_det = 0;
+    std::vector<int> a, b, det_index;
+    std::vector<double> c;
+    int bucket[(MSD_KMAX + 1) * (MSD_KMAX + 1) + 1] = {0};
+    int *d_a = nullptr, *d_b = nullptr, *d_det_index = nullptr;
+    double* d_c = nullptr;
+};
+
+struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct msd_ctx {
+    int device = 0, M = 0, n[2] = {0, 0}, prec = MSD_FP64;
+    std::string err;
+    bool have_ham = false, have_trial = false;
+    int n_chol = 0;
+    double e0 = 0;
+    std::vector<double> h_h1, h_L;
+    double* d_h1 = nullptr;
+    double* d_Lcat = nullptr;   // [n_chol][Kd]
+    long long Kd = 0;
+    SpinHost sp[2];
+    PairHost pairs;
+    std::map<std::string, Buf> arena;
+    size_t ws_limit = (size_t)4 << 30;
+    int chunk = 0;
+    unsigned* d_err = nullptr;
+    unsigned* h_err = nullptr;
+    bool sync = true;
+    // timing
+    bool timing = false;
+    std::vector<std::string> knames;
+    std::vector<long long> klaunch;
+    std::vector<double> kms;
+    struct Pending { int k; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> ev_pool;
+    int open_k = -1;
+    cudaEvent_t open_ev = nullptr;
+    TimerHook hook;
+};
+
+namespace {
+
+int fail(msd_ctx* c, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf; else g_create_error = buf;
+    return code;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(ctx, MSD_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define CKLAUNCH()                                                                        \
+    do {                                                                                  \
+        cudaError_t e_ = cudaGetLastError();                                              \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(ctx, MSD_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+int upload(msd_ctx* ctx, T** dst, const std::vector<T>& src)
+{
+    if (*dst) { cudaFree(*dst); *dst = nullptr; }
+    if (src.empty()) return MSD_OK;
+    CK(cudaMalloc((void**)dst, sizeof(T) * src.size()));
+    CK(cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice));
+    return MSD_OK;
+}
+
+void timer_begin(void* self, const char* name, cudaStream_t st)
+{
+    msd_ctx* c = (msd_ctx*)self;
+    int k = -1;
+    for (size_t i = 0; i < c->knames.size(); ++i)
+        if (c->knames[i] == name) { k = (int)i; break; }
+    if (k < 0) {
+        k = (int)c->knames.size();
+        c->knames.push_back(name);
+        c->klaunch.push_back(0);
+        c->kms.push_back(0);
+    }
+    cudaEvent_t e;
+    if (c->ev_pool.empty()) cudaEventCreate(&e);
+    else { e = c->ev_pool.back(); c->ev_pool.pop_back(); }
+    cudaEventRecord(e, st);
+    c->open_k = k;
+    c->open_ev = e;
+}
+
+void timer_end(void* self, cudaStream_t st)
+{
+    msd_ctx* c = (msd_ctx*)self;
+    if (c->open_k < 0) return;
+    cudaEvent_t e;
+    if (c->ev_pool.empty()) cudaEventCreate(&e);
+    else { e = c->ev_pool.back(); c->ev_pool.pop_back(); }
+    cudaEventRecord(e, st);
+    c->pending.push_back({c->open_k, c->open_ev, e});
+    c->open_k = -1;
+}
+
+void collect_timing(msd_ctx* c)
+{
+    for (auto& p : c->pending) {
+        cudaEventSynchronize(p.b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, p.a, p.b);
+        c->kms[p.k] += ms;
+        c->klaunch[p.k] += 1;
+        c->ev_pool.push_back(p.a);
+        c->ev_pool.push_back(p.b);
+    }
+    c->pending.clear();
+}
+
+// Named device buffer of at least `bytes` (contents undefined on growth).
+int arena_get(msd_ctx* ctx, const char* name, size_t bytes, void** out)
+{
+    Buf& b = ctx->arena[name];
+    if (b.bytes < bytes) {
+        if (b.p) { cudaDeviceSynchronize(); cudaFree(b.p); b.p = nullptr; b.bytes = 0; }
+        bytes = (bytes + 255) & ~(size_t)255;
+        cudaError_t e = cudaMalloc(&b.p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, MSD_ERR_NOMEM, "device allocation of %zu bytes for %s failed", bytes, name);
+        }
+        b.bytes = bytes;
+    }
+    *out = b.p;
+    return MSD_OK;
+}
+
+bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+SpinTables tables(const SpinHost& s, int cap)
+{
+    SpinTables t;
+    t.N = s.N; t.nh = s.nh; t.np = s.np; t.n_str = s.n_str;
+    for (int k = 0; k < MSD_KMAX + 2; ++k) t.bucket[k] = s.bucket[k];
+    t.occ0 = s.d_occ0; t.hole_pos = s.d_hole_pos; t.part_orb = s.d_part_orb;
+    t.str_h = s.d_str_h; t.str_p = s.d_str_p; t.str_sign = s.d_str_sign;
+    t.csr_off = s.d_csr_off; t.csr_other = s.d_csr_other; t.csr_c = s.d_csr_c;
+    long long off = 0;
+    for (int k = 0; k <= MSD_KMAX; ++k) {
+        t.b_off[k] = off;
+        off += (long long)cap * k * k * (s.bucket[k + 1] - s.bucket[k]);
+    }
+    t.b_off[MSD_KMAX + 1] = off;
+    t.b_per_walker = s.b_per_walker;
+    return t;
+}
+
+PairTables pair_tables(const PairHost& p)
+{
+    PairTables t;
+    t.n_det = p.n_det;
+    for (int i = 0; i < (MSD_KMAX + 1) * (MSD_KMAX + 1) + 1; ++i) t.bucket[i] = p.bucket[i];
+    t.a = p.d_a; t.b = p.d_b; t.c = p.d_c; t.det_index = p.d_det_index;
+    return t;
+}
+
+// Excitation strings of one spin from the occupation lists (Sec. II B: CI
+// determinants as excitations of the reference, grouped by level).
+int build_spin(msd_ctx* ctx, int s, const int32_t* occ, int n_det, std::vector<int>& sid)
+{
+    SpinHost& S = ctx->sp[s];
+    const int N = ctx->n[s], M = ctx->M;
+    S = SpinHost{};
+    S.N = N;
+    S.occ0.assign(occ, occ + N);
+    std::vector<int> pos0(M, -1);
+    for (int j = 0; j < N; ++j) {
+        const int o = S.occ0[j];
+        if (o < 0 || o >= M) return fail(ctx, MSD_ERR_ARG, "occupation %d out of range [0,%d)", o, M);
+        if (j && o <= S.occ0[j - 1]) return fail(ctx, MSD_ERR_ARG, "reference occupations not strictly ascending");
+        pos0[o] = j;
+    }
+    std::map<std::vector<int>, int> key2tmp;
+    std::vector<std::vector<int>> keys;
+    std::vector<int> tmp_of_det(n_det);
+    std::vector<char> is_hole(M, 0), is_part(M, 0);
+    std::vector<int> holes, parts, key;
+    for (int I = 0; I < n_det; ++I) {
+        const int32_t* o = occ + (size_t)I * N;
+        holes.clear(); parts.clear();
+        std::vector<char> in(M, 0);
+        for (int j = 0; j < N; ++j) {
+            if (o[j] < 0 || o[j] >= M)
+                return fail(ctx, MSD_ERR_ARG, "determinant %d: orbital %d out of range", I, o[j]);
+            if (j && o[j] <= o[j - 1])
+                return fail(ctx, MSD_ERR_ARG, "determinant %d: occupations not strictly ascending", I);
+            in[o[j]] = 1;
+            if (pos0[o[j]] < 0) parts.push_back(o[j]);
+        }
+        for (int j = 0; j < N; ++j)
+            if (!in[S.occ0[j]]) holes.push_back(S.occ0[j]);
+        if ((int)holes.size() > MSD_KMAX)
+            return fail(ctx, MSD_ERR_SHAPE, "determinant %d: excitation level %d above %d", I,
+                        (int)holes.size(), MSD_KMAX);
+        for (int h : holes) is_hole[h] = 1;
+        for (int p : parts) is_part[p] = 1;
+        key.assign(holes.begin(), holes.end());
+        key.insert(key.end(), parts.begin(), parts.end());
+        auto it = key2tmp.find(key);
+        if (it == key2tmp.end()) {
+            it = key2tmp.emplace(key, (int)keys.size()).first;
+            keys.push_back(key);
+        }
+        tmp_of_det[I] = it->second;
+    }
+    for (int o = 0; o < M; ++o) {
+        if (is_hole[o]) { S.hole_orb.push_back(o); S.hole_pos.push_back(pos0[o]); }
+        if (is_part[o]) S.part_orb.push_back(o);
+    }
+    S.nh = (int)S.hole_orb.size();
+    S.np = (int)S.part_orb.size();
+    if (S.nh * S.np > MSD_XMAX)
+        return fail(ctx, MSD_ERR_SHAPE, "spin %d: active block %d x %d exceeds %d entries", s, S.nh,
+                    S.np, MSD_XMAX);
+    std::vector<int> hidx(M, -1), pidx(M, -1);
+    for (int i = 0; i < S.nh; ++i) hidx[S.hole_orb[i]] = i;
+    for (int i = 0; i < S.np; ++i) pidx[S.part_orb[i]] = i;
+    // order strings by level, then lexicographically
+    std::vector<int> order(keys.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::sort(order.begin(), order.end(), [&](int x, int y) {
+        if (keys[x].size() != keys[y].size()) return keys[x].size() < keys[y].size();
+        return keys[x] < keys[y];
+    });
+    std::vector<int> final_of_tmp(keys.size());
+    S.n_str = (int)keys.size();
+    S.str_h.assign((size_t)S.n_str * MSD_KMAX, 0);
+    S.str_p.assign((size_t)S.n_str * MSD_KMAX, 0);
+    S.str_sign.assign(S.n_str, 1);
+    S.str_k.assign(S.n_str, 0);
+    for (int f = 0; f < S.n_str; ++f) {
+        const std::vector<int>& k = keys[order[f]];
+        final_of_tmp[order[f]] = f;
+        const int lvl = (int)k.size() / 2;
+        S.str_k[f] = lvl;
+        std::vector<int> inplace(S.occ0);
+        for (int i = 0; i < lvl; ++i) {
+            S.str_h[(size_t)f * MSD_KMAX + i] = (uint8_t)hidx[k[i]];
+            S.str_p[(size_t)f * MSD_KMAX + i] = (uint8_t)pidx[k[lvl + i]];
+            inplace[pos0[k[i]]] = k[lvl + i];
+        }
+        int inv = 0;   // parity of the permutation that sorts the in-place list
+        for (int i = 0; i < N; ++i)
+            for (int j = i + 1; j < N; ++j) inv += inplace[i] > inplace[j];
+        S.str_sign[f] = (inv & 1) ? -1 : 1;
+    }
+    for (int k = 0; k <= MSD_KMAX + 1; ++k) S.bucket[k] = 0;
+    for (int f = 0; f < S.n_str; ++f) S.bucket[S.str_k[f] + 1]++;
+    for (int k = 1; k <= MSD_KMAX + 1; ++k) S.bucket[k] += S.bucket[k - 1];
+    if (S.bucket[1] != 1 || keys[order[0]].size() != 0)
+        return fail(ctx, MSD_ERR_ARG, "spin %d: the reference string is missing", s);
+    S.b_per_walker = 0;
+    for (int k = 0; k <= MSD_KMAX; ++k) S.b_per_walker += (long long)k * k * (S.bucket[k + 1] - S.bucket[k]);
+    sid.resize(n_det);
+    for (int I = 0; I < n_det; ++I) sid[I] = final_of_tmp[tmp_of_det[I]];
+    return MSD_OK;
+}
+
+int upload_spin(msd_ctx* ctx, SpinHost& S)
+{
+    int rc;
+    if ((rc = upload(ctx, &S.d_occ0, S.occ0))) return rc;
+    if ((rc = upload(ctx, &S.d_hole_pos, S.hole_pos))) return rc;
+    if ((rc = upload(ctx, &S.d_part_orb, S.part_orb))) return rc;
+    if ((rc = upload(ctx, &S.d_str_h, S.str_h))) return rc;
+    if ((rc = upload(ctx, &S.d_str_p, S.str_p))) return rc;
+    if ((rc = upload(ctx, &S.d_str_sign, S.str_sign))) return rc;
+    if ((rc = upload(ctx, &S.d_csr_off, S.csr_off))) return rc;
+    if ((rc = upload(ctx, &S.d_csr_other, S.csr_other))) return rc;
+    if ((rc = upload(ctx, &S.d_csr_c, S.csr_c))) return rc;
+    return MSD_OK;
+}
+
+void free_spin(SpinHost& S)
+{
+    cudaFree(S.d_occ0); cudaFree(S.d_hole_pos); cudaFree(S.d_part_orb); cudaFree(S.d_str_h);
+    cudaFree(S.d_str_p); cudaFree(S.d_str_sign); cudaFree(S.d_csr_off); cudaFree(S.d_csr_other);
+    cudaFree(S.d_csr_c); cudaFree(S.d_Lh);
+    S.d_occ0 = S.d_hole_pos = S.d_part_orb = nullptr;
+    S.d_str_h = S.d_str_p = nullptr;
+    S.d_str_sign = nullptr;
+    S.d_csr_off = S.d_csr_other = nullptr;
+    S.d_csr_c = nullptr;
+    S.d_Lh = nullptr;
+}
+
+// Half-rotated Cholesky vectors (the "half_rotate" of the trial, Sec. III):
+// rows occ0 then P of each L_g, per spin, and both spins concatenated.
+int build_half_rotated(msd_ctx* ctx)
+{
+    if (!ctx->have_ham || !ctx->have_trial) return MSD_OK;
+    const int M = ctx->M, G = ctx->n_chol;
+    long long Kd = 0;
+    for (int s = 0; s < 2; ++s) Kd += (long long)(ctx->sp[s].N + ctx->sp[s].np) * M;
+    ctx->Kd = Kd;
+    std::vector<double> cat((size_t)G * Kd);
+    long long off = 0;
+    for (int s = 0; s < 2; ++s) {
+        SpinHost& S = ctx->sp[s];
+        const int NC = S.N + S.np;
+        std::vector<double> lh((size_t)G * NC * M);
+        for (int g = 0; g < G; ++g)
+            for (int c = 0; c < NC; ++c) {
+                const int row = c < S.N ? S.occ0[c] : S.part_orb[c - S.N];
+                const double* src = &ctx->h_L[((size_t)g * M + row) * M];
+                std::copy(src, src + M, &lh[((size_t)g * NC + c) * M]);
+                std::copy(src, src + M, &cat[(size_t)g * Kd + off + (size_t)c * M]);
+            }
+        int rc = upload(ctx, &S.d_Lh, lh);
+        if (rc) return rc;
+        off += (long long)NC * M;
+    }
+    return upload(ctx, &ctx->d_Lcat, cat);
+}
+
+int check_ready(msd_ctx* ctx)
+{
+    if (!ctx) return MSD_ERR_ARG;
+    if (!ctx->have_ham || !ctx->have_trial)
+        return fail(ctx, MSD_ERR_STATE, "set the Hamiltonian and the trial first");
+    return MSD_OK;
+}
+
+// Walkers per chunk for a given per-walker footprint.
+int chunk_for(msd_ctx* ctx, size_t per_walker, int n_w)
+{
+    size_t c = per_walker ? ctx->ws_limit / per_walker : (size_t)n_w;
+    if (c < 1) c = 1;
+    if (c > (size_t)n_w) c = n_w;
+    ctx->chunk = (int)c;
+    return (int)c;
+}
+
+// Inputs: device pointers pass through; host pointers are copied into
+// context-owned staging buffers.
+struct Staged {
+    const double2* pa;
+    const double2* pb;
+    bool host_any;
+};
+
+int stage_inputs(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b,
+                 cudaStream_t st, Staged& out)
+{
+    const size_t ba = sizeof(double2) * (size_t)n_w * ctx->M * ctx->n[0];
+    const size_t bb = sizeof(double2) * (size_t)n_w * ctx->M * ctx->n[1];
+    out.host_any = false;
+    if (is_device_ptr(phi_a)) out.pa = (const double2*)phi_a;
+    else {
+        void* p; int rc = arena_get(ctx, "stage_phi_a", ba, &p); if (rc) return rc;
+        CK(cudaMemcpyAsync(p, phi_a, ba, cudaMemcpyHostToDevice, st));
+        out.pa = (const double2*)p; out.host_any = true;
+    }
+    if (is_device_ptr(phi_b)) out.pb = (const double2*)phi_b;
+    else {
+        void* p; int rc = arena_get(ctx, "stage_phi_b", bb, &p); if (rc) return rc;
+        CK(cudaMemcpyAsync(p, phi_b, bb, cudaMemcpyHostToDevice, st));
+        out.pb = (const double2*)p; out.host_any = true;
+    }
+    return MSD_OK;
+}
+
+// Output either written directly (device) or via staging then copied back.
+struct Out {
+    double* user = nullptr;
+    double2* dev = nullptr;
+    size_t bytes = 0;
+    bool host = false;
+};
+
+int stage_output(msd_ctx* ctx, const char* name, double* user, size_t n_complex, Out& o)
+{
+    o.user = user;
+    o.bytes = sizeof(double2) * n_complex;
+    if (!user) { o.dev = nullptr; return MSD_OK; }
+    if (is_device_ptr(user)) { o.dev = (double2*)user; o.host = false; return MSD_OK; }
+    void* p; int rc = arena_get(ctx, name, o.bytes, &p); if (rc) return rc;
+    o.dev = (double2*)p; o.host = true;
+    return MSD_OK;
+}
+
+int finish(msd_ctx* ctx, cudaStream_t st, std::initializer_list<Out*> outs, bool host_in)
+{
+    bool host = host_in;
+    for (Out* o : outs)
+        if (o->user && o->host) {
+            CK(cudaMemcpyAsync(o->user, o->dev, o->bytes, cudaMemcpyDeviceToHost, st));
+            host = true;
+        }
+    CKLAUNCH();
+    if (ctx->sync || host) {
+        CK(cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const unsigned e = *ctx->h_err;
+        if (e & MSD_DEV_ERR_SINGULAR)
+            return fail(ctx, MSD_ERR_REF_SINGULAR, "D_0^dag phi is singular for some walker");
+        if (e & MSD_DEV_ERR_TIMEOUT) return fail(ctx, MSD_ERR_TIMEOUT, "a device-side wait expired");
+        if (e & MSD_DEV_ERR_BOUNDS) return fail(ctx, MSD_ERR_SHAPE, "a device-side bounds check failed");
+    }
+    return MSD_OK;
+}
+
+// Per-chunk workspace for the overlap part.
+struct Chunk {
+    double2 *Gr[2], *O0[2], *Gact[2], *r[2], *wts[2], *part;
+    void* B[2];
+    int nslot, nR;
+};
+
+size_t overlap_bytes_per_walker(msd_ctx* ctx, bool want_b, int nslot)
+{
+    size_t b = 0;
+    for (int s = 0; s < 2; ++s) {
+        const SpinHost& S = ctx->sp[s];
+        b += (size_t)S.N * ctx->M + 1 + (size_t)S.nh * S.np + 2 * (size_t)S.n_str;
+        if (want_b) b += S.b_per_walker;
+    }
+    b += nslot;
+    return b * sizeof(double2);
+}
+
+int chunk_alloc(msd_ctx* ctx, int cap, bool want_b, int nslot, Chunk& c)
+{
+    int rc;
+    static const char* nGr[2] = {"Gr_a", "Gr_b"}, *nO0[2] = {"O0_a", "O0_b"};
+    static const char* nGa[2] = {"Gact_a", "Gact_b"}, *nr[2] = {"r_a", "r_b"};
+    static const char* nw[2] = {"wts_a", "wts_b"}, *nB[2] = {"B_a", "B_b"};
+    for (int s = 0; s < 2; ++s) {
+        const SpinHost& S = ctx->sp[s];
+        void* p;
+        if ((rc = arena_get(ctx, nGr[s], sizeof(double2) * cap * S.N * ctx->M, &p))) return rc; c.Gr[s] = (double2*)p;
+        if ((rc = arena_get(ctx, nO0[s], sizeof(double2) * cap, &p))) return rc; c.O0[s] = (double2*)p;
+        if ((rc = arena_get(ctx, nGa[s], sizeof(double2) * cap * std::max(1, S.nh * S.np), &p))) return rc; c.Gact[s] = (double2*)p;
+        if ((rc = arena_get(ctx, nr[s], sizeof(double2) * cap * S.n_str, &p))) return rc; c.r[s] = (double2*)p;
+        if ((rc = arena_get(ctx, nw[s], sizeof(double2) * cap * S.n_str, &p))) return rc; c.wts[s] = (double2*)p;
+        c.B[s] = nullptr;
+        if (want_b) {
+            if ((rc = arena_get(ctx, nB[s], sizeof(double2) * std::max<long long>(1, cap * S.b_per_walker), &p))) return rc;
+            c.B[s] = p;
+        }
+    }
+    void* p;
+    if ((rc = arena_get(ctx, "part", sizeof(double2) * cap * std::max(1, nslot), &p))) return rc;
+    c.part = (double2*)p;
+    c.nslot = nslot;
+    c.nR = weights_blocks(tables(ctx->sp[0], cap));
+    return MSD_OK;
+}
+
+// Reference inverse, string minors and weights for walkers [w0, w0 + nw).
+int run_overlap_part(msd_ctx* ctx, const Staged& in, int w0, int nw, int cap, Chunk& c,
+                     bool want_b, bool fp32_b, cudaStream_t st)
+{
+    const int M = ctx->M;
+    const TimerHook& th = ctx->hook;
+    SpinTables T[2] = {tables(ctx->sp[0], cap), tables(ctx->sp[1], cap)};
+    const double2* phi[2] = {in.pa + (size_t)w0 * M * ctx->n[0], in.pb + (size_t)w0 * M * ctx->n[1]};
+    for (int s = 0; s < 2; ++s) {
+        th.begin("k_ref", st);
+        launch_ref(phi[s], nw, M, ctx->n[s], T[s], c.Gr[s], c.O0[s], c.Gact[s], ctx->d_err, st);
+        th.end(st);
+        CKLAUNCH();
+    }
+    for (int s = 0; s < 2; ++s) {
+        launch_strings(T[s], nw, c.Gact[s], c.r[s], c.B[s], fp32_b, want_b, st, th);
+        CKLAUNCH();
+    }
+    th.begin("k_weights", st);
+    launch_weights(T[0], nw, c.r[0], c.r[1], T[1].n_str, c.wts[0], c.part, c.nslot, 0, st);
+    launch_weights(T[1], nw, c.r[1], c.r[0], T[0].n_str, c.wts[1], nullptr, c.nslot, 0, st);
+    th.end(st);
+    CKLAUNCH();
+    return MSD_OK;
+}
+
+int begin_call(msd_ctx* ctx, int n_w, const double* pa, const double* pb, cudaStream_t st)
+{
+    int rc = check_ready(ctx);
+    if (rc) return rc;
+    if (n_w < 0 || (n_w > 0 && (!pa || !pb))) return fail(ctx, MSD_ERR_ARG, "bad walker arguments");
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), st));
+    return MSD_OK;
+}
+
+}  // namespace
+
+// ========================================================================
+extern "C" {
+
+int msd_create(msd_ctx** out, int M, int n_alpha, int n_beta, int precision, int device)
+{
+    msd_ctx* ctx = nullptr;
+    if (!out) return fail(nullptr, MSD_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (M <= 0 || n_alpha <= 0 || n_beta <= 0 || n_alpha > M || n_beta > M)
+        return fail(nullptr, MSD_ERR_ARG, "invalid sizes M=%d n_alpha=%d n_beta=%d", M, n_alpha, n_beta);
+    if (n_alpha > MSD_NMAX || n_beta > MSD_NMAX)
+        return fail(nullptr, MSD_ERR_SHAPE, "at most %d electrons per spin", MSD_NMAX);
+    if (precision != MSD_FP64 && precision != MSD_MIXED)
+        return fail(nullptr, MSD_ERR_ARG, "unknown precision %d", precision);
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return fail(nullptr, MSD_ERR_CUDA, "CUDA device %d not available", device);
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return fail(nullptr, MSD_ERR_CUDA, "cudaSetDevice failed");
+    ctx = new msd_ctx();
+    ctx->device = device; ctx->M = M; ctx->n[0] = n_alpha; ctx->n[1] = n_beta; ctx->prec = precision;
+    if (cudaMalloc(&ctx->d_err, sizeof(unsigned)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_err, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return fail(nullptr, MSD_ERR_NOMEM, "allocation failed");
+    }
+    cudaMemset(ctx->d_err, 0, sizeof(unsigned));
+    ctx->hook.self = ctx;
+    *out = ctx;
+    return MSD_OK;
+}
+
+void msd_destroy(msd_ctx* ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto& kv : ctx->arena) cudaFree(kv.second.p);
+    for (int s = 0; s < 2; ++s) free_spin(ctx->sp[s]);
+    cudaFree(ctx->pairs.d_a); cudaFree(ctx->pairs.d_b); cudaFree(ctx->pairs.d_c);
+    cudaFree(ctx->pairs.d_det_index);
+    cudaFree(ctx->d_h1); cudaFree(ctx->d_Lcat); cudaFree(ctx->d_err);
+    cudaFreeHost(ctx->h_err);
+    for (auto& p : ctx->pending) { ctx->ev_pool.push_back(p.a); ctx->ev_pool.push_back(p.b); }
+    for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+    delete ctx;
+}
+
+const char* msd_last_error(const msd_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+int msd_set_hamiltonian(msd_ctx* ctx, const double* h1, double e0, int n_chol, const double* L)
+{
+    if (!ctx) return MSD_ERR_ARG;
+    if (!h1 || !L || n_chol <= 0) return fail(ctx, MSD_ERR_ARG, "h1, L and n_chol > 0 are required");
+    CK(cudaSetDevice(ctx->device));
+    const int M = ctx->M;
+    ctx->h_h1.assign(h1, h1 + (size_t)2 * M * M);
+    ctx->h_L.assign(L, L + (size_t)n_chol * M * M);
+    ctx->n_chol = n_chol;
+    ctx->e0 = e0;
+    int rc = upload(ctx, &ctx->d_h1, ctx->h_h1);
+    if (rc) return rc;
+    ctx->have_ham = true;
+    return build_half_rotated(ctx);
+}
+
+int msd_set_trial(msd_ctx* ctx, int n_det, const double* coeff, const int32_t* occ_a,
+                  const int32_t* occ_b)
+{
+    if (!ctx) return MSD_ERR_ARG;
+    if (n_det <= 0 || !coeff || !occ_a || !occ_b) return fail(ctx, MSD_ERR_ARG, "empty trial");
+    CK(cudaSetDevice(ctx->device));
+    ctx->have_trial = false;
+    std::vector<int> sid[2];
+    const int32_t* occ[2] = {occ_a, occ_b};
+    for (int s = 0; s < 2; ++s) {
+        free_spin(ctx->sp[s]);
+        int rc = build_spin(ctx, s, occ[s], n_det, sid[s]);
+        if (rc) return rc;
+    }
+    // determinants ordered by (level_a, level_b, a, b)
+    PairHost& P = ctx->pairs;
+    cudaFree(P.d_a); cudaFree(P.d_b); cudaFree(P.d_c); cudaFree(P.d_det_index);
+    P = PairHost{};
+    P.n_det = n_det;
+    std::vector<int> order(n_det);
+    for (int i = 0; i < n_det; ++i) order[i] = i;
+    auto lv = [&](int s, int I) { return ctx->sp[s].str_k[sid[s][I]]; };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        const int bx = lv(0, x) * (MSD_KMAX + 1) + lv(1, x), by = lv(0, y) * (MSD_KMAX + 1) + lv(1, y);
+        if (bx != by) return bx < by;
+        if (sid[0][x] != sid[0][y]) return sid[0][x] < sid[0][y];
+        return sid[1][x] < sid[1][y];
+    });
+    for (int i = 0; i < n_det; ++i) {
+        const int I = order[i];
+        P.a.push_back(sid[0][I]); P.b.push_back(sid[1][I]);
+        P.c.push_back(coeff[I]); P.det_index.push_back(I);
+        P.bucket[lv(0, I) * (MSD_KMAX + 1) + lv(1, I) + 1]++;
+    }
+    for (int i = 1; i < (MSD_KMAX + 1) * (MSD_KMAX + 1) + 1; ++i) P.bucket[i] += P.bucket[i - 1];
+    // CSR per spin: determinants containing each string
+    for (int s = 0; s < 2; ++s) {
+        SpinHost& S = ctx->sp[s];
+        S.csr_off.assign(S.n_str + 1, 0);
+        for (int I = 0; I < n_det; ++I) S.csr_off[sid[s][I] + 1]++;
+        for (int i = 0; i < S.n_str; ++i) S.csr_off[i + 1] += S.csr_off[i];
+        std::vector<int> fill(S.csr_off.begin(), S.csr_off.end() - 1);
+        S.csr_other.assign(n_det, 0);
+        S.csr_c.assign(n_det, 0);
+        for (int i = 0; i < n_det; ++i) {   // in pair order: deterministic sums
+            const int I = order[i];
+            const int e = fill[sid[s][I]]++;
+            S.csr_other[e] = sid[1 - s][I];
+            S.csr_c[e] = coeff[I];
+        }
+        int rc = upload_spin(ctx, S);
+        if (rc) return rc;
+    }
+    int rc;
+    if ((rc = upload(ctx, &P.d_a, P.a))) return rc;
+    if ((rc = upload(ctx, &P.d_b, P.b))) return rc;
+    if ((rc = upload(ctx, &P.d_c, P.c))) return rc;
+    if ((rc = upload(ctx, &P.d_det_index, P.det_index))) return rc;
+    // shared-memory needs of the energy kernels
+    for (int s = 0; s < 2; ++s) {
+        const SpinTables t = tables(ctx->sp[s], 1);
+        if (fepi_smem(t) > 200 * 1024 || string_energy_smem(t, false) > 220 * 1024)
+            return fail(ctx, MSD_ERR_SHAPE, "spin %d: N=%d, active block %dx%d too large", s, t.N, t.nh, t.np);
+    }
+    ctx->have_trial = true;
+    return build_half_rotated(ctx);
+}
+
+int msd_set_precision(msd_ctx* ctx, int precision)
+{
+    if (!ctx) return MSD_ERR_ARG;
+    if (precision != MSD_FP64 && precision != MSD_MIXED)
+        return fail(ctx, MSD_ERR_ARG, "unknown precision %d", precision);
+    ctx->prec = precision;
+    return MSD_OK;
+}
+
+int msd_overlap(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b, double* ovlp,
+                double* ratio_sum, void* stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = begin_call(ctx, n_w, phi_a, phi_b, st);
+    if (rc) return rc;
+    if (n_w == 0) return MSD_OK;
+    if (!ovlp && !ratio_sum) return fail(ctx, MSD_ERR_ARG, "no output requested");
+    Staged in;
+    if ((rc = stage_inputs(ctx, n_w, phi_a, phi_b, st, in))) return rc;
+    Out o_ov, o_rs;
+    if ((rc = stage_output(ctx, "out_ovlp", ovlp, n_w, o_ov))) return rc;
+    if ((rc = stage_output(ctx, "out_rsum", ratio_sum, n_w, o_rs))) return rc;
+    const int nR = weights_blocks(tables(ctx->sp[0], 1));
+    const int cap = chunk_for(ctx, overlap_bytes_per_walker(ctx, false, nR), n_w);
+    Chunk c;
+    if ((rc = chunk_alloc(ctx, cap, false, nR, c))) return rc;
+    for (int w0 = 0; w0 < n_w; w0 += cap) {
+        const int nw = std::min(cap, n_w - w0);
+        if ((rc = run_overlap_part(ctx, in, w0, nw, cap, c, false, false, st))) return rc;
+        ctx->hook.begin("k_sum_slots", st);
+        launch_sum_slots(nw, c.part, c.nslot, 0, c.nR, o_rs.dev ? o_rs.dev + w0 : nullptr, c.O0[0],
+                         c.O0[1], o_ov.dev ? o_ov.dev + w0 : nullptr, st);
+        ctx->hook.end(st);
+        CKLAUNCH();
+    }
+    return finish(ctx, st, {&o_ov, &o_rs}, in.host_any);
+}
+
+int msd_det_ratios(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b, double* ratios,
+                   double* ref_ovlp, void* stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = begin_call(ctx, n_w, phi_a, phi_b, st);
+    if (rc) return rc;
+    if (n_w == 0) return MSD_OK;
+    if (!ratios) return fail(ctx, MSD_ERR_ARG, "ratios is NULL");
+    Staged in;
+    if ((rc = stage_inputs(ctx, n_w, phi_a, phi_b, st, in))) return rc;
+    Out o_r, o_o;
+    if ((rc = stage_output(ctx, "out_ratios", ratios, (size_t)n_w * ctx->pairs.n_det, o_r))) return rc;
+    if ((rc = stage_output(ctx, "out_refovlp", ref_ovlp, n_w, o_o))) return rc;
+    const int nR = weights_blocks(tables(ctx->sp[0], 1));
+    const int cap = chunk_for(ctx, overlap_bytes_per_walker(ctx, false, nR), n_w);
+    Chunk c;
+    if ((rc = chunk_alloc(ctx, cap, false, nR, c))) return rc;
+    for (int w0 = 0; w0 < n_w; w0 += cap) {
+        const int nw = std::min(cap, n_w - w0);
+        if ((rc = run_overlap_part(ctx, in, w0, nw, cap, c, false, false, st))) return rc;
+        ctx->hook.begin("k_det_ratios", st);
+        launch_det_ratios(pair_tables(ctx->pairs), nw, ctx->sp[0].n_str, ctx->sp[1].n_str, c.r[0],
+                          c.r[1], o_r.dev + (size_t)w0 * ctx->pairs.n_det, st);
+        if (o_o.dev) launch_ref_ovlp(nw, c.O0[0], c.O0[1], o_o.dev + w0, st);
+        ctx->hook.end(st);
+        CKLAUNCH();
+    }
+    return finish(ctx, st, {&o_r, &o_o}, in.host_any);
+}
+
+int msd_force_bias(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b, double* vbias,
+                   double* ovlp, void* stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = begin_call(ctx, n_w, phi_a, phi_b, st);
+    if (rc) return rc;
+    if (n_w == 0) return MSD_OK;
+    if (!vbias) return fail(ctx, MSD_ERR_ARG, "vbias is NULL");
+    const bool fp32 = ctx->prec == MSD_MIXED;
+    Staged in;
+    if ((rc = stage_inputs(ctx, n_w, phi_a, phi_b, st, in))) return rc;
+    Out o_v, o_ov;
+    if ((rc = stage_output(ctx, "out_vbias", vbias, (size_t)n_w * ctx->n_chol, o_v))) return rc;
+    if ((rc = stage_output(ctx, "out_ovlp", ovlp, n_w, o_ov))) return rc;
+    const int nR = weights_blocks(tables(ctx->sp[0], 1));
+    size_t per = overlap_bytes_per_walker(ctx, true, nR);
+    per += sizeof(double2) * (ctx->Kd + 1 + ctx->sp[0].nh * ctx->sp[0].np + ctx->sp[1].nh * ctx->sp[1].np);
+    const int cap = chunk_for(ctx, per, n_w);
+    Chunk c;
+    if ((rc = chunk_alloc(ctx, cap, true, nR, c))) return rc;
+    void *GT, *Rs, *Cm[2];
+    if ((rc = arena_get(ctx, "GT", sizeof(double2) * cap * ctx->Kd, &GT))) return rc;
+    if ((rc = arena_get(ctx, "Rsum", sizeof(double2) * cap, &Rs))) return rc;
+    if ((rc = arena_get(ctx, "Cm_a", sizeof(double2) * cap * std::max(1, ctx->sp[0].nh * ctx->sp[0].np), &Cm[0]))) return rc;
+    if ((rc = arena_get(ctx, "Cm_b", sizeof(double2) * cap * std::max(1, ctx->sp[1].nh * ctx->sp[1].np), &Cm[1]))) return rc;
+    for (int w0 = 0; w0 < n_w; w0 += cap) {
+        const int nw = std::min(cap, n_w - w0);
+        if ((rc = run_overlap_part(ctx, in, w0, nw, cap, c, true, fp32, st))) return rc;
+        const TimerHook& th = ctx->hook;
+        th.begin("k_sum_slots", st);
+        launch_sum_slots(nw, c.part, c.nslot, 0, c.nR, (double2*)Rs, c.O0[0], c.O0[1],
+                         o_ov.dev ? o_ov.dev + w0 : nullptr, st);
+        th.end(st);
+        long long off = 0;
+        for (int s = 0; s < 2; ++s) {
+            const SpinTables T = tables(ctx->sp[s], cap);
+            th.begin("k_cmat", st);
+            launch_cmat(T, nw, c.r[s], c.wts[s], c.B[s], fp32, (double2*)Cm[s], st);
+            th.end(st);
+            th.begin("k_gt", st);
+            launch_gt(T, nw, ctx->M, c.Gr[s], (double2*)Cm[s], (double2*)Rs, (double2*)GT, ctx->Kd, off, st);
+            th.end(st);
+            off += (long long)(T.N + T.np) * ctx->M;
+        }
+        CKLAUNCH();
+        {
+            th.begin("k_gemm_vbias", st);
+            launch_gemm_zd(nw, ctx->n_chol, (int)ctx->Kd, (const double2*)GT, ctx->Kd, ctx->d_Lcat,
+                           ctx->Kd, o_v.dev + (size_t)w0 * ctx->n_chol, ctx->n_chol, st);
+            th.end(st);
+        }
+        CKLAUNCH();
+    }
+    return finish(ctx, st, {&o_v, &o_ov}, in.host_any);
+}
+
+int msd_local_energy(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b, double* e_loc,
+                     double* ovlp, void* stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = begin_call(ctx, n_w, phi_a, phi_b, st);
+    if (rc) return rc;
+    if (n_w == 0) return MSD_OK;
+    if (!e_loc) return fail(ctx, MSD_ERR_ARG, "e_loc is NULL");
+    const bool fp32 = ctx->prec == MSD_MIXED;
+    const int M = ctx->M, G = ctx->n_chol;
+    Staged in;
+    if ((rc = stage_inputs(ctx, n_w, phi_a, phi_b, st, in))) return rc;
+    Out o_e, o_ov;
+    if ((rc = stage_output(ctx, "out_eloc", e_loc, n_w, o_e))) return rc;
+    if ((rc = stage_output(ctx, "out_ovlp", ovlp, n_w, o_ov))) return rc;
+    SpinTables T1[2] = {tables(ctx->sp[0], 1), tables(ctx->sp[1], 1)};
+    const int nR = weights_blocks(T1[0]);
+    const int nE = string_energy_slots(T1[0]) + string_energy_slots(T1[1]) +
+                   pair_cross_slots(pair_tables(ctx->pairs));
+    const int nslot = nR + nE;
+    const int X[2] = {T1[0].nh * T1[0].np, T1[1].nh * T1[1].np};
+    size_t per = overlap_bytes_per_walker(ctx, true, nslot);
+    size_t e_per = 8 + 2;
+    for (int s = 0; s < 2; ++s)
+        e_per += (size_t)T1[s].N * G * (T1[s].N + T1[s].np) + (size_t)G * (2 + 2 * X[s]) + 3 * X[s] + 1;
+    e_per += (size_t)X[0] * X[0] + (size_t)X[1] * X[1] + (size_t)X[0] * X[1];
+    per += e_per * sizeof(double2);
+    const int cap = chunk_for(ctx, per, n_w);
+    Chunk c;
+    if ((rc = chunk_alloc(ctx, cap, true, nslot, c))) return rc;
+    void *F[2], *v0[2], *xx[2], *La[2], *Xi[2], *Lh1[2], *e1[2], *Y[2], *Kaa, *Kbb, *Kab, *scal;
+    static const char* nm[2][8] = {{"F_a", "v0_a", "xx_a", "Lact_a", "Xic_a", "Lh1_a", "e1_a", "Y_a"},
+                                   {"F_b", "v0_b", "xx_b", "Lact_b", "Xic_b", "Lh1_b", "e1_b", "Y_b"}};
+    for (int s = 0; s < 2; ++s) {
+        const int NC = T1[s].N + T1[s].np;
+        const size_t xs = std::max(1, X[s]);
+        if ((rc = arena_get(ctx, nm[s][0], sizeof(double2) * cap * T1[s].N * (size_t)G * NC, &F[s]))) return rc;
+        if ((rc = arena_get(ctx, nm[s][1], sizeof(double2) * cap * (size_t)G, &v0[s]))) return rc;
+        if ((rc = arena_get(ctx, nm[s][2], sizeof(double2) * cap * (size_t)G, &xx[s]))) return rc;
+        if ((rc = arena_get(ctx, nm[s][3], sizeof(double2) * cap * (size_t)G * xs, &La[s]))) return rc;
+        if ((rc = arena_get(ctx, nm[s][4], sizeof(double2) * cap * (size_t)G * xs, &Xi[s]))) return rc;
+        if ((rc = arena_get(ctx, nm[s][5], sizeof(double2) * cap * xs, &Lh1[s]))) return rc;
+        if ((rc = arena_get(ctx, nm[s][6], sizeof(double2) * cap, &e1[s]))) return rc;
+        if ((rc = arena_get(ctx, nm[s][7], sizeof(double2) * cap * xs, &Y[s]))) return rc;
+    }
+    if ((rc = arena_get(ctx, "K_aa", sizeof(double2) * cap * std::max(1, X[0] * X[0]), &Kaa))) return rc;
+    if ((rc = arena_get(ctx, "K_bb", sizeof(double2) * cap * std::max(1, X[1] * X[1]), &Kbb))) return rc;
+    if ((rc = arena_get(ctx, "K_ab", sizeof(double2) * cap * std::max(1, X[0] * X[1]), &Kab))) return rc;
+    if ((rc = arena_get(ctx, "scal", sizeof(double2) * cap * 8, &scal))) return rc;
+    const TimerHook& th = ctx->hook;
+    for (int w0 = 0; w0 < n_w; w0 += cap) {
+        const int nw = std::min(cap, n_w - w0);
+        if ((rc = run_overlap_part(ctx, in, w0, nw, cap, c, true, fp32, st))) return rc;
+        SpinTables T[2] = {tables(ctx->sp[0], cap), tables(ctx->sp[1], cap)};
+        for (int s = 0; s < 2; ++s) {
+            const int NC = T[s].N + T[s].np;
+            th.begin("k_gemm_F", st);
+            launch_gemm_zd(nw * T[s].N, G * NC, M, c.Gr[s], M, ctx->sp[s].d_Lh, M, (double2*)F[s],
+                           (long long)G * NC, st);
+            th.end(st);
+            th.begin("k_fepi", st);
+            launch_fepi(T[s], nw, M, G, (double2*)F[s], (long long)G * NC, c.Gr[s], (double2*)v0[s],
+                        (double2*)xx[s], (double2*)La[s], (double2*)Xi[s], st);
+            th.end(st);
+            th.begin("k_onebody", st);
+            launch_onebody(T[s], nw, M, ctx->d_h1 + (size_t)s * M * M, c.Gr[s], (double2*)e1[s],
+                           (double2*)Lh1[s], st);
+            th.end(st);
+            CKLAUNCH();
+        }
+        th.begin("k_gamma_reduce", st);
+        for (int s = 0; s < 2; ++s)
+            launch_gamma_reduce(nw, X[s], G, s, (double2*)v0[0], (double2*)v0[1], (double2*)xx[s],
+                                (double2*)La[s], (double2*)Xi[s], (double2*)Lh1[s], Y[s], fp32,
+                                (double2*)scal, st);
+        th.end(st);
+        th.begin("k_gram", st);
+        launch_gram(nw, X[0], X[0], G, (double2*)La[0], (double2*)La[0], Kaa, fp32, st);
+        launch_gram(nw, X[1], X[1], G, (double2*)La[1], (double2*)La[1], Kbb, fp32, st);
+        launch_gram(nw, X[0], X[1], G, (double2*)La[0], (double2*)La[1], Kab, fp32, st);
+        th.end(st);
+        CKLAUNCH();
+        int slot = nR;
+        void* Kss[2] = {Kaa, Kbb};
+        th.begin("k_string_energy", st);
+        for (int s = 0; s < 2; ++s) {
+            launch_string_energy(T[s], nw, c.r[s], c.wts[s], c.B[s], Kss[s], Y[s], fp32, c.part,
+                                 c.nslot, slot, st);
+            slot += string_energy_slots(T[s]);
+        }
+        th.end(st);
+        CKLAUNCH();
+        th.begin("k_pair_cross", st);
+        launch_pair_cross(T[0], T[1], pair_tables(ctx->pairs), nw, c.r[0], c.r[1], c.B[0], c.B[1],
+                          Kab, fp32, c.part, c.nslot, slot, st);
+        th.end(st);
+        CKLAUNCH();
+        th.begin("k_final", st);
+        launch_final(nw, c.part, c.nslot, c.nR, ctx->e0, (double2*)e1[0], (double2*)e1[1],
+                     (double2*)scal, c.O0[0], c.O0[1], o_e.dev + w0, o_ov.dev ? o_ov.dev + w0 : nullptr, st);
+        th.end(st);
+        CKLAUNCH();
+    }
+    return finish(ctx, st, {&o_e, &o_ov}, in.host_any);
+}
+
+int msd_info(const msd_ctx* ctx, int key, long long* value)
+{
+    if (!ctx || !value) return MSD_ERR_ARG;
+    switch (key) {
+    case MSD_INFO_N_DET: *value = ctx->pairs.n_det; break;
+    case MSD_INFO_N_CHOL: *value = ctx->n_chol; break;
+    case MSD_INFO_N_STRINGS_A: *value = ctx->sp[0].n_str; break;
+    case MSD_INFO_N_STRINGS_B: *value = ctx->sp[1].n_str; break;
+    case MSD_INFO_N_HOLES_A: *value = ctx->sp[0].nh; break;
+    case MSD_INFO_N_PARTS_A: *value = ctx->sp[0].np; break;
+    case MSD_INFO_N_HOLES_B: *value = ctx->sp[1].nh; break;
+    case MSD_INFO_N_PARTS_B: *value = ctx->sp[1].np; break;
+    case MSD_INFO_WORKSPACE_BYTES: {
+        long long b = 0;
+        for (auto& kv : ctx->arena) b += (long long)kv.second.bytes;
+        *value = b;
+        break;
+    }
+    case MSD_INFO_WALKER_CHUNK: *value = ctx->chunk; break;
+    default: return MSD_ERR_ARG;
+    }
+    return MSD_OK;
+}
+
+int msd_set_timing(msd_ctx* ctx, int enable)
+{
+    if (!ctx) return MSD_ERR_ARG;
+    ctx->timing = enable != 0;
+    ctx->hook.begin_fn = ctx->timing ? timer_begin : nullptr;
+    ctx->hook.end_fn = ctx->timing ? timer_end : nullptr;
+    return MSD_OK;
+}
+
+int msd_reset_stats(msd_ctx* ctx)
+{
+    if (!ctx) return MSD_ERR_ARG;
+    collect_timing(ctx);
+    std::fill(ctx->klaunch.begin(), ctx->klaunch.end(), 0);
+    std::fill(ctx->kms.begin(), ctx->kms.end(), 0.0);
+    return MSD_OK;
+}
+
+int msd_kernel_count(const msd_ctx* ctx) { return ctx ? (int)ctx->knames.size() : 0; }
+
+int msd_kernel_stat(msd_ctx* ctx, int index, const char** name, long long* launches, double* total_ms)
+{
+    if (!ctx || index < 0 || index >= (int)ctx->knames.size()) return MSD_ERR_ARG;
+    collect_timing(ctx);
+    if (name) *name = ctx->knames[index].c_str();
+    if (launches) *launches = ctx->klaunch[index];
+    if (total_ms) *total_ms = ctx->kms[index];
+    return MSD_OK;
+}
+
+int msd_set_workspace_limit(msd_ctx* ctx, size_t bytes)
+{
+    if (!ctx) return MSD_ERR_ARG;
+    ctx->ws_limit = bytes ? bytes : ((size_t)4 << 30);
+    return MSD_OK;
+}
+
+int msd_set_sync(msd_ctx* ctx, int sync)
+{
+    if (!ctx) return MSD_ERR_ARG;
+    ctx->sync = sync != 0;
+    return MSD_OK;
+}
+
+}  // extern "C"

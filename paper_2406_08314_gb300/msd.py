@@ -1,0 +1,220 @@
+"""Python binding of libmsd (include/msd.h): argument marshalling only.
+
+Every step of the hot path runs in the CUDA library. Importing this module
+loads libmsd.so; it raises if the library has not been built (there is no
+fallback of any kind). Walkers and outputs are torch tensors (complex128) on
+the context's CUDA device, or host arrays (numpy or CPU torch tensors),
+which the library stages through device memory.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MSD_FP64 = 0
+MSD_MIXED = 1
+_ERRORS = {-1: "MSD_ERR_ARG", -2: "MSD_ERR_SHAPE", -3: "MSD_ERR_CUDA", -4: "MSD_ERR_TIMEOUT",
+           -5: "MSD_ERR_REF_SINGULAR", -6: "MSD_ERR_STATE", -7: "MSD_ERR_NOMEM"}
+EXPORTS = ["msd_create", "msd_destroy", "msd_last_error", "msd_set_hamiltonian", "msd_set_trial",
+           "msd_set_precision", "msd_overlap", "msd_det_ratios", "msd_force_bias",
+           "msd_local_energy", "msd_info", "msd_set_timing", "msd_reset_stats",
+           "msd_kernel_count", "msd_kernel_stat", "msd_set_workspace_limit", "msd_set_sync"]
+INFO = {"n_det": 1, "n_chol": 2, "n_strings_a": 3, "n_strings_b": 4, "n_holes_a": 5,
+        "n_parts_a": 6, "n_holes_b": 7, "n_parts_b": 8, "workspace_bytes": 9, "walker_chunk": 10}
+
+
+class MSDError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRORS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = _ERRORS.get(code, str(code))
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmsd.so not found at {path}; build it with "
+                           "`python -m paper_2406_08314_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(path)
+    vp, ci, dp = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
+    lib.msd_create.argtypes = [ctypes.POINTER(vp), ci, ci, ci, ci, ci]
+    lib.msd_destroy.argtypes = [vp]
+    lib.msd_destroy.restype = None
+    lib.msd_last_error.argtypes = [vp]
+    lib.msd_last_error.restype = ctypes.c_char_p
+    lib.msd_set_hamiltonian.argtypes = [vp, vp, ctypes.c_double, ci, vp]
+    lib.msd_set_trial.argtypes = [vp, ci, vp, vp, vp]
+    lib.msd_set_precision.argtypes = [vp, ci]
+    for f in ("msd_overlap", "msd_det_ratios", "msd_force_bias", "msd_local_energy"):
+        getattr(lib, f).argtypes = [vp, ci, vp, vp, vp, vp, vp]
+    lib.msd_info.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_longlong)]
+    lib.msd_set_timing.argtypes = [vp, ci]
+    lib.msd_reset_stats.argtypes = [vp]
+    lib.msd_kernel_count.argtypes = [vp]
+    lib.msd_kernel_stat.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_char_p),
+                                    ctypes.POINTER(ctypes.c_longlong), dp]
+    lib.msd_set_workspace_limit.argtypes = [vp, ctypes.c_size_t]
+    lib.msd_set_sync.argtypes = [vp, ci]
+    for f in EXPORTS:
+        if f not in ("msd_destroy", "msd_last_error"):
+            getattr(lib, f).restype = ci
+    return lib
+
+
+_lib = load_library()
+
+
+def lib() -> ctypes.CDLL:
+    return _lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _is_cuda(x) -> bool:
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
+def _ptr(x):
+    """Data pointer of a contiguous complex128 torch tensor or numpy array."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags.c_contiguous and x.dtype == np.complex128
+        return ctypes.c_void_p(x.ctypes.data)
+    torch = _torch()
+    assert x.is_contiguous() and x.dtype == torch.complex128, "expected contiguous complex128"
+    return ctypes.c_void_p(x.data_ptr())
+
+
+class Context:
+    """One trial + Hamiltonian on one GPU. Mirrors the C-ABI entry points."""
+
+    def __init__(self, system, precision: str | int = "fp64", device: int = 0):
+        prec = {"fp64": MSD_FP64, "mixed": MSD_MIXED}.get(precision, precision)
+        h = ctypes.c_void_p()
+        rc = _lib.msd_create(ctypes.byref(h), system.M, system.n_alpha, system.n_beta, int(prec),
+                             int(device))
+        if rc:
+            raise MSDError(rc, _lib.msd_last_error(None).decode())
+        self._h = h
+        self.device = device
+        self.M, self.n_alpha, self.n_beta = system.M, system.n_alpha, system.n_beta
+        self.n_chol = system.n_chol
+        self.n_det = system.n_det
+        h1 = np.ascontiguousarray(system.h1, np.float64)
+        L = np.ascontiguousarray(system.L, np.float64)
+        self._check(_lib.msd_set_hamiltonian(h, h1.ctypes.data_as(ctypes.c_void_p), float(system.e0),
+                                             L.shape[0], L.ctypes.data_as(ctypes.c_void_p)))
+        self.set_trial(system.coeff, system.occ_a, system.occ_b)
+
+    def _check(self, rc):
+        if rc:
+            raise MSDError(rc, _lib.msd_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.msd_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def set_trial(self, coeff, occ_a, occ_b):
+        c = np.ascontiguousarray(coeff, np.float64)
+        a = np.ascontiguousarray(occ_a, np.int32)
+        b = np.ascontiguousarray(occ_b, np.int32)
+        self._check(_lib.msd_set_trial(self._h, c.shape[0], c.ctypes.data_as(ctypes.c_void_p),
+                                       a.ctypes.data_as(ctypes.c_void_p),
+                                       b.ctypes.data_as(ctypes.c_void_p)))
+        self.n_det = c.shape[0]
+
+    def set_precision(self, precision):
+        prec = {"fp64": MSD_FP64, "mixed": MSD_MIXED}.get(precision, precision)
+        self._check(_lib.msd_set_precision(self._h, int(prec)))
+
+    def info(self, key: str) -> int:
+        v = ctypes.c_longlong()
+        self._check(_lib.msd_info(self._h, INFO[key], ctypes.byref(v)))
+        return v.value
+
+    # -------------------------------------------------------------- outputs
+    def _alloc(self, like, shape):
+        if _is_cuda(like):
+            torch = _torch()
+            return torch.empty(shape, dtype=torch.complex128, device=like.device)
+        return np.empty(shape, np.complex128)
+
+    def _stream(self, like, stream):
+        if stream is not None:
+            return ctypes.c_void_p(int(stream))
+        if _is_cuda(like):
+            return ctypes.c_void_p(_torch().cuda.current_stream(like.device).cuda_stream)
+        return ctypes.c_void_p(0)
+
+    def _walkers(self, phi_a, phi_b):
+        n_w = phi_a.shape[0]
+        assert tuple(phi_a.shape) == (n_w, self.M, self.n_alpha), phi_a.shape
+        assert tuple(phi_b.shape) == (n_w, self.M, self.n_beta), phi_b.shape
+        return n_w
+
+    def overlap(self, phi_a, phi_b, stream=None, ratio_sum=False):
+        n_w = self._walkers(phi_a, phi_b)
+        ov = self._alloc(phi_a, (n_w,))
+        rs = self._alloc(phi_a, (n_w,)) if ratio_sum else None
+        self._check(_lib.msd_overlap(self._h, n_w, _ptr(phi_a), _ptr(phi_b), _ptr(ov), _ptr(rs),
+                                     self._stream(phi_a, stream)))
+        return (ov, rs) if ratio_sum else ov
+
+    def det_ratios(self, phi_a, phi_b, stream=None, ref_ovlp=False):
+        n_w = self._walkers(phi_a, phi_b)
+        r = self._alloc(phi_a, (n_w, self.n_det))
+        o = self._alloc(phi_a, (n_w,)) if ref_ovlp else None
+        self._check(_lib.msd_det_ratios(self._h, n_w, _ptr(phi_a), _ptr(phi_b), _ptr(r), _ptr(o),
+                                        self._stream(phi_a, stream)))
+        return (r, o) if ref_ovlp else r
+
+    def force_bias(self, phi_a, phi_b, stream=None, ovlp=False, out=None):
+        n_w = self._walkers(phi_a, phi_b)
+        v = out if out is not None else self._alloc(phi_a, (n_w, self.n_chol))
+        o = self._alloc(phi_a, (n_w,)) if ovlp else None
+        self._check(_lib.msd_force_bias(self._h, n_w, _ptr(phi_a), _ptr(phi_b), _ptr(v), _ptr(o),
+                                        self._stream(phi_a, stream)))
+        return (v, o) if ovlp else v
+
+    def local_energy(self, phi_a, phi_b, stream=None, ovlp=False, out=None):
+        n_w = self._walkers(phi_a, phi_b)
+        e = out if out is not None else self._alloc(phi_a, (n_w,))
+        o = self._alloc(phi_a, (n_w,)) if ovlp else None
+        self._check(_lib.msd_local_energy(self._h, n_w, _ptr(phi_a), _ptr(phi_b), _ptr(e), _ptr(o),
+                                          self._stream(phi_a, stream)))
+        return (e, o) if ovlp else e
+
+    # --------------------------------------------------------------- timing
+    def set_timing(self, enable=True):
+        self._check(_lib.msd_set_timing(self._h, int(bool(enable))))
+
+    def reset_stats(self):
+        self._check(_lib.msd_reset_stats(self._h))
+
+    def kernel_stats(self) -> dict:
+        out = {}
+        for i in range(_lib.msd_kernel_count(self._h)):
+            name = ctypes.c_char_p()
+            n = ctypes.c_longlong()
+            ms = ctypes.c_double()
+            self._check(_lib.msd_kernel_stat(self._h, i, ctypes.byref(name), ctypes.byref(n),
+                                             ctypes.byref(ms)))
+            out[name.value.decode()] = (n.value, ms.value)
+        return out
+
+    def set_workspace_limit(self, nbytes: int):
+        self._check(_lib.msd_set_workspace_limit(self._h, int(nbytes)))
+
+    def set_sync(self, sync: bool):
+        self._check(_lib.msd_set_sync(self._h, int(bool(sync))))

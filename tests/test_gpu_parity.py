@@ -1,0 +1,231 @@
+"""CUDA path (through the C-ABI) against the CPU oracle, element by element on
+the same seeded inputs. FP64 mode must match within 1e-10 relative to the
+cancellation scale of each quantity:
+  |dO_T|  <= 1e-10 * sum_I |c_I O_I|
+  |dE_L|  <= 1e-10 * sum_I |c_I O_I E_I| / |O_T|
+  |dv_g|  <= 1e-10 * (sum_I |c_I O_I| / |O_T|) * max_g |v_g|
+  |dr_I|  <= 1e-10 * max(1, |r_I|)
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_08314_gb300 import synth
+from tiny import tiny_system, tiny_walkers
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def msd():
+    from paper_2406_08314_gb300 import build
+    build.build()
+    from paper_2406_08314_gb300 import msd as m
+    return m
+
+
+def _cuda(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _np(t):
+    return t.cpu().numpy() if hasattr(t, "cpu") else np.asarray(t)
+
+
+def _ref(sys_, pa, pb):
+    out = oracle.msd(sys_, pa, pb, energy=True, vbias=True, per_det=True)
+    cO = sys_.coeff[None, :] * out["det_ovlp"]
+    out["scale_o"] = np.sum(np.abs(cO), axis=1)
+    out["scale_e"] = np.sum(np.abs(cO * out["det_e"]), axis=1) / np.abs(out["ovlp"])
+    out["canc"] = out["scale_o"] / np.abs(out["ovlp"])
+    return out
+
+
+def _check_all(m, sys_, pa, pb, ref, precision="fp64", tol=TOL, tol_e=None):
+    ctx = m.Context(sys_, precision)
+    da, db = _cuda(pa), _cuda(pb)
+    ov, rs = ctx.overlap(da, db, ratio_sum=True)
+    ov = _np(ov)
+    assert np.all(np.abs(ov - ref["ovlp"]) <= tol * ref["scale_o"]), \
+        np.max(np.abs(ov - ref["ovlp"]) / ref["scale_o"])
+    r, o0 = ctx.det_ratios(da, db, ref_ovlp=True)
+    r = _np(r)
+    want_r = ref["det_ovlp"] / ref["det_ovlp"][:, :1]
+    assert np.all(np.abs(r - want_r) <= tol * np.maximum(1, np.abs(want_r))), \
+        np.max(np.abs(r - want_r) / np.maximum(1, np.abs(want_r)))
+    assert np.allclose(_np(o0), ref["det_ovlp"][:, 0], rtol=tol, atol=0)
+    v = _np(ctx.force_bias(da, db))
+    vt = tol * ref["canc"] * np.max(np.abs(ref["vbias"]), axis=1)
+    assert np.all(np.abs(v - ref["vbias"]) <= vt[:, None]), \
+        np.max(np.abs(v - ref["vbias"]) / vt[:, None] * tol)
+    e, o2 = ctx.local_energy(da, db, ovlp=True)
+    e = _np(e)
+    te = (tol_e or tol) * ref["scale_e"]
+    assert np.all(np.abs(e - ref["e_loc"]) <= te), np.max(np.abs(e - ref["e_loc"]) / ref["scale_e"])
+    assert np.all(np.abs(_np(o2) - ref["ovlp"]) <= tol * ref["scale_o"])
+    ctx.close()
+    return dict(e=e, v=v, ov=ov)
+
+
+def test_small_workload_fp64(msd):
+    s, w = synth.config_system("small", seed=0)
+    ref = _ref(s, w.phi_a, w.phi_b)
+    _check_all(msd, s, w.phi_a, w.phi_b, ref)
+
+
+def _relabel(sys_, pa, pb, seed):
+    """Permute orbital labels so the reference is not the first N orbitals."""
+    perm = np.random.default_rng(seed).permutation(sys_.M)
+    inv = np.argsort(perm)
+    sys_.h1 = sys_.h1[:, perm][:, :, perm]
+    sys_.L = np.ascontiguousarray(sys_.L[:, perm][:, :, perm])
+    sys_.occ_a = np.sort(inv[sys_.occ_a], axis=1).astype(np.int32)
+    sys_.occ_b = np.sort(inv[sys_.occ_b], axis=1).astype(np.int32)
+    return sys_, np.ascontiguousarray(pa[:, perm]), np.ascontiguousarray(pb[:, perm])
+
+
+@pytest.mark.parametrize("M,na,nb,n_det,max_level,seed", [
+    (12, 5, 4, 150, 4, 0),
+    (13, 7, 6, 300, 12, 1),     # levels up to 6 per spin
+    (9, 1, 3, 40, None, 2),     # a single alpha electron
+])
+def test_tiny_systems_any_reference(msd, M, na, nb, n_det, max_level, seed):
+    s = tiny_system(seed, M, na, nb, n_chol=7, n_det=n_det, max_level=max_level)
+    pa, pb = tiny_walkers(seed, M, na, nb, n_w=3, noise=0.6)
+    s, pa, pb = _relabel(s, pa, pb, seed)
+    ref = _ref(s, pa, pb)
+    _check_all(msd, s, pa, pb, ref)
+
+
+def test_cu2o2_shaped_fp64(msd):
+    s, w = synth.config_system("cu2o2", seed=0, n_w=2)
+    ref = _ref(s, w.phi_a, w.phi_b)
+    _check_all(msd, s, w.phi_a, w.phi_b, ref)
+
+
+@pytest.fixture(scope="module")
+def fe2s2():
+    return synth.config_system("fe2s2", seed=0, n_w=640)
+
+
+def _subtrial(s, idx):
+    import copy
+    t = copy.copy(s)
+    t.coeff = np.ascontiguousarray(s.coeff[idx])
+    t.occ_a = np.ascontiguousarray(s.occ_a[idx])
+    t.occ_b = np.ascontiguousarray(s.occ_b[idx])
+    return t
+
+
+def test_fe2s2_shaped_subset_fp64(msd, fe2s2):
+    """Full Hamiltonian, orbital and Cholesky sizes; 300 determinants drawn
+    across all levels; 2 walkers."""
+    s, w = fe2s2
+    idx = np.concatenate([[0], np.sort(np.random.default_rng(5).choice(
+        np.arange(1, s.n_det), 299, replace=False))])
+    t = _subtrial(s, idx)
+    pa, pb = w.phi_a[:2], w.phi_b[:2]
+    ref = _ref(t, pa, pb)
+    _check_all(msd, t, pa, pb, ref)
+
+
+def test_fe2s2_full_size_sampled_ratios(msd, fe2s2):
+    """Full size, bench launch configuration: sampled per-determinant ratios
+    against the oracle's full N x N determinants."""
+    s, w = fe2s2
+    ctx = msd.Context(s, "fp64")
+    da, db = _cuda(w.phi_a), _cuda(w.phi_b)
+    r = ctx.det_ratios(da, db)
+    rng = np.random.default_rng(3)
+    for wk in rng.choice(w.n_w, 3, replace=False):
+        o0, _ = oracle.det_terms(s.M, s.occ_a[0], s.occ_b[0], s.h1, s.e0, s.L[:1],
+                                 w.phi_a[wk], w.phi_b[wk])
+        for I in rng.choice(s.n_det, 40, replace=False):
+            oi, _ = oracle.det_terms(s.M, s.occ_a[I], s.occ_b[I], s.h1, s.e0, s.L[:1],
+                                     w.phi_a[wk], w.phi_b[wk])
+            got = complex(r[wk, I].item())
+            assert abs(got - oi / o0) <= TOL * max(1, abs(oi / o0))
+    ctx.close()
+
+
+def test_fe2s2_full_size_additivity(msd, fe2s2):
+    """Full size: the numerators sum_I c_I r_I (E_I, v_I) are additive over a
+    split of the determinant list, so E_L and vbias of the full trial follow
+    from two half trials (each keeps D0 first; the second with c_0 = 0)."""
+    s, w = fe2s2
+    da, db = _cuda(w.phi_a), _cuda(w.phi_b)
+    rng = np.random.default_rng(9)
+    rest = rng.permutation(np.arange(1, s.n_det))
+    A = np.concatenate([[0], np.sort(rest[: s.n_det // 2])])
+    B = np.concatenate([[0], np.sort(rest[s.n_det // 2:])])
+    tB = _subtrial(s, B)
+    tB.coeff = tB.coeff.copy()
+    tB.coeff[0] = 0.0
+    res = {}
+    for name, t in (("full", s), ("A", _subtrial(s, A)), ("B", tB)):
+        ctx = msd.Context(t, "fp64")
+        _, R = ctx.overlap(da, db, ratio_sum=True)
+        e = ctx.local_energy(da, db)
+        v = ctx.force_bias(da, db)
+        res[name] = (_np(R), _np(e), _np(v))
+        ctx.close()
+    RA, eA, vA = res["A"]
+    RB, eB, vB = res["B"]
+    R, e, v = res["full"]
+    assert np.allclose(RA + RB, R, rtol=1e-11, atol=0)
+    e_comb = (eA * RA + eB * RB) / R
+    canc = (np.abs(RA) + np.abs(RB)) / np.abs(R)
+    assert np.all(np.abs(e_comb - e) <= 1e-10 * canc * (np.abs(eA) + np.abs(eB)))
+    v_comb = (vA * RA[:, None] + vB * RB[:, None]) / R[:, None]
+    assert np.all(np.abs(v_comb - v) <= 1e-10 * canc[:, None] * np.max(np.abs(v), axis=1, keepdims=True))
+
+
+# ------------------------------------------------------------------ edges
+def test_edge_cases(msd):
+    s, w = synth.config_system("small", seed=1)
+    ctx = msd.Context(s, "fp64")
+    import torch
+    empty = torch.empty((0, s.M, s.n_alpha), dtype=torch.complex128, device="cuda")
+    empty_b = torch.empty((0, s.M, s.n_beta), dtype=torch.complex128, device="cuda")
+    assert ctx.local_energy(empty, empty_b).shape == (0,)
+    # singular reference block: walker orthogonal to the reference orbitals
+    pa = w.phi_a[:2].copy()
+    pa[1, : s.n_alpha, :] = 0.0
+    with pytest.raises(msd.MSDError) as ei:
+        ctx.local_energy(_cuda(pa), _cuda(w.phi_b[:2]))
+    assert ei.value.name == "MSD_ERR_REF_SINGULAR"
+    # unsorted occupations
+    bad = s.occ_a.copy()
+    bad[3] = bad[3][::-1]
+    with pytest.raises(msd.MSDError) as ei:
+        ctx.set_trial(s.coeff, bad, s.occ_b)
+    assert ei.value.name == "MSD_ERR_ARG"
+    ctx.close()
+
+
+def test_single_determinant_and_host_buffers(msd):
+    s, w = synth.config_system("small", seed=2)
+    t = _subtrial(s, np.array([0]))
+    ref = _ref(t, w.phi_a, w.phi_b)
+    ctx = msd.Context(t, "fp64")
+    e = ctx.local_energy(w.phi_a, w.phi_b)          # numpy in, numpy out (host path)
+    assert isinstance(e, np.ndarray)
+    assert np.all(np.abs(e - ref["e_loc"]) <= TOL * ref["scale_e"])
+    v = ctx.force_bias(w.phi_a, w.phi_b)
+    assert np.allclose(v, ref["vbias"], rtol=1e-10, atol=1e-12)
+    ctx.close()
+
+
+def test_walker_chunking_matches(msd):
+    s, w = synth.config_system("cu2o2", seed=0, n_w=24)
+    da, db = _cuda(w.phi_a), _cuda(w.phi_b)
+    ctx = msd.Context(s, "fp64")
+    e1, v1 = _np(ctx.local_energy(da, db)), _np(ctx.force_bias(da, db))
+    ctx.set_workspace_limit(64 << 20)               # forces several walker chunks
+    e2, v2 = _np(ctx.local_energy(da, db)), _np(ctx.force_bias(da, db))
+    assert ctx.info("walker_chunk") < 24
+    assert np.allclose(e1, e2, rtol=1e-13, atol=0) and np.allclose(v1, v2, rtol=1e-13, atol=1e-15)
+    ctx.close()
