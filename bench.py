@@ -1,0 +1,476 @@
+#!/usr/bin/env python3
+"""Throughput of the multi-Slater-determinant AFQMC hot path on GB300.
+
+Metric: walker x determinant overlap + energy evaluations per second on the
+iron-sulfur-dimer-shaped workload (M = 160 orbitals, 30 + 30 electrons,
+30e/20o active space, N_det = 120000, N_chol = 800, 640 walkers), mixed
+precision, with the plain FP64 GPU path and its error measured beside it.
+
+One step = the whole hot path over the 640 walkers: force bias and local
+energy, each with the trial overlap (reference inverse, excitation-string
+minors, cofactor Green's function, Cholesky contractions, per-determinant
+energy, reductions). Inputs are resident in device memory; L2 is flushed
+between timed steps. With --gpus N (one process per GPU under torchrun)
+every rank evaluates its own 640 walkers (weak scaling, no data exchange).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("walker·det overlap+energy evals/s at N_det=1.2e5; mixed vs FP64 at stated error")
+UNIT = "walker*det/s"
+# GB300: 152 SMs at up to 2070 MHz; 2 FP64 and 128 FP32 FMA per SM per clock.
+FP64_ALU_GFLOPS = 152 * 2 * 2 * 2.070
+FP32_ALU_GFLOPS = 152 * 128 * 2 * 2.070
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="fe2s2")
+    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--n-w", type=int, default=None)
+    p.add_argument("--fp64-steps", type=int, default=2)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(world):
+    if world > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group("gloo")
+
+
+def aggregate(ms_total: float, units: float):
+    """Max of the timed device milliseconds and sum of the units over ranks
+    (gloo on host tensors: timing bookkeeping, not part of the data path)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return ms_total, units
+    t = torch.tensor([ms_total], dtype=torch.float64)
+    u = torch.tensor([units], dtype=torch.float64)
+    dist.barrier()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed
+    region (read-only queries)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            import torch
+            ident = str(self.dev)
+            uuid = getattr(torch.cuda.get_device_properties(self.dev), "uuid", None)
+            if uuid is not None:
+                ident = "GPU-" + str(uuid)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", ident], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------- work accounting
+def string_levels(occ, n_det):
+    """Distinct excitation strings of one spin (relative to determinant 0)
+    and their levels, for work accounting."""
+    import numpy as np
+    ref = set(occ[0].tolist())
+    seen = {}
+    for I in range(n_det):
+        row = occ[I].tolist()
+        holes = tuple(sorted(ref - set(row)))
+        parts = tuple(sorted(set(row) - ref))
+        seen.setdefault((holes, parts), len(holes))
+    lv = np.bincount(np.array(list(seen.values())), minlength=8)
+    hole_orbs = set()
+    part_orbs = set()
+    for (h, p) in seen:
+        hole_orbs.update(h)
+        part_orbs.update(p)
+    return lv, len(hole_orbs), len(part_orbs)
+
+
+def algorithmic_work(s, n_w):
+    """Algorithmic flops per call of each kernel group (one step = one
+    force-bias call + one local-energy call). Complex multiply-add = 8 flops,
+    complex x real = 4 flops."""
+    import numpy as np
+    M, G = s.M, s.n_chol
+    spins = []
+    for occ, N in ((s.occ_a, s.n_alpha), (s.occ_b, s.n_beta)):
+        lv, nh, np_ = string_levels(occ, s.n_det)
+        spins.append(dict(N=N, lv=lv, nh=nh, np=np_, X=nh * np_, NC=N + np_))
+    k = np.arange(8)
+    pair_lv = {}
+    ref_a, ref_b = set(s.occ_a[0].tolist()), set(s.occ_b[0].tolist())
+    for I in range(s.n_det):
+        ka = len(ref_a - set(s.occ_a[I].tolist()))
+        kb = len(ref_b - set(s.occ_b[I].tolist()))
+        pair_lv[(ka, kb)] = pair_lv.get((ka, kb), 0) + 1
+    w = {}
+    # reference inverse: LU + inverse + Theta product + active block, both spins
+    w["k_ref"] = sum(8 * (4 / 3 * sp["N"] ** 3 + M * sp["N"] ** 2 + sp["X"] * sp["N"]) for sp in spins) * n_w
+    # string minors: LU (k^3/3) + inverse (k^3) complex MACs
+    w["k_strings"] = sum(float(np.sum(sp["lv"] * 8 * (4 / 3) * k ** 3)) for sp in spins) * n_w
+    w["k_gemm_F"] = sum(4.0 * sp["N"] * M * G * sp["NC"] for sp in spins) * n_w
+    w["k_fepi"] = sum(8.0 * (sp["N"] ** 2 + sp["N"] ** 2 * sp["np"] + sp["nh"] * sp["N"] * sp["np"]) * G
+                      for sp in spins) * n_w
+    w["k_gram"] = 8.0 * G * (spins[0]["X"] ** 2 + spins[1]["X"] ** 2 + spins[0]["X"] * spins[1]["X"]) * n_w
+    w["k_string_energy"] = sum(float(np.sum(sp["lv"] * (10 * k ** 4 + 16 * k ** 2))) for sp in spins) * n_w
+    w["k_pair_cross"] = sum(8.0 * n * (ka * ka * kb * kb + ka * ka) for (ka, kb), n in pair_lv.items()
+                            if ka and kb) * n_w
+    Kd = sum(sp["NC"] * M for sp in spins)
+    w["k_gemm_vbias"] = 4.0 * Kd * G * n_w
+    return w, spins
+
+
+# -------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    from paper_2406_08314_gb300 import build, synth
+    if rank == 0:
+        build.build()
+    barrier()
+    from paper_2406_08314_gb300 import msd
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    s, wk = synth.config_system(args.workload, seed=rank, n_w=args.n_w)
+    n_w, n_det = wk.n_w, s.n_det
+    units_per_step = n_w * n_det
+    da = torch.from_numpy(wk.phi_a).to(dev)
+    db = torch.from_numpy(wk.phi_b).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = msd.Context(s, args.precision, device=local)
+    ctx.set_sync(False)
+    vb = torch.empty((n_w, s.n_chol), dtype=torch.complex128, device=dev)
+    el = torch.empty((n_w,), dtype=torch.complex128, device=dev)
+    ov = torch.empty((n_w,), dtype=torch.complex128, device=dev)
+
+    def step():
+        ctx.force_bias(da, db, out=vb)
+        ctx.local_energy(da, db, out=el)
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    for _ in range(args.warmup):
+        step()
+    ctx.set_sync(True)
+    ctx.local_energy(da, db, out=el)       # surfaces any device-side error
+    ctx.set_sync(False)
+    torch.cuda.synchronize(dev)
+    ctx.set_timing(True)
+    ctx.reset_stats()
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = msd.launch_count()
+    barrier()
+    torch.cuda.synchronize(dev)
+    ms_total = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        ms_total += e0.elapsed_time(e1)
+    torch.cuda.synchronize(dev)
+    launches = msd.launch_count() - launches0
+    clocks = sampler.stop()
+    kstats = ctx.kernel_stats()
+    ctx.set_timing(False)
+    ms_max, units = aggregate(ms_total, float(units_per_step * args.steps))
+    ms_per_step = ms_max / args.steps
+    value = units / (ms_max / 1e3)
+
+    # plain FP64 GPU path beside it, and the error of this mode against it
+    fp64 = None
+    if args.precision == "mixed" and args.fp64_steps > 0:
+        ctx.set_sync(True)
+        ctx.force_bias(da, db, out=vb)
+        e_m, o_m = ctx.local_energy(da, db, ovlp=True)
+        v_m = vb.clone()
+        ctx.set_precision("fp64")
+        ctx.set_sync(False)
+        step()                      # warm-up of the FP64 path
+        torch.cuda.synchronize(dev)
+        t64 = 0.0
+        for _ in range(args.fp64_steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            t64 += e0.elapsed_time(e1)
+        ctx.set_sync(True)
+        ctx.force_bias(da, db, out=vb)
+        e_d, o_d = ctx.local_energy(da, db, ovlp=True)
+        de = (e_m - e_d).abs().cpu().numpy()
+        dv = (v_m - vb).abs().max(dim=1).values.cpu().numpy()
+        vscale = vb.abs().max(dim=1).values.cpu().numpy()
+        do = ((o_m - o_d).abs() / o_d.abs()).cpu().numpy()
+        t64_max, u64 = aggregate(t64, float(units_per_step * args.fp64_steps))
+        fp64 = {"value": u64 / (t64_max / 1e3), "ms_per_step": t64_max / args.fp64_steps,
+                "steps": args.fp64_steps,
+                "error_of_mixed": {
+                    "e_loc_abs_max_Ha": float(de.max()), "e_loc_abs_median_Ha": float(np.median(de)),
+                    "vbias_rel_max": float(np.max(dv / vscale)),
+                    "ovlp_rel_max": float(do.max())}}
+        ctx.set_precision(args.precision)
+
+    # end to end through the C-ABI with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        ha = torch.from_numpy(wk.phi_a).pin_memory()
+        hb = torch.from_numpy(wk.phi_b).pin_memory()
+        ctx.set_sync(True)
+        for _ in range(1):
+            ctx.force_bias(ha, hb)
+            ctx.local_energy(ha, hb, ovlp=True)
+        barrier()
+        t0 = time.perf_counter()
+        n_e2e = max(1, min(args.steps, 5))
+        for _ in range(n_e2e):
+            v_h = ctx.force_bias(ha, hb)
+            e_h, o_h = ctx.local_energy(ha, hb, ovlp=True)
+        wall = (time.perf_counter() - t0) * 1e3
+        wall_max, u_e2e = aggregate(wall, float(units_per_step * n_e2e))
+        phi_bytes = ha.numel() * 16 + hb.numel() * 16
+        e2e = {"value": u_e2e / (wall_max / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": 2 * phi_bytes,
+               "d2h_bytes_per_step": int(v_h.nbytes + e_h.nbytes + o_h.nbytes)}
+
+    work, spins = algorithmic_work(s, n_w)
+    peaks, peak_src = load_peaks()
+    kernels = {}
+    for name, (n_launch, ms) in kstats.items():
+        steps = args.steps
+        entry = {"launches": n_launch, "ms_per_step": ms / steps,
+                 "share": ms / max(1e-9, sum(v[1] for v in kstats.values()))}
+        if name in work and ms > 0:
+            entry["gflops"] = work[name] * steps / (ms / 1e3) / 1e9
+        kernels[name] = entry
+    dom = max(kstats.items(), key=lambda kv: kv[1][1])[0] if kstats else None
+    roofline = None
+    if dom is not None:
+        d = kernels[dom]
+        fp64_kernels = args.precision == "fp64" or dom in ("k_gemm_F", "k_gemm_vbias", "k_ref",
+                                                           "k_strings")
+        peak = FP64_ALU_GFLOPS if fp64_kernels else FP32_ALU_GFLOPS
+        ach = d.get("gflops")
+        roofline = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak,
+                    "unit": "GFLOP/s", "frac": (ach / peak) if ach else None, "traffic": None,
+                    "peak_source": ("derived: 152 SMs x 2070 MHz x "
+                                    + ("2 FP64" if fp64_kernels else "128 FP32")
+                                    + " FMA/clk/SM")}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(s, wk, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 minors + f32 contractions" if args.precision == "mixed" else "f64",
+            "data": "synthetic (seeded; shapes of the paper's Fe2S2 system)",
+            "config": {"workload": f"{args.workload}: M={s.M}, {s.n_alpha}+{s.n_beta} e, "
+                                   f"N_det={n_det}, N_chol={s.n_chol}, {n_w} walkers/GPU",
+                       "precision": args.precision, "n_walkers": n_w, "n_det": n_det,
+                       "n_chol": s.n_chol, "M": s.M,
+                       "step": "force bias + local energy (each with overlap)",
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": f"walker replicas x{world}",
+                       "strings": [int(sp["lv"].sum()) for sp in spins]},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "fp64": fp64,
+            "kernels": kernels,
+            "peaks_source": peak_src,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+# -------------------------------------------------------- CPU baseline
+def cpu_baseline(s, wk, seconds):
+    """The oracle (naive per-determinant FP64, OpenMP over determinants) on a
+    bounded sample: walker 0 against random chunks of 32 determinants until
+    `seconds` of work; value in walker*det/s."""
+    import copy
+
+    import numpy as np
+
+    import oracle
+    rng = np.random.default_rng(1234)
+    order = rng.permutation(s.n_det)
+    done = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds and done < s.n_det:
+        idx = np.sort(order[done: done + 32])
+        t = copy.copy(s)
+        t.coeff, t.occ_a, t.occ_b = s.coeff[idx], s.occ_a[idx], s.occ_b[idx]
+        oracle.msd(t, wk.phi_a[:1], wk.phi_b[:1], energy=True, vbias=True)
+        done += len(idx)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": done / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"1 walker x {done} random determinants (chunks of 32), {dt:.1f} s; "
+                      "overlap, force bias and energy per determinant"}
+
+
+# ---------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    """The oracle as it stands, on the host cores: each step evaluates walker 0
+    against a bounded random sample of the workload's determinants."""
+    if rank != 0:
+        return
+    import copy
+
+    import numpy as np
+
+    import oracle
+    from paper_2406_08314_gb300 import synth
+    oracle.build()
+    s, wk = synth.config_system(args.workload, seed=0, n_w=args.n_w or 4)
+    rng = np.random.default_rng(99)
+    per_step = 48
+
+    def step(i):
+        idx = np.sort(rng.choice(s.n_det, per_step, replace=False))
+        t = copy.copy(s)
+        t.coeff, t.occ_a, t.occ_b = s.coeff[idx], s.occ_a[idx], s.occ_b[idx]
+        oracle.msd(t, wk.phi_a[:1], wk.phi_b[:1], energy=True, vbias=True)
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        step(i)
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded; shapes of the paper's Fe2S2 system)",
+            "config": {"workload": f"{args.workload}: M={s.M}, {s.n_alpha}+{s.n_beta} e, "
+                                   f"N_det={s.n_det}, N_chol={s.n_chol}",
+                       "sample_per_step": f"1 walker x {per_step} random determinants"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"1 walker x {per_step} random determinants per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    dist_init(world)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+    barrier()
+
+
+if __name__ == "__main__":
+    main()

@@ -174,6 +174,10 @@ int msd_set_workspace_limit(msd_ctx* ctx, size_t bytes);
    reported by the next synchronising call. */
 int msd_set_sync(msd_ctx* ctx, int sync);
 
+/* Number of CUDA kernels the library has launched in this process (all
+   contexts), for launch accounting by benchmarks. */
+long long msd_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -46,6 +46,9 @@ __host__ __device__ __forceinline__ float2 ffma(float2 b, float2 c, float2 a) {
     return make_float2(fmaf(b.x, c.x, fmaf(-b.y, c.y, a.x)), fmaf(b.x, c.y, fmaf(b.y, c.x, a.y)));
 }
 
+// Count of kernel launches made by the library (for launch accounting).
+void msd_note_launch();
+
 // ------------------------------------------------------------ device state
 // Error word bits set by kernels (read back by the host after a call).
 #define MSD_DEV_ERR_SINGULAR 1u

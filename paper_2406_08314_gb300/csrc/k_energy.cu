@@ -78,7 +78,7 @@ void launch_gemm_zd(int Mr, int Nc, int K, const double2* A, long long lda, cons
                     long long ldb, double2* C, long long ldc, cudaStream_t st)
 {
     dim3 grid((Nc + 63) / 64, (Mr + 63) / 64);
-    k_gemm_zd<<<grid, 256, 0, st>>>(Mr, Nc, K, A, lda, B, ldb, C, ldc);
+    k_gemm_zd<<<grid, 256, 0, st>>>(Mr, Nc, K, A, lda, B, ldb, C, ldc); msd_note_launch();
 }
 
 // ------------------------------------------------------------------------
@@ -142,7 +142,7 @@ void launch_fepi(const SpinTables& tb, int nw, int M, int n_chol, const double2*
     dim3 grid(n_chol, nw);
     const size_t smem = fepi_smem(tb);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_fepi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_fepi<<<grid, 128, smem, st>>>(tb, M, n_chol, F, ldf, Gr, v0, xx, Lact, Xic);
+    k_fepi<<<grid, 128, smem, st>>>(tb, M, n_chol, F, ldf, Gr, v0, xx, Lact, Xic); msd_note_launch();
 }
 
 // ------------------------------------------------------------------------
@@ -191,7 +191,7 @@ void launch_onebody(const SpinTables& tb, int nw, int M, const double* h1, const
 {
     size_t smem = sizeof(double2) * tb.nh * (tb.N + tb.np);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_onebody, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_onebody<<<nw, 128, smem, st>>>(tb, M, h1, Gr, e1, Lh);
+    k_onebody<<<nw, 128, smem, st>>>(tb, M, h1, Gr, e1, Lh); msd_note_launch();
 }
 
 // ------------------------------------------------------------------------
@@ -246,6 +246,7 @@ void launch_gamma_reduce(int nw, int X, int n_chol, int spin, const double2* v0a
     else
         k_gamma_reduce<double><<<nw, 128, 0, st>>>(X, n_chol, spin, v0a, v0b, xx, Lact, Xic, Lh,
                                                    (double*)Y, scal);
+    msd_note_launch();
 }
 
 // ------------------------------------------------------------------------
@@ -297,6 +298,7 @@ void launch_gram(int nw, int Xp, int Xq, int n_chol, const double2* P, const dou
     dim3 grid((Xq + 31) / 32, (Xp + 31) / 32, nw);
     if (fp32) k_gram<float><<<grid, 256, 0, st>>>(Xp, Xq, n_chol, P, Q, (float*)K);
     else k_gram<double><<<grid, 256, 0, st>>>(Xp, Xq, n_chol, P, Q, (double*)K);
+    msd_note_launch();
 }
 
 // ------------------------------------------------------------------------
@@ -408,10 +410,10 @@ static void launch_se_k(const SpinTables& tb, int nw, const double2* r, const do
     const size_t smem = string_energy_smem(tb, fp32);
     if (fp32) {
         cudaFuncSetAttribute(k_string_energy<KL, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_string_energy<KL, float><<<grid, 128, smem, st>>>(tb, r, wts, B, K, Y, part, nslot, slot);
+        k_string_energy<KL, float><<<grid, 128, smem, st>>>(tb, r, wts, B, K, Y, part, nslot, slot); msd_note_launch();
     } else {
         cudaFuncSetAttribute(k_string_energy<KL, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_string_energy<KL, double><<<grid, 128, smem, st>>>(tb, r, wts, B, K, Y, part, nslot, slot);
+        k_string_energy<KL, double><<<grid, 128, smem, st>>>(tb, r, wts, B, K, Y, part, nslot, slot); msd_note_launch();
     }
     slot += nb;
 }
@@ -525,10 +527,10 @@ static void launch_pc_k(const SpinTables& ta, const SpinTables& tb, const PairTa
     const size_t smem = (fp32 ? sizeof(float2) : sizeof(double2)) * (size_t)(ta.nh * ta.np) * (tb.nh * tb.np);
     if (fp32) {
         cudaFuncSetAttribute(k_pair_cross<KB, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_pair_cross<KB, float><<<grid, 128, smem, st>>>(ta, tb, pt, ka, lo, n, ra, rb, Ba, Bb, K, part, nslot, slot);
+        k_pair_cross<KB, float><<<grid, 128, smem, st>>>(ta, tb, pt, ka, lo, n, ra, rb, Ba, Bb, K, part, nslot, slot); msd_note_launch();
     } else {
         cudaFuncSetAttribute(k_pair_cross<KB, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_pair_cross<KB, double><<<grid, 128, smem, st>>>(ta, tb, pt, ka, lo, n, ra, rb, Ba, Bb, K, part, nslot, slot);
+        k_pair_cross<KB, double><<<grid, 128, smem, st>>>(ta, tb, pt, ka, lo, n, ra, rb, Ba, Bb, K, part, nslot, slot); msd_note_launch();
     }
     slot += nb;
 }
@@ -590,5 +592,5 @@ void launch_final(int nw, const double2* part, int nslot, int nR, double e0, con
                   double2* eloc, double2* ovlp, cudaStream_t st)
 {
     k_final<<<(nw + 127) / 128, 128, 0, st>>>(nw, part, nslot, nR, e0, e1a, e1b, scal, O0a, O0b,
-                                             eloc, ovlp);
+                                             eloc, ovlp); msd_note_launch();
 }

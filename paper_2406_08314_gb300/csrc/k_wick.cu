@@ -122,7 +122,7 @@ void launch_ref(const double2* phi, int nw, int M, int N, const SpinTables& T, d
     size_t smem = sizeof(double2) * 2 * N * N;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_ref, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_ref<<<nw, 256, smem, st>>>(phi, M, N, T.occ0, T.hole_pos, T.nh, T.part_orb, T.np, Gr, O0,
-                                 Gact, err);
+                                 Gact, err); msd_note_launch();
 }
 
 // ------------------------------------------------------------------------
@@ -229,6 +229,7 @@ static void launch_strings_k(const SpinTables& tb, int nw, const double2* Gact, 
     dim3 grid((ns + 127) / 128, nw);
     if (fp32) k_strings<K, float><<<grid, 128, 0, st>>>(tb, nw, Gact, r, B, want_b);
     else k_strings<K, double><<<grid, 128, 0, st>>>(tb, nw, Gact, r, B, want_b);
+    msd_note_launch();
 }
 
 // Reference string (level 0): ratio 1.
@@ -243,7 +244,7 @@ void launch_strings(const SpinTables& tb, int nw, const double2* Gact, double2* 
 {
     if (tb.bucket[1] > tb.bucket[0]) {
         th.begin("k_ref_string", st);
-        k_ref_string<<<(nw + 127) / 128, 128, 0, st>>>(nw, tb.n_str, r);
+        k_ref_string<<<(nw + 127) / 128, 128, 0, st>>>(nw, tb.n_str, r); msd_note_launch();
         th.end(st);
     }
     th.begin("k_strings", st);
@@ -294,7 +295,7 @@ void launch_weights(const SpinTables& tb, int nw, const double2* r_self, const d
                     int n_other, double2* wts, double2* part, int nslot, int slot0, cudaStream_t st)
 {
     dim3 grid(weights_blocks(tb), nw);
-    k_weights<<<grid, 256, 0, st>>>(tb, r_self, r_other, n_other, wts, part, nslot, slot0);
+    k_weights<<<grid, 256, 0, st>>>(tb, r_self, r_other, n_other, wts, part, nslot, slot0); msd_note_launch();
 }
 
 // ------------------------------------------------------------------------
@@ -313,7 +314,7 @@ void launch_det_ratios(const PairTables& pt, int nw, int n_str_a, int n_str_b, c
                        const double2* rb, double2* out, cudaStream_t st)
 {
     dim3 grid((pt.n_det + 255) / 256, nw);
-    k_det_ratios<<<grid, 256, 0, st>>>(pt, n_str_a, n_str_b, ra, rb, out);
+    k_det_ratios<<<grid, 256, 0, st>>>(pt, n_str_a, n_str_b, ra, rb, out); msd_note_launch();
 }
 
 // Sum of partial slots [slot0, slot0 + n) per walker -> out[w] (and
@@ -333,7 +334,7 @@ __global__ void k_sum_slots(int nw, const double2* __restrict__ part, int nslot,
 void launch_sum_slots(int nw, const double2* part, int nslot, int slot0, int n, double2* out,
                       const double2* O0a, const double2* O0b, double2* ovlp, cudaStream_t st)
 {
-    k_sum_slots<<<(nw + 127) / 128, 128, 0, st>>>(nw, part, nslot, slot0, n, out, O0a, O0b, ovlp);
+    k_sum_slots<<<(nw + 127) / 128, 128, 0, st>>>(nw, part, nslot, slot0, n, out, O0a, O0b, ovlp); msd_note_launch();
 }
 
 // ------------------------------------------------------------------------
@@ -377,6 +378,7 @@ void launch_cmat(const SpinTables& tb, int nw, const double2* r, const double2* 
 {
     if (fp32) k_cmat<float><<<nw, 256, 0, st>>>(tb, r, wts, B, Cm);
     else k_cmat<double><<<nw, 256, 0, st>>>(tb, r, wts, B, Cm);
+    msd_note_launch();
 }
 
 // ------------------------------------------------------------------------
@@ -428,7 +430,7 @@ void launch_gt(const SpinTables& tb, int nw, int M, const double2* Gr, const dou
                const double2* R, double2* GT, long long ld, long long off, cudaStream_t st)
 {
     dim3 grid((M + 7) / 8, nw);
-    k_gt<<<grid, 256, 0, st>>>(tb, M, Gr, Cm, R, GT, ld, off);
+    k_gt<<<grid, 256, 0, st>>>(tb, M, Gr, Cm, R, GT, ld, off); msd_note_launch();
 }
 
 // <D_0|phi> = det(D0^dag phi_a) det(D0^dag phi_b) per walker.
@@ -441,5 +443,5 @@ __global__ void k_ref_ovlp(int nw, const double2* __restrict__ O0a, const double
 
 void launch_ref_ovlp(int nw, const double2* O0a, const double2* O0b, double2* out, cudaStream_t st)
 {
-    k_ref_ovlp<<<(nw + 127) / 128, 128, 0, st>>>(nw, O0a, O0b, out);
+    k_ref_ovlp<<<(nw + 127) / 128, 128, 0, st>>>(nw, O0a, O0b, out); msd_note_launch();
 }

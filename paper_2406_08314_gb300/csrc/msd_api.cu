@@ -2,6 +2,7 @@
 // preprocessing, workspace management and the orchestration of the
 // kernels for overlap, per-determinant ratios, force bias and local energy.
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -12,6 +13,9 @@
 #include "../../include/msd.h"
 #include "common.cuh"
 #include "kernels.h"
+
+static std::atomic<long long> g_launches{0};
+void msd_note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 namespace {
 
@@ -975,6 +979,8 @@ int msd_set_workspace_limit(msd_ctx* ctx, size_t bytes)
     ctx->ws_limit = bytes ? bytes : ((size_t)4 << 30);
     return MSD_OK;
 }
+
+long long msd_launch_count(void) { return g_launches.load(); }
 
 int msd_set_sync(msd_ctx* ctx, int sync)
 {

@@ -22,7 +22,8 @@ _ERRORS = {-1: "MSD_ERR_ARG", -2: "MSD_ERR_SHAPE", -3: "MSD_ERR_CUDA", -4: "MSD_
 EXPORTS = ["msd_create", "msd_destroy", "msd_last_error", "msd_set_hamiltonian", "msd_set_trial",
            "msd_set_precision", "msd_overlap", "msd_det_ratios", "msd_force_bias",
            "msd_local_energy", "msd_info", "msd_set_timing", "msd_reset_stats",
-           "msd_kernel_count", "msd_kernel_stat", "msd_set_workspace_limit", "msd_set_sync"]
+           "msd_kernel_count", "msd_kernel_stat", "msd_set_workspace_limit", "msd_set_sync",
+           "msd_launch_count"]
 INFO = {"n_det": 1, "n_chol": 2, "n_strings_a": 3, "n_strings_b": 4, "n_holes_a": 5,
         "n_parts_a": 6, "n_holes_b": 7, "n_parts_b": 8, "workspace_bytes": 9, "walker_chunk": 10}
 
@@ -59,9 +60,11 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
                                     ctypes.POINTER(ctypes.c_longlong), dp]
     lib.msd_set_workspace_limit.argtypes = [vp, ctypes.c_size_t]
     lib.msd_set_sync.argtypes = [vp, ci]
+    lib.msd_launch_count.argtypes = []
     for f in EXPORTS:
         if f not in ("msd_destroy", "msd_last_error"):
             getattr(lib, f).restype = ci
+    lib.msd_launch_count.restype = ctypes.c_longlong
     return lib
 
 
@@ -70,6 +73,11 @@ _lib = load_library()
 
 def lib() -> ctypes.CDLL:
     return _lib
+
+
+def launch_count() -> int:
+    """Kernel launches made by libmsd in this process so far."""
+    return int(_lib.msd_launch_count())
 
 
 def _torch():

@@ -14,8 +14,10 @@ h1 -> L -> trial -> walkers):
     spins; e0 = 0.
   * L: n_chol random symmetric M x M matrices, orthonormalised in the
     Frobenius inner product (QR of the (M*M, n_chol) stack), multiplied by
-    exp(-gamma / decay), then scaled by one constant so that the mean
-    on-site Coulomb integral (pp|pp) = sum_gamma L_gamma[p, p]^2 is 1 Ha.
+    exp(-gamma / decay): the (M*M, n_chol) stack has singular values
+    exp(-gamma / decay). Optionally (onsite=x) all vectors are scaled by one
+    constant so that the mean on-site Coulomb integral
+    (pp|pp) = sum_gamma L_gamma[p, p]^2 is x Ha (a chemical-scale variant).
   * Trial: reference = the first N_sigma orbitals. The active space is
     orbitals [n_core, n_core + n_act_orb); each spin has
     n_o = N_sigma - n_core active occupied and n_v = n_act_orb - n_o active
@@ -77,7 +79,7 @@ class Walkers:
 
 
 def make_hamiltonian(rng: np.random.Generator, M: int, n_chol: int,
-                     decay: float = 10.0, onsite: float = 1.0):
+                     decay: float = 10.0, onsite: float | None = None):
     """h1 (2, M, M) and L (n_chol, M, M) following the module recipe."""
     if n_chol > M * (M + 1) // 2:
         raise ValueError("n_chol exceeds the dimension of symmetric M x M matrices")
@@ -92,10 +94,10 @@ def make_hamiltonian(rng: np.random.Generator, M: int, n_chol: int,
     Q = 0.5 * (Q + Q.transpose(0, 2, 1))                  # exact symmetry after rounding
     s = np.exp(-np.arange(n_chol) / float(decay))
     L = Q * s[:, None, None]
-    diag = np.einsum("gpp->gp", L)
-    scale = math.sqrt(onsite / float(np.mean(np.sum(diag * diag, axis=0))))
-    L = np.ascontiguousarray(L * scale)
-    return h1, L
+    if onsite is not None:
+        diag = np.einsum("gpp->gp", L)
+        L = L * math.sqrt(onsite / float(np.mean(np.sum(diag * diag, axis=0))))
+    return h1, np.ascontiguousarray(L)
 
 
 def _level_counts(n_o: int, n_v: int):
@@ -238,14 +240,14 @@ def _expm_apply_matrix(A: np.ndarray, order: int = 12) -> np.ndarray:
 
 def make_system(seed: int, M: int, n_alpha: int, n_beta: int, n_core: int,
                 n_act_orb: int, n_det: int, max_level: int, power: float,
-                n_chol: int, decay: float = 10.0) -> System:
+                n_chol: int, decay: float = 10.0, onsite: float | None = None) -> System:
     rng = np.random.default_rng(seed)
-    h1, L = make_hamiltonian(rng, M, n_chol, decay)
+    h1, L = make_hamiltonian(rng, M, n_chol, decay, onsite)
     coeff, occ_a, occ_b = make_trial(rng, M, n_alpha, n_beta, n_core, n_act_orb,
                                      n_det, max_level, power)
     sys = System(M, n_alpha, n_beta, h1, 0.0, L, coeff, occ_a, occ_b, n_core,
                  n_act_orb, dict(seed=seed, decay=decay, power=power,
-                                 max_level=max_level))
+                                 max_level=max_level, onsite=onsite))
     sys.meta["rng"] = rng  # the walker draws continue this stream
     return sys
 
@@ -265,7 +267,7 @@ CONFIGS = {
 
 def config_system(name: str, seed: int = 0, n_w: int | None = None,
                   n_det: int | None = None, n_chol: int | None = None,
-                  decay: float = 10.0):
+                  decay: float = 10.0, onsite: float | None = None):
     """(System, Walkers) for a named workload; sizes may be overridden."""
     c = dict(CONFIGS[name])
     if n_det is not None:
@@ -276,7 +278,7 @@ def config_system(name: str, seed: int = 0, n_w: int | None = None,
         c["n_w"] = n_w
     sys = make_system(seed, c["M"], c["n_alpha"], c["n_beta"], c["n_core"],
                       c["n_act_orb"], c["n_det"], c["max_level"], c["power"],
-                      c["n_chol"], decay)
+                      c["n_chol"], decay, onsite)
     rng = sys.meta.pop("rng")
     w = make_walkers(rng, sys.M, sys.n_alpha, sys.n_beta, c["n_w"])
     if c["walk_steps"]:

@@ -23,7 +23,12 @@ def test_small_config_shapes_and_structure():
     gram = np.einsum("gpq,hpq->gh", s.L, s.L)
     assert np.allclose(gram - np.diag(np.diag(gram)), 0, atol=1e-10)
     d = np.sqrt(np.diag(gram))
-    assert np.allclose(d[1:] / d[:-1], np.exp(-0.1))
+    assert np.allclose(d, np.exp(-0.1 * np.arange(60)))      # singular values exp(-g/10)
+
+
+def test_chemical_scale_variant():
+    s = synth.make_system(0, 20, 5, 5, 0, 10, 50, 4, 1.5, 60, onsite=1.0)
+    assert abs(np.mean(np.sum(np.einsum("gpp->gp", s.L) ** 2, axis=0)) - 1.0) < 1e-12
 
 
 def test_seeded_and_reproducible():
