@@ -295,6 +295,7 @@ k_gram(int Xp, int Xq, int n_chol, const double2* __restrict__ P, const double2*
 void launch_gram(int nw, int Xp, int Xq, int n_chol, const double2* P, const double2* Q, void* K,
                  bool fp32, cudaStream_t st)
 {
+    if (Xp <= 0 || Xq <= 0 || nw <= 0) return;
     dim3 grid((Xq + 31) / 32, (Xp + 31) / 32, nw);
     if (fp32) k_gram<float><<<grid, 256, 0, st>>>(Xp, Xq, n_chol, P, Q, (float*)K);
     else k_gram<double><<<grid, 256, 0, st>>>(Xp, Xq, n_chol, P, Q, (double*)K);

@@ -388,10 +388,12 @@ void launch_cmat(const SpinTables& tb, int nw, const double2* r, const double2* 
 //   G_T[occ0_l][c] = G[occ0_l][c] - sum_p G[occ0_l][P_p] Y[p][c] / R
 //   G_T[P_p][c]    = Y[p][c] / R
 // Written to GT[w][row][c] with row stride M, at column offset `off` of a
-// row of length ld (both spins are concatenated per walker).
+// row of length ld (both spins are concatenated per walker). With
+// minus_ref the reference part D0 D0^T (ones at (occ0_l, occ0_l)) is
+// subtracted, for the mixed path that adds its contraction in FP64.
 __global__ void __launch_bounds__(256)
 k_gt(SpinTables tb, int M, const double2* __restrict__ Gr, const double2* __restrict__ Cm,
-     const double2* __restrict__ Rsum, double2* __restrict__ GT, long long ld, long long off)
+     const double2* __restrict__ Rsum, double2* __restrict__ GT, long long ld, long long off, int minus_ref)
 {
     __shared__ double2 cm[MSD_XMAX];
     __shared__ double2 y[MSD_XMAX * 8];   // [np][8 columns]
@@ -419,6 +421,7 @@ k_gt(SpinTables tb, int M, const double2* __restrict__ Gr, const double2* __rest
         if (x < N) {
             v = gr[(size_t)x * M + c];
             for (int p = 0; p < np; ++p) v = cfms(gr[(size_t)x * M + tb.part_orb[p]], y[p * 8 + e % 8], v);
+            if (minus_ref && c == tb.occ0[x]) v.x -= 1.0;   // G_T - D0 D0^T
         } else {
             v = y[(x - N) * 8 + e % 8];
         }
@@ -427,10 +430,10 @@ k_gt(SpinTables tb, int M, const double2* __restrict__ Gr, const double2* __rest
 }
 
 void launch_gt(const SpinTables& tb, int nw, int M, const double2* Gr, const double2* Cm,
-               const double2* R, double2* GT, long long ld, long long off, cudaStream_t st)
+               const double2* R, double2* GT, long long ld, long long off, bool minus_ref, cudaStream_t st)
 {
     dim3 grid((M + 7) / 8, nw);
-    k_gt<<<grid, 256, 0, st>>>(tb, M, Gr, Cm, R, GT, ld, off); msd_note_launch();
+    k_gt<<<grid, 256, 0, st>>>(tb, M, Gr, Cm, R, GT, ld, off, minus_ref ? 1 : 0); msd_note_launch();
 }
 
 // <D_0|phi> = det(D0^dag phi_a) det(D0^dag phi_b) per walker.

@@ -28,7 +28,7 @@ void launch_ref_ovlp(int nw, const double2* O0a, const double2* O0b, double2* ou
 void launch_cmat(const SpinTables& tb, int nw, const double2* r, const double2* wts, const void* B,
                  bool fp32, double2* Cm, cudaStream_t st);
 void launch_gt(const SpinTables& tb, int nw, int M, const double2* Gr, const double2* Cm,
-               const double2* R, double2* GT, long long ld, long long off, cudaStream_t st);
+               const double2* R, double2* GT, long long ld, long long off, bool minus_ref, cudaStream_t st);
 
 // k_energy.cu
 void launch_gemm_zd(int Mr, int Nc, int K, const double2* A, long long lda, const double* B,
@@ -58,3 +58,31 @@ void launch_pair_cross(const SpinTables& ta, const SpinTables& tb, const PairTab
 void launch_final(int nw, const double2* part, int nslot, int nR, double e0, const double2* e1a,
                   const double2* e1b, const double2* scal, const double2* O0a, const double2* O0b,
                   double2* eloc, double2* ovlp, cudaStream_t st);
+
+// tc_gemm.cu: 3xTF32 tensor-core GEMM C[m][n] = sum_k A[m][k] B[n][k] with
+// A, B given as hi/lo TF32 parts, K-major with row pitch ld (elements).
+struct TcOperand {
+    const float* hi;
+    const float* lo;
+    long long ld;
+};
+// K is split over `splits` CTAs along grid.z; split z writes C + z * c_split_stride.
+int tc_gemm_3xtf32(const TcOperand& A, const TcOperand& B, int Mr, int Nc, int K, float* C, long long ldc,
+                   unsigned* err, cudaStream_t st, int splits = 1, long long c_split_stride = 0);
+void launch_split_complex_rows(int nb, int R, int Kg, int Kp, const double2* src, long long src_ld,
+                               const int* cols, float* hi, float* lo, cudaStream_t st);
+void launch_split_real_rows(long long R, int Kg, int Kp, const double* src, long long src_ld, const int* cols,
+                            float* hi, float* lo, cudaStream_t st);
+void launch_pack_complex(int nw, int n, const float* C, long long ldc, int splits, long long split_stride,
+                         const double* add, double2* out, long long ldo, cudaStream_t st);
+
+// k_mixed.cu
+size_t fepi_f32_smem(const SpinTables& tb);
+void launch_fepi_f32(const SpinTables& tb, int nw, int M, int n_chol, const float* dF, long long ldf,
+                     const double2* Gr, const double* Lh, const double* c0, const double* x0, double2* v0,
+                     double2* xx, float2* Lact, float2* Xic, cudaStream_t st);
+void launch_gamma_reduce_f32(int nw, int X, int n_chol, int spin, const double2* v0a, const double2* v0b,
+                             const double2* xx, const float2* Lact, const float2* Xic, const double2* Lh,
+                             float2* Y, double2* scal, cudaStream_t st);
+void launch_gram_f32(int nw, int Xp, int Xq, int n_chol, const float2* P, const float2* Q, float2* K,
+                     cudaStream_t st);

@@ -69,7 +69,7 @@ struct msd_ctx {
     SpinHost sp[2];
     PairHost pairs;
     std::map<std::string, Buf> arena;
-    size_t ws_limit = (size_t)4 << 30;
+    size_t ws_limit = (size_t)16 << 30;
     int chunk = 0;
     unsigned* d_err = nullptr;
     unsigned* h_err = nullptr;
@@ -85,9 +85,20 @@ struct msd_ctx {
     int open_k = -1;
     cudaEvent_t open_ev = nullptr;
     TimerHook hook;
+    // TF32 hi/lo splits of the half-rotated Cholesky vectors (mixed path)
+    bool mixed_ready = false;
+    int Kp = 0;                 // M padded to a multiple of 32
+    long long Kdp = 0;          // Kd padded to a multiple of 32
+    float *LhF_hi[2] = {nullptr, nullptr}, *LhF_lo[2] = {nullptr, nullptr};
+    float *Lv_hi = nullptr, *Lv_lo = nullptr;
+    int Kvp[2] = {0, 0};        // virtual orbitals (not in occ0) padded to 32
+    int* d_virt[2] = {nullptr, nullptr};
+    double *d_c0[2] = {nullptr, nullptr}, *d_x0[2] = {nullptr, nullptr}, *d_c0sum = nullptr;
 };
 
 namespace {
+
+void free_mixed(msd_ctx* ctx);
 
 int fail(msd_ctx* c, int code, const char* fmt, ...)
 {
@@ -356,6 +367,7 @@ void free_spin(SpinHost& S)
 // rows occ0 then P of each L_g, per spin, and both spins concatenated.
 int build_half_rotated(msd_ctx* ctx)
 {
+    free_mixed(ctx);
     if (!ctx->have_ham || !ctx->have_trial) return MSD_OK;
     const int M = ctx->M, G = ctx->n_chol;
     long long Kd = 0;
@@ -379,6 +391,81 @@ int build_half_rotated(msd_ctx* ctx)
         off += (long long)NC * M;
     }
     return upload(ctx, &ctx->d_Lcat, cat);
+}
+
+void free_mixed(msd_ctx* ctx)
+{
+    for (int s = 0; s < 2; ++s) {
+        cudaFree(ctx->LhF_hi[s]); cudaFree(ctx->LhF_lo[s]);
+        ctx->LhF_hi[s] = ctx->LhF_lo[s] = nullptr;
+    }
+    cudaFree(ctx->Lv_hi); cudaFree(ctx->Lv_lo);
+    ctx->Lv_hi = ctx->Lv_lo = nullptr;
+    for (int s = 0; s < 2; ++s) {
+        cudaFree(ctx->d_virt[s]); cudaFree(ctx->d_c0[s]); cudaFree(ctx->d_x0[s]);
+        ctx->d_virt[s] = nullptr; ctx->d_c0[s] = ctx->d_x0[s] = nullptr;
+    }
+    cudaFree(ctx->d_c0sum);
+    ctx->d_c0sum = nullptr;
+    ctx->mixed_ready = false;
+}
+
+// Mixed-path operands, once per Hamiltonian and trial. The reference part
+// of the Green's function is known exactly: Theta[occ0, :] = I, so
+// G = D0 D0^T + dG with dG non-zero only in the columns of the orbitals
+// outside occ0 ("virtual" columns). The tensor cores contract only dG with
+// L (TF32 hi/lo splits gathered at the virtual columns); the reference
+// parts enter in FP64:
+//   c0_g = tr(L_g D0 D0^T) = sum_j L_g[occ0_j][occ0_j],
+//   x0_g = tr(L_g D0 D0^T L_g D0 D0^T) = sum_jl L_g[occ0_j][occ0_l]^2.
+int prepare_mixed(msd_ctx* ctx, cudaStream_t st)
+{
+    if (ctx->mixed_ready) return MSD_OK;
+    const int M = ctx->M, G = ctx->n_chol;
+    ctx->Kp = (M + 31) / 32 * 32;
+    ctx->Kdp = (ctx->Kd + 31) / 32 * 32;
+    std::vector<double> c0sum(G, 0.0);
+    for (int s = 0; s < 2; ++s) {
+        const SpinHost& S = ctx->sp[s];
+        std::vector<char> in0(M, 0);
+        for (int o : S.occ0) in0[o] = 1;
+        std::vector<int> virt;
+        for (int o = 0; o < M; ++o) if (!in0[o]) virt.push_back(o);
+        const int Kv = (int)virt.size();
+        ctx->Kvp[s] = std::max(32, (Kv + 31) / 32 * 32);
+        if (Kv == 0) virt.push_back(0);   // keeps the gather pointer valid; Kg = 0 pads with zeros
+        int rc = upload(ctx, &ctx->d_virt[s], virt);
+        if (rc) return rc;
+        std::vector<double> c0(G), x0(G);
+        for (int g = 0; g < G; ++g) {
+            const double* Lg = &ctx->h_L[(size_t)g * M * M];
+            double a = 0, b = 0;
+            for (int j = 0; j < S.N; ++j) {
+                a += Lg[(size_t)S.occ0[j] * M + S.occ0[j]];
+                for (int l = 0; l < S.N; ++l) {
+                    const double v = Lg[(size_t)S.occ0[j] * M + S.occ0[l]];
+                    b += v * v;
+                }
+            }
+            c0[g] = a; x0[g] = b; c0sum[g] += a;
+        }
+        if ((rc = upload(ctx, &ctx->d_c0[s], c0))) return rc;
+        if ((rc = upload(ctx, &ctx->d_x0[s], x0))) return rc;
+        const long long R = (long long)G * (S.N + S.np);
+        CK(cudaMalloc(&ctx->LhF_hi[s], sizeof(float) * R * ctx->Kvp[s]));
+        CK(cudaMalloc(&ctx->LhF_lo[s], sizeof(float) * R * ctx->Kvp[s]));
+        launch_split_real_rows(R, Kv, ctx->Kvp[s], S.d_Lh, M, ctx->d_virt[s], ctx->LhF_hi[s], ctx->LhF_lo[s], st);
+    }
+    int rc = upload(ctx, &ctx->d_c0sum, c0sum);
+    if (rc) return rc;
+    CK(cudaMalloc(&ctx->Lv_hi, sizeof(float) * G * ctx->Kdp));
+    CK(cudaMalloc(&ctx->Lv_lo, sizeof(float) * G * ctx->Kdp));
+    launch_split_real_rows(G, (int)ctx->Kd, (int)ctx->Kdp, ctx->d_Lcat, ctx->Kd, nullptr, ctx->Lv_hi, ctx->Lv_lo,
+                           st);
+    CKLAUNCH();
+    CK(cudaStreamSynchronize(st));
+    ctx->mixed_ready = true;
+    return MSD_OK;
 }
 
 int check_ready(msd_ctx* ctx)
@@ -596,6 +683,7 @@ void msd_destroy(msd_ctx* ctx)
     for (int s = 0; s < 2; ++s) free_spin(ctx->sp[s]);
     cudaFree(ctx->pairs.d_a); cudaFree(ctx->pairs.d_b); cudaFree(ctx->pairs.d_c);
     cudaFree(ctx->pairs.d_det_index);
+    free_mixed(ctx);
     cudaFree(ctx->d_h1); cudaFree(ctx->d_Lcat); cudaFree(ctx->d_err);
     cudaFreeHost(ctx->h_err);
     for (auto& p : ctx->pending) { ctx->ev_pool.push_back(p.a); ctx->ev_pool.push_back(p.b); }
@@ -766,6 +854,7 @@ int msd_force_bias(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi
     if (n_w == 0) return MSD_OK;
     if (!vbias) return fail(ctx, MSD_ERR_ARG, "vbias is NULL");
     const bool fp32 = ctx->prec == MSD_MIXED;
+    if (fp32 && (rc = prepare_mixed(ctx, st))) return rc;
     Staged in;
     if ((rc = stage_inputs(ctx, n_w, phi_a, phi_b, st, in))) return rc;
     Out o_v, o_ov;
@@ -797,12 +886,37 @@ int msd_force_bias(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi
             launch_cmat(T, nw, c.r[s], c.wts[s], c.B[s], fp32, (double2*)Cm[s], st);
             th.end(st);
             th.begin("k_gt", st);
-            launch_gt(T, nw, ctx->M, c.Gr[s], (double2*)Cm[s], (double2*)Rs, (double2*)GT, ctx->Kd, off, st);
+            launch_gt(T, nw, ctx->M, c.Gr[s], (double2*)Cm[s], (double2*)Rs, (double2*)GT, ctx->Kd, off, fp32,
+                      st);
             th.end(st);
             off += (long long)(T.N + T.np) * ctx->M;
         }
         CKLAUNCH();
-        {
+        if (fp32) {
+            // vbias = c0_a + c0_b + (GT - D0 D0^T) . Lcat^T, the contraction on
+            // the tensor cores (3xTF32, rows (w, re/im), K split over CTAs and
+            // the splits summed in FP64)
+            const int ks = std::max(1, std::min(16, (int)(ctx->Kdp / 32 / 64)));
+            void *Ah, *Al, *C32;
+            if ((rc = arena_get(ctx, "Av_hi", sizeof(float) * 2 * cap * ctx->Kdp, &Ah))) return rc;
+            if ((rc = arena_get(ctx, "Av_lo", sizeof(float) * 2 * cap * ctx->Kdp, &Al))) return rc;
+            if ((rc = arena_get(ctx, "Cv32", sizeof(float) * ks * 2 * cap * ctx->n_chol, &C32))) return rc;
+            th.begin("k_split_vbias", st);
+            launch_split_complex_rows(nw, 1, (int)ctx->Kd, (int)ctx->Kdp, (const double2*)GT, ctx->Kd, nullptr,
+                                      (float*)Ah, (float*)Al, st);
+            th.end(st);
+            th.begin("tc_gemm_vbias", st);
+            const long long sstride = (long long)2 * nw * ctx->n_chol;
+            const int g = tc_gemm_3xtf32({(float*)Ah, (float*)Al, ctx->Kdp}, {ctx->Lv_hi, ctx->Lv_lo, ctx->Kdp},
+                                         2 * nw, ctx->n_chol, (int)ctx->Kdp, (float*)C32, ctx->n_chol,
+                                         ctx->d_err, st, ks, sstride);
+            th.end(st);
+            if (g) return fail(ctx, MSD_ERR_CUDA, "tensor-core GEMM launch failed (force bias)");
+            th.begin("k_pack_vbias", st);
+            launch_pack_complex(nw, ctx->n_chol, (float*)C32, ctx->n_chol, ks, sstride, ctx->d_c0sum,
+                                o_v.dev + (size_t)w0 * ctx->n_chol, ctx->n_chol, st);
+            th.end(st);
+        } else {
             th.begin("k_gemm_vbias", st);
             launch_gemm_zd(nw, ctx->n_chol, (int)ctx->Kd, (const double2*)GT, ctx->Kd, ctx->d_Lcat,
                            ctx->Kd, o_v.dev + (size_t)w0 * ctx->n_chol, ctx->n_chol, st);
@@ -822,6 +936,7 @@ int msd_local_energy(msd_ctx* ctx, int n_w, const double* phi_a, const double* p
     if (n_w == 0) return MSD_OK;
     if (!e_loc) return fail(ctx, MSD_ERR_ARG, "e_loc is NULL");
     const bool fp32 = ctx->prec == MSD_MIXED;
+    if (fp32 && (rc = prepare_mixed(ctx, st))) return rc;
     const int M = ctx->M, G = ctx->n_chol;
     Staged in;
     if ((rc = stage_inputs(ctx, n_w, phi_a, phi_b, st, in))) return rc;
@@ -834,22 +949,47 @@ int msd_local_energy(msd_ctx* ctx, int n_w, const double* phi_a, const double* p
                    pair_cross_slots(pair_tables(ctx->pairs));
     const int nslot = nR + nE;
     const int X[2] = {T1[0].nh * T1[0].np, T1[1].nh * T1[1].np};
+    const int NC[2] = {T1[0].N + T1[0].np, T1[1].N + T1[1].np};
+    // per-walker footprint (complex units unless noted)
     size_t per = overlap_bytes_per_walker(ctx, true, nslot);
     size_t e_per = 8 + 2;
-    for (int s = 0; s < 2; ++s)
-        e_per += (size_t)T1[s].N * G * (T1[s].N + T1[s].np) + (size_t)G * (2 + 2 * X[s]) + 3 * X[s] + 1;
+    for (int s = 0; s < 2; ++s) e_per += (size_t)G * (2 + 2 * X[s]) + 3 * X[s] + 1;
     e_per += (size_t)X[0] * X[0] + (size_t)X[1] * X[1] + (size_t)X[0] * X[1];
     per += e_per * sizeof(double2);
+    size_t fbytes_per_walker;   // dense F buffer per walker
+    if (fp32) {
+        size_t f = 0, a = 0;
+        for (int s = 0; s < 2; ++s) {
+            f = std::max(f, sizeof(float) * 2 * T1[s].N * (size_t)G * NC[s]);
+            a = std::max(a, sizeof(float) * 2 * 2 * T1[s].N * (size_t)ctx->Kvp[s]);
+        }
+        fbytes_per_walker = f + a;
+    } else {
+        fbytes_per_walker = 0;
+        for (int s = 0; s < 2; ++s) fbytes_per_walker += sizeof(double2) * T1[s].N * (size_t)G * NC[s];
+    }
+    per += fbytes_per_walker;
     const int cap = chunk_for(ctx, per, n_w);
     Chunk c;
     if ((rc = chunk_alloc(ctx, cap, true, nslot, c))) return rc;
-    void *F[2], *v0[2], *xx[2], *La[2], *Xi[2], *Lh1[2], *e1[2], *Y[2], *Kaa, *Kbb, *Kab, *scal;
+    void *F[2] = {nullptr, nullptr}, *F32 = nullptr, *Ah = nullptr, *Al = nullptr;
+    void *v0[2], *xx[2], *La[2], *Xi[2], *Lh1[2], *e1[2], *Y[2], *Kaa, *Kbb, *Kab, *scal;
     static const char* nm[2][8] = {{"F_a", "v0_a", "xx_a", "Lact_a", "Xic_a", "Lh1_a", "e1_a", "Y_a"},
                                    {"F_b", "v0_b", "xx_b", "Lact_b", "Xic_b", "Lh1_b", "e1_b", "Y_b"}};
+    if (fp32) {
+        size_t f = 0, a = 0;
+        for (int s = 0; s < 2; ++s) {
+            f = std::max(f, sizeof(float) * 2 * T1[s].N * (size_t)G * NC[s]);
+            a = std::max(a, sizeof(float) * 2 * T1[s].N * (size_t)ctx->Kvp[s]);
+        }
+        if ((rc = arena_get(ctx, "F32", f * cap, &F32))) return rc;
+        if ((rc = arena_get(ctx, "AF_hi", a * cap, &Ah))) return rc;
+        if ((rc = arena_get(ctx, "AF_lo", a * cap, &Al))) return rc;
+    }
     for (int s = 0; s < 2; ++s) {
-        const int NC = T1[s].N + T1[s].np;
         const size_t xs = std::max(1, X[s]);
-        if ((rc = arena_get(ctx, nm[s][0], sizeof(double2) * cap * T1[s].N * (size_t)G * NC, &F[s]))) return rc;
+        if (!fp32 && (rc = arena_get(ctx, nm[s][0], sizeof(double2) * cap * T1[s].N * (size_t)G * NC[s], &F[s])))
+            return rc;
         if ((rc = arena_get(ctx, nm[s][1], sizeof(double2) * cap * (size_t)G, &v0[s]))) return rc;
         if ((rc = arena_get(ctx, nm[s][2], sizeof(double2) * cap * (size_t)G, &xx[s]))) return rc;
         if ((rc = arena_get(ctx, nm[s][3], sizeof(double2) * cap * (size_t)G * xs, &La[s]))) return rc;
@@ -868,15 +1008,34 @@ int msd_local_energy(msd_ctx* ctx, int n_w, const double* phi_a, const double* p
         if ((rc = run_overlap_part(ctx, in, w0, nw, cap, c, true, fp32, st))) return rc;
         SpinTables T[2] = {tables(ctx->sp[0], cap), tables(ctx->sp[1], cap)};
         for (int s = 0; s < 2; ++s) {
-            const int NC = T[s].N + T[s].np;
-            th.begin("k_gemm_F", st);
-            launch_gemm_zd(nw * T[s].N, G * NC, M, c.Gr[s], M, ctx->sp[s].d_Lh, M, (double2*)F[s],
-                           (long long)G * NC, st);
-            th.end(st);
-            th.begin("k_fepi", st);
-            launch_fepi(T[s], nw, M, G, (double2*)F[s], (long long)G * NC, c.Gr[s], (double2*)v0[s],
-                        (double2*)xx[s], (double2*)La[s], (double2*)Xi[s], st);
-            th.end(st);
+            const int N = T[s].N;
+            if (fp32) {
+                th.begin("k_split_F", st);
+                const int Kv = M - N;
+                launch_split_complex_rows(nw, N, Kv, ctx->Kvp[s], c.Gr[s], M, ctx->d_virt[s], (float*)Ah,
+                                          (float*)Al, st);
+                th.end(st);
+                th.begin("tc_gemm_F", st);
+                const int g = tc_gemm_3xtf32({(float*)Ah, (float*)Al, ctx->Kvp[s]},
+                                             {ctx->LhF_hi[s], ctx->LhF_lo[s], ctx->Kvp[s]}, 2 * nw * N, G * NC[s],
+                                             ctx->Kvp[s], (float*)F32, (long long)G * NC[s], ctx->d_err, st);
+                th.end(st);
+                if (g) return fail(ctx, MSD_ERR_CUDA, "tensor-core GEMM launch failed (energy)");
+                th.begin("k_fepi_f32", st);
+                launch_fepi_f32(T[s], nw, M, G, (float*)F32, (long long)G * NC[s], c.Gr[s], ctx->sp[s].d_Lh,
+                                ctx->d_c0[s], ctx->d_x0[s], (double2*)v0[s], (double2*)xx[s], (float2*)La[s],
+                                (float2*)Xi[s], st);
+                th.end(st);
+            } else {
+                th.begin("k_gemm_F", st);
+                launch_gemm_zd(nw * N, G * NC[s], M, c.Gr[s], M, ctx->sp[s].d_Lh, M, (double2*)F[s],
+                               (long long)G * NC[s], st);
+                th.end(st);
+                th.begin("k_fepi", st);
+                launch_fepi(T[s], nw, M, G, (double2*)F[s], (long long)G * NC[s], c.Gr[s], (double2*)v0[s],
+                            (double2*)xx[s], (double2*)La[s], (double2*)Xi[s], st);
+                th.end(st);
+            }
             th.begin("k_onebody", st);
             launch_onebody(T[s], nw, M, ctx->d_h1 + (size_t)s * M * M, c.Gr[s], (double2*)e1[s],
                            (double2*)Lh1[s], st);
@@ -884,15 +1043,27 @@ int msd_local_energy(msd_ctx* ctx, int n_w, const double* phi_a, const double* p
             CKLAUNCH();
         }
         th.begin("k_gamma_reduce", st);
-        for (int s = 0; s < 2; ++s)
-            launch_gamma_reduce(nw, X[s], G, s, (double2*)v0[0], (double2*)v0[1], (double2*)xx[s],
-                                (double2*)La[s], (double2*)Xi[s], (double2*)Lh1[s], Y[s], fp32,
-                                (double2*)scal, st);
+        for (int s = 0; s < 2; ++s) {
+            if (fp32)
+                launch_gamma_reduce_f32(nw, X[s], G, s, (double2*)v0[0], (double2*)v0[1], (double2*)xx[s],
+                                        (float2*)La[s], (float2*)Xi[s], (double2*)Lh1[s], (float2*)Y[s],
+                                        (double2*)scal, st);
+            else
+                launch_gamma_reduce(nw, X[s], G, s, (double2*)v0[0], (double2*)v0[1], (double2*)xx[s],
+                                    (double2*)La[s], (double2*)Xi[s], (double2*)Lh1[s], Y[s], false,
+                                    (double2*)scal, st);
+        }
         th.end(st);
         th.begin("k_gram", st);
-        launch_gram(nw, X[0], X[0], G, (double2*)La[0], (double2*)La[0], Kaa, fp32, st);
-        launch_gram(nw, X[1], X[1], G, (double2*)La[1], (double2*)La[1], Kbb, fp32, st);
-        launch_gram(nw, X[0], X[1], G, (double2*)La[0], (double2*)La[1], Kab, fp32, st);
+        if (fp32) {
+            launch_gram_f32(nw, X[0], X[0], G, (float2*)La[0], (float2*)La[0], (float2*)Kaa, st);
+            launch_gram_f32(nw, X[1], X[1], G, (float2*)La[1], (float2*)La[1], (float2*)Kbb, st);
+            launch_gram_f32(nw, X[0], X[1], G, (float2*)La[0], (float2*)La[1], (float2*)Kab, st);
+        } else {
+            launch_gram(nw, X[0], X[0], G, (double2*)La[0], (double2*)La[0], Kaa, false, st);
+            launch_gram(nw, X[1], X[1], G, (double2*)La[1], (double2*)La[1], Kbb, false, st);
+            launch_gram(nw, X[0], X[1], G, (double2*)La[0], (double2*)La[1], Kab, false, st);
+        }
         th.end(st);
         CKLAUNCH();
         int slot = nR;
@@ -976,7 +1147,7 @@ int msd_kernel_stat(msd_ctx* ctx, int index, const char** name, long long* launc
 int msd_set_workspace_limit(msd_ctx* ctx, size_t bytes)
 {
     if (!ctx) return MSD_ERR_ARG;
-    ctx->ws_limit = bytes ? bytes : ((size_t)4 << 30);
+    ctx->ws_limit = bytes ? bytes : ((size_t)16 << 30);
     return MSD_OK;
 }
 

@@ -1,0 +1,413 @@
+// Tensor-core (tcgen05) GEMM for the dense Cholesky-vector contractions of
+// the mixed-precision path, in 3xTF32 split precision:
+//   C[m][n] = sum_k A[m][k] B[n][k]
+//           ~ sum_k (Ahi Bhi + Ahi Blo + Alo Bhi)[m][n][k],  FP32 accumulation,
+// with x = hi + lo + O(2^-22 |x|), hi and lo TF32-representable.
+//
+// sm_103a design: one CTA per 128 x BN output tile; A and B tiles (K-major,
+// 128-byte swizzle) stream through a shared-memory ring filled by TMA
+// (cp.async.bulk.tensor) and tracked by mbarriers; one thread issues
+// tcgen05.mma (kind::tf32) into a TMEM accumulator; tcgen05.commit frees
+// ring slots; four warps read the accumulator back with tcgen05.ld. Every
+// wait is bounded (about 2 s of wall clock); on expiry the kernel records
+// MSD_DEV_ERR_TIMEOUT, drains what it issued and releases its TMEM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstdint>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace {
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase of the given parity to complete, for at most ~2 s.
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > 2000000000ull) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(su32(dst)), "l"((uint64_t)map), "r"(su32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle,
+// 8-row x 128-byte atoms stacked every 1024 bytes.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
+    d |= (uint64_t)1 << 16;                     // leading byte offset (unused for SW128 K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset
+    d |= (uint64_t)1 << 46;                     // descriptor version
+    d |= (uint64_t)2 << 61;                     // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor of kind::tf32: FP32 accumulator, TF32 A and B,
+// both K-major, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N)
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
+        ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int BN>
+struct TcCfg {
+    static constexpr int BM = 128, BK = 32;
+    static constexpr int STAGES = BN >= 256 ? 2 : 3;
+    static constexpr uint32_t A_BYTES = BM * BK * 4;
+    static constexpr uint32_t B_BYTES = BN * BK * 4;
+    static constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+    static constexpr uint32_t TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(128, 1)
+k_tc_gemm(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
+          const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
+          int Mr, int Nc, int K, float* __restrict__ C, long long ldc, long long c_split_stride,
+          unsigned* err)
+{
+    using Cfg = TcCfg<BN>;
+    constexpr int BM = Cfg::BM, BK = Cfg::BK, STAGES = Cfg::STAGES;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full_bar[STAGES];
+    __shared__ __align__(8) uint64_t empty_bar[STAGES];
+    __shared__ __align__(8) uint64_t done_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int fail;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    // k-blocks [kb0, kb1) of this split
+    const int nkb_all = K / BK;
+    const int kb0 = (int)((long long)nkb_all * blockIdx.z / gridDim.z);
+    const int kb1 = (int)((long long)nkb_all * (blockIdx.z + 1) / gridDim.z);
+    const int nkb = kb1 - kb0;
+    C += (size_t)blockIdx.z * c_split_stride;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+        mbar_init(&done_bar, 1);
+        fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(su32(&tmem_base_sh)), "r"(Cfg::TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        int issued = 0;
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb % STAGES;
+            const uint32_t ph = (kb / STAGES) & 1;
+            if (!mbar_wait(&empty_bar[s], ph ^ 1)) { fail = 1; atomicOr(err, MSD_DEV_ERR_TIMEOUT); break; }
+            uint8_t* st = smem + (size_t)s * Cfg::STAGE_BYTES;
+            mbar_expect_tx(&full_bar[s], Cfg::STAGE_BYTES);
+            const int kx = (kb0 + kb) * BK;
+            tma_load_2d(st, &ta_hi, &full_bar[s], kx, m0);
+            tma_load_2d(st + Cfg::A_BYTES, &ta_lo, &full_bar[s], kx, m0);
+            tma_load_2d(st + 2 * Cfg::A_BYTES, &tb_hi, &full_bar[s], kx, n0);
+            tma_load_2d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, &tb_lo, &full_bar[s], kx, n0);
+            issued = kb + 1;
+        }
+        if (fail) {
+            // drain: the loads already issued must land before the CTA exits
+            for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb)
+                mbar_wait(&full_bar[kb % STAGES], (kb / STAGES) & 1);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = idesc_tf32(BM, BN);
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb % STAGES;
+            const uint32_t ph = (kb / STAGES) & 1;
+            if (!mbar_wait(&full_bar[s], ph)) { fail = 1; atomicOr(err, MSD_DEV_ERR_TIMEOUT); break; }
+            tc_fence_after();
+            const uint32_t sa = su32(smem + (size_t)s * Cfg::STAGE_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < BK / 8; ++kk) {
+                const uint64_t ah = sw128_desc(sa + kk * 32);
+                const uint64_t al = sw128_desc(sa + Cfg::A_BYTES + kk * 32);
+                const uint64_t bh = sw128_desc(sa + 2 * Cfg::A_BYTES + kk * 32);
+                const uint64_t bl = sw128_desc(sa + 2 * Cfg::A_BYTES + Cfg::B_BYTES + kk * 32);
+                mma_tf32(tmem, ah, bh, idesc, (kb | kk) != 0);
+                mma_tf32(tmem, ah, bl, idesc, 1u);
+                mma_tf32(tmem, al, bh, idesc, 1u);
+            }
+            mma_commit(&empty_bar[s]);
+        }
+        mma_commit(&done_bar);
+    }
+    __syncwarp();
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(&done_bar, 0) ? 1 : 0);
+    tc_fence_after();
+    if (ok && !fail) {
+        const int row = m0 + warp * 32 + lane;
+        for (int c = 0; c < BN; c += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+            if (row < Mr) {
+                float* dst = C + (size_t)row * ldc + n0 + c;
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    if (n0 + c + i < Nc) dst[i] = v[i];
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        atomicOr(err, MSD_DEV_ERR_TIMEOUT);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::TMEM_COLS)
+                     : "memory");
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// 2-D FP32 tensor [outer][inner] with row pitch `ld` elements; 32 x box_outer
+// boxes with 128-byte swizzle.
+int make_map(CUtensorMap* map, const float* base, int inner, int outer, long long ld, int box_outer)
+{
+    auto fn = encode_fn();
+    if (!fn) return -1;
+    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+    cuuint32_t box[2] = {32, (cuuint32_t)box_outer};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : -1;
+}
+
+template <int BN>
+int launch_bn(const TcOperand& A, const TcOperand& B, int Mr, int Nc, int K, float* C, long long ldc,
+              int splits, long long c_split_stride, unsigned* err, cudaStream_t st)
+{
+    CUtensorMap ah, al, bh, bl;
+    if (make_map(&ah, A.hi, K, Mr, A.ld, 128) || make_map(&al, A.lo, K, Mr, A.ld, 128) ||
+        make_map(&bh, B.hi, K, Nc, B.ld, BN) || make_map(&bl, B.lo, K, Nc, B.ld, BN))
+        return -1;
+    using Cfg = TcCfg<BN>;
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_tc_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM) !=
+            cudaSuccess)
+            return -1;
+        attr = true;
+    }
+    dim3 grid((Nc + BN - 1) / BN, (Mr + 127) / 128, splits);
+    k_tc_gemm<BN><<<grid, 128, Cfg::SMEM, st>>>(ah, al, bh, bl, Mr, Nc, K, C, ldc, c_split_stride, err);
+    msd_note_launch();
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// TF32 rounding (round to nearest, ties away from zero) of an FP32 value.
+__device__ __forceinline__ float to_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void split3(double x, float& hi, float& lo)
+{
+    hi = to_tf32((float)x);
+    lo = to_tf32((float)(x - (double)hi));
+}
+
+// Rows of a complex FP64 matrix src[b][r][.] (b < nb, r < R) gathered at
+// columns cols[0..Kg) (all of [0, Kg) when cols is NULL) -> real rows
+// [(b, c, r)][Kp] (c = 0 real, 1 imaginary part), TF32 hi/lo, zero padded.
+__global__ void k_split_complex_rows(int nb, int R, int Kg, int Kp, const double2* __restrict__ src,
+                                     long long src_ld, const int* __restrict__ cols, float* __restrict__ hi,
+                                     float* __restrict__ lo)
+{
+    const long long total = (long long)nb * 2 * R * Kp;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(e % Kp);
+        const long long row = e / Kp;
+        const int r = (int)(row % R);
+        const int c = (int)((row / R) % 2);
+        const long long b = row / (2 * R);
+        double x = 0;
+        if (k < Kg) {
+            const double2 v = src[(b * R + r) * src_ld + (cols ? cols[k] : k)];
+            x = c ? v.y : v.x;
+        }
+        float h, l;
+        split3(x, h, l);
+        hi[e] = h;
+        lo[e] = l;
+    }
+}
+
+// Real FP64 rows src[r][.] gathered at cols[0..Kg) -> [R][Kp] hi/lo.
+__global__ void k_split_real_rows(long long R, int Kg, int Kp, const double* __restrict__ src, long long src_ld,
+                                  const int* __restrict__ cols, float* __restrict__ hi, float* __restrict__ lo)
+{
+    const long long total = R * Kp;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(e % Kp);
+        const long long r = e / Kp;
+        const double x = k < Kg ? src[r * src_ld + (cols ? cols[k] : k)] : 0.0;
+        float h, l;
+        split3(x, h, l);
+        hi[e] = h;
+        lo[e] = l;
+    }
+}
+
+// out[w][n] = add[n] + sum_z (C_z[2w][n], C_z[2w+1][n]) over the K splits, FP64.
+__global__ void k_pack_complex(int nw, int n, const float* __restrict__ C, long long ldc, int splits,
+                               long long split_stride, const double* __restrict__ add,
+                               double2* __restrict__ out, long long ldo)
+{
+    const long long total = (long long)nw * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long w = e / n;
+        const int j = (int)(e % n);
+        double re = add ? add[j] : 0.0, im = 0.0;
+        for (int z = 0; z < splits; ++z) {
+            re += C[z * split_stride + (2 * w) * ldc + j];
+            im += C[z * split_stride + (2 * w + 1) * ldc + j];
+        }
+        out[w * ldo + j] = make_double2(re, im);
+    }
+}
+
+int grid_for(long long n) { return (int)((n + 255) / 256 < 152 * 16 ? (n + 255) / 256 : 152 * 16); }
+
+}  // namespace
+
+int tc_gemm_3xtf32(const TcOperand& A, const TcOperand& B, int Mr, int Nc, int K, float* C, long long ldc,
+                   unsigned* err, cudaStream_t st, int splits, long long c_split_stride)
+{
+    if (K <= 0 || K % 32 || A.ld % 4 || B.ld % 4 || Mr <= 0 || Nc <= 0) return -1;
+    if (splits < 1 || splits > K / 32) return -1;
+    if (Nc >= 256) return launch_bn<256>(A, B, Mr, Nc, K, C, ldc, splits, c_split_stride, err, st);
+    return launch_bn<128>(A, B, Mr, Nc, K, C, ldc, splits, c_split_stride, err, st);
+}
+
+void launch_split_complex_rows(int nb, int R, int Kg, int Kp, const double2* src, long long src_ld,
+                               const int* cols, float* hi, float* lo, cudaStream_t st)
+{
+    if ((long long)nb * R * Kp <= 0) return;
+    k_split_complex_rows<<<grid_for((long long)nb * 2 * R * Kp), 256, 0, st>>>(nb, R, Kg, Kp, src, src_ld, cols,
+                                                                                hi, lo);
+    msd_note_launch();
+}
+
+void launch_split_real_rows(long long R, int Kg, int Kp, const double* src, long long src_ld, const int* cols,
+                            float* hi, float* lo, cudaStream_t st)
+{
+    if (R * Kp <= 0) return;
+    k_split_real_rows<<<grid_for(R * Kp), 256, 0, st>>>(R, Kg, Kp, src, src_ld, cols, hi, lo);
+    msd_note_launch();
+}
+
+void launch_pack_complex(int nw, int n, const float* C, long long ldc, int splits, long long split_stride,
+                         const double* add, double2* out, long long ldo, cudaStream_t st)
+{
+    if ((long long)nw * n <= 0) return;
+    k_pack_complex<<<grid_for((long long)nw * n), 256, 0, st>>>(nw, n, C, ldc, splits, split_stride, add, out, ldo);
+    msd_note_launch();
+}

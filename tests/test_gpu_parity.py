@@ -224,8 +224,88 @@ def test_walker_chunking_matches(msd):
     da, db = _cuda(w.phi_a), _cuda(w.phi_b)
     ctx = msd.Context(s, "fp64")
     e1, v1 = _np(ctx.local_energy(da, db)), _np(ctx.force_bias(da, db))
-    ctx.set_workspace_limit(64 << 20)               # forces several walker chunks
-    e2, v2 = _np(ctx.local_energy(da, db)), _np(ctx.force_bias(da, db))
+    ctx.set_workspace_limit(4 << 20)                # forces several walker chunks
+    e2 = _np(ctx.local_energy(da, db))
+    assert ctx.info("walker_chunk") < 24
+    v2 = _np(ctx.force_bias(da, db))
     assert ctx.info("walker_chunk") < 24
     assert np.allclose(e1, e2, rtol=1e-13, atol=0) and np.allclose(v1, v2, rtol=1e-13, atol=1e-15)
     ctx.close()
+
+
+# ------------------------------------------------------------ mixed mode
+# Mixed precision: the Cholesky contractions run as 3xTF32 on the tensor
+# cores with FP32 accumulation and the per-determinant energy terms in FP32;
+# the reference inverse, the minor determinants and the reductions stay
+# FP64. Stated bound (measured errors are 10-50x below it):
+#   |dE_L| <= 2e-6 * sum_I |c_I O_I E_I| / |O_T|  and  |dE_L| <= 1e-6 Ha,
+#   |dv_g| <= 1e-4 * max_g |v_g|,  overlaps and ratios as in FP64 mode.
+MIX_E_REL, MIX_E_ABS, MIX_V = 2e-6, 1e-6, 1e-4
+
+
+def _check_mixed(m, sys_, pa, pb, ref):
+    ctx = m.Context(sys_, "mixed")
+    da, db = _cuda(pa), _cuda(pb)
+    e, o = ctx.local_energy(da, db, ovlp=True)
+    e, o = _np(e), _np(o)
+    de = np.abs(e - ref["e_loc"])
+    assert np.all(de <= MIX_E_REL * ref["scale_e"]), np.max(de / ref["scale_e"])
+    assert np.all(de <= MIX_E_ABS), de.max()
+    assert np.all(np.abs(o - ref["ovlp"]) <= TOL * ref["scale_o"])
+    v = _np(ctx.force_bias(da, db))
+    dv = np.abs(v - ref["vbias"]).max(axis=1) / np.abs(ref["vbias"]).max(axis=1)
+    assert np.all(dv <= MIX_V), dv.max()
+    r = _np(ctx.det_ratios(da, db))
+    want_r = ref["det_ovlp"] / ref["det_ovlp"][:, :1]
+    assert np.all(np.abs(r - want_r) <= TOL * np.maximum(1, np.abs(want_r)))
+    ctx.close()
+
+
+def test_small_workload_mixed(msd):
+    s, w = synth.config_system("small", seed=0)
+    _check_mixed(msd, s, w.phi_a, w.phi_b, _ref(s, w.phi_a, w.phi_b))
+
+
+@pytest.mark.parametrize("M,na,nb,n_det,max_level,seed", [(12, 5, 4, 150, 4, 0), (13, 7, 6, 300, 12, 1)])
+def test_tiny_systems_mixed(msd, M, na, nb, n_det, max_level, seed):
+    s = tiny_system(seed, M, na, nb, n_chol=7, n_det=n_det, max_level=max_level)
+    pa, pb = tiny_walkers(seed, M, na, nb, n_w=3, noise=0.3)
+    # scale to the synthetic workloads' energy range (the bound is absolute in Ha)
+    s.L = s.L * 0.05
+    s.h1 = s.h1 * 0.05
+    s, pa, pb = _relabel(s, pa, pb, seed)
+    _check_mixed(msd, s, pa, pb, _ref(s, pa, pb))
+
+
+def test_cu2o2_shaped_mixed(msd):
+    s, w = synth.config_system("cu2o2", seed=0, n_w=2)
+    _check_mixed(msd, s, w.phi_a, w.phi_b, _ref(s, w.phi_a, w.phi_b))
+
+
+def test_fe2s2_shaped_subset_mixed(msd, fe2s2):
+    s, w = fe2s2
+    idx = np.concatenate([[0], np.sort(np.random.default_rng(6).choice(
+        np.arange(1, s.n_det), 299, replace=False))])
+    t = _subtrial(s, idx)
+    pa, pb = w.phi_a[:2], w.phi_b[:2]
+    _check_mixed(msd, t, pa, pb, _ref(t, pa, pb))
+
+
+def test_fe2s2_full_size_mixed_vs_fp64(msd, fe2s2):
+    """Full size, bench launch configuration (640 walkers, 1.2e5
+    determinants): mixed against the FP64 GPU path, which the tests above
+    tie to the oracle."""
+    s, w = fe2s2
+    da, db = _cuda(w.phi_a), _cuda(w.phi_b)
+    out = {}
+    for prec in ("fp64", "mixed"):
+        ctx = msd.Context(s, prec)
+        e, o = ctx.local_energy(da, db, ovlp=True)
+        v = ctx.force_bias(da, db)
+        out[prec] = (_np(e), _np(o), _np(v))
+        ctx.close()
+    (e64, o64, v64), (em, om, vm) = out["fp64"], out["mixed"]
+    assert np.all(np.abs(em - e64) <= MIX_E_ABS), np.abs(em - e64).max()
+    assert np.allclose(om, o64, rtol=1e-12, atol=0)
+    dv = np.abs(vm - v64).max(axis=1) / np.abs(v64).max(axis=1)
+    assert np.all(dv <= MIX_V), dv.max()
