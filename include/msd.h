@@ -140,6 +140,13 @@ int msd_force_bias(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi
 int msd_local_energy(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b,
                      double* e_loc, double* ovlp, void* stream);
 
+/* Overlap, force bias and local energy in one pass: the reference inverse,
+   the excitation-string minors and the CI weights are computed once and
+   shared. Outputs as in msd_overlap (ovlp), msd_force_bias (vbias) and
+   msd_local_energy (e_loc); any of them may be NULL, but not all. */
+int msd_evaluate(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b,
+                 double* ovlp, double* vbias, double* e_loc, void* stream);
+
 /* Introspection. Keys: */
 #define MSD_INFO_N_DET          1
 #define MSD_INFO_N_CHOL         2

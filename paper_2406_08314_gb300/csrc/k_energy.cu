@@ -337,12 +337,12 @@ k_string_energy(SpinTables tb, const double2* __restrict__ r, const double2* __r
         int hx[KL], px[KL];   // hole row offset h*np, particle index p
 #pragma unroll
         for (int i = 0; i < KL; ++i) { hx[i] = sh[i] * np; px[i] = sp[i]; }
-        const T2* B = reinterpret_cast<const T2*>(Bin) + (size_t)(tb.b_off[KL] + (long long)w * KL * KL * ns);
+        const T2* B = reinterpret_cast<const T2*>(Bin) + (size_t)tb.b_off[KL] + ((size_t)w * ns + sl) * (KL * KL);
         T2 b[KL][KL];
 #pragma unroll
         for (int i = 0; i < KL; ++i)
 #pragma unroll
-            for (int j = 0; j < KL; ++j) b[i][j] = B[(size_t)(i * KL + j) * ns + sl];
+            for (int j = 0; j < KL; ++j) b[i][j] = B[i * KL + j];
         T lr = 0, li = 0;      // linear part
         T qr = 0, qi = 0;      // Qc - Qx
 #pragma unroll 1
@@ -352,7 +352,7 @@ k_string_energy(SpinTables tb, const double2* __restrict__ r, const double2* __r
             for (int j = 0; j < KL; ++j) {
                 const int hj = sh[j] * np;
                 const int xij = hj + pi;
-                const T2 bij = B[(size_t)(i * KL + j) * ns + sl];
+                const T2 bij = B[i * KL + j];
                 const T2 y = ys[xij];
                 lr += bij.x * y.x - bij.y * y.y;
                 li += bij.x * y.y + bij.y * y.x;
@@ -474,13 +474,13 @@ k_pair_cross(SpinTables ta, SpinTables tbb, PairTables pt, int ka, int lo, int n
 #pragma unroll
             for (int l = 0; l < KB; ++l)
                 xb[k][l] = tbb.str_h[(size_t)b * MSD_KMAX + l] * tbb.np + tbb.str_p[(size_t)b * MSD_KMAX + k];
-        const T2* Ba = reinterpret_cast<const T2*>(Ba_in) + (size_t)(ta.b_off[ka] + (long long)w * ka * ka * nsa);
-        const T2* Bb = reinterpret_cast<const T2*>(Bb_in) + (size_t)(tbb.b_off[KB] + (long long)w * KB * KB * nsb);
+        const T2* Ba = reinterpret_cast<const T2*>(Ba_in) + (size_t)ta.b_off[ka] + ((size_t)w * nsa + sa) * (ka * ka);
+        const T2* Bb = reinterpret_cast<const T2*>(Bb_in) + (size_t)tbb.b_off[KB] + ((size_t)w * nsb + sb) * (KB * KB);
         T2 bb[KB][KB];
 #pragma unroll
         for (int k = 0; k < KB; ++k)
 #pragma unroll
-            for (int l = 0; l < KB; ++l) bb[k][l] = Bb[(size_t)(k * KB + l) * nsb + sb];
+            for (int l = 0; l < KB; ++l) bb[k][l] = Bb[k * KB + l];
         const uint8_t* ah = ta.str_h + (size_t)a * MSD_KMAX;
         const uint8_t* ap = ta.str_p + (size_t)a * MSD_KMAX;
         T xr = 0, xim = 0;
@@ -488,7 +488,7 @@ k_pair_cross(SpinTables ta, SpinTables tbb, PairTables pt, int ka, int lo, int n
         for (int i = 0; i < ka; ++i)
 #pragma unroll 1
             for (int j = 0; j < ka; ++j) {
-                const T2 ba = Ba[(size_t)(i * ka + j) * nsa + sa];
+                const T2 ba = Ba[i * ka + j];
                 const T2* krow = ks + (size_t)(ah[j] * ta.np + ap[i]) * Xb;
                 T zr = 0, zi = 0;
 #pragma unroll

@@ -2,6 +2,8 @@
 // part of the generalized-Wick evaluation (Sec. III "Implementation":
 // get_dets), plus the cofactor accumulation behind the mixed Green's
 // function (reduce_CI) and its rank-n_p update.
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -127,17 +129,19 @@ void launch_ref(const double2* phi, int nw, int M, int N, const SpinTables& T, d
 
 // ------------------------------------------------------------------------
 // Excitation strings of level K for one spin (get_dets / build_det_matrix):
-// A[i][j] = G[h_i][p_j] (a K x K minor of G), pivoted LU in FP64 gives
-// r = sign * det A, the overlap ratio <D_s|phi>/<D_0|phi> of the string's
-// spin sector; B = A^-1 (precision T: double in FP64 mode, float in mixed
-// mode) is stored for the Green's-function and energy terms.
-// One thread per (walker, string); the walker's active block lives in
-// shared memory.
+// A[i][j] = G[h_i][p_j] (a K x K minor of G). LU with partial pivoting in
+// FP64 gives r = sign * det A, the overlap ratio <D_s|phi>/<D_0|phi> of the
+// string's spin sector. B = A^-1 (precision T: double in FP64 mode, float
+// in mixed mode, solved from the LU factors with the pivot reciprocals) is
+// stored per string, K*K entries contiguous (B[i][j] at i*K + j), for the
+// Green's-function and energy terms. One thread per (walker, string); the
+// walker's active block lives in shared memory.
 template <int K, typename T>
 __global__ void __launch_bounds__(128)
 k_strings(SpinTables tb, int nw, const double2* __restrict__ Gact, double2* __restrict__ r,
           void* __restrict__ Bout, int want_b)
 {
+    using T2 = typename std::conditional<std::is_same<T, float>::value, float2, double2>::type;
     __shared__ double2 g[MSD_XMAX];
     const int w = blockIdx.y;
     const int X = tb.nh * tb.np;
@@ -147,26 +151,27 @@ k_strings(SpinTables tb, int nw, const double2* __restrict__ Gact, double2* __re
     const int sl = blockIdx.x * blockDim.x + threadIdx.x;
     if (sl >= ns) return;
     const int s = tb.bucket[K] + sl;
-    int hh[K], pp[K];
-#pragma unroll
-    for (int i = 0; i < K; ++i) { hh[i] = tb.str_h[(size_t)s * MSD_KMAX + i]; pp[i] = tb.str_p[(size_t)s * MSD_KMAX + i]; }
+    const uint8_t* sh = tb.str_h + (size_t)s * MSD_KMAX;
+    const uint8_t* sp = tb.str_p + (size_t)s * MSD_KMAX;
     double2 a[K][K];
 #pragma unroll
     for (int i = 0; i < K; ++i)
 #pragma unroll
-        for (int j = 0; j < K; ++j) a[i][j] = g[hh[i] * tb.np + pp[j]];
+        for (int j = 0; j < K; ++j) a[i][j] = g[sh[i] * tb.np + sp[j]];
     int perm[K];
 #pragma unroll
     for (int i = 0; i < K; ++i) perm[i] = i;
     double2 det = cz(tb.str_sign[s], 0);
+    double2 dinv[K];
     bool sing = false;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
+        // pivot: largest |re| + |im| in column k
         int p = k;
-        double best = a[k][k].x * a[k][k].x + a[k][k].y * a[k][k].y;
+        double best = fabs(a[k][k].x) + fabs(a[k][k].y);
 #pragma unroll
         for (int i = k + 1; i < K; ++i) {
-            double v = a[i][k].x * a[i][k].x + a[i][k].y * a[i][k].y;
+            const double v = fabs(a[i][k].x) + fabs(a[i][k].y);
             if (v > best) { best = v; p = i; }
         }
         if (best == 0.0) sing = true;
@@ -180,43 +185,53 @@ k_strings(SpinTables tb, int nw, const double2* __restrict__ Gact, double2* __re
             }
         }
         det = cmul(det, a[k][k]);
-        if (!sing) {
-            const double2 inv = cdiv(cz(1, 0), a[k][k]);
+        const double m2 = a[k][k].x * a[k][k].x + a[k][k].y * a[k][k].y;
+        const double im2 = sing ? 0.0 : 1.0 / m2;
+        dinv[k] = cz(a[k][k].x * im2, -a[k][k].y * im2);
 #pragma unroll
-            for (int i = k + 1; i < K; ++i) {
-                const double2 f = cmul(a[i][k], inv);
-                a[i][k] = f;
+        for (int i = k + 1; i < K; ++i) {
+            const double2 f = cmul(a[i][k], dinv[k]);
+            a[i][k] = f;
 #pragma unroll
-                for (int j = k + 1; j < K; ++j) a[i][j] = cfms(f, a[k][j], a[i][j]);
-            }
+            for (int j = k + 1; j < K; ++j) a[i][j] = cfms(f, a[k][j], a[i][j]);
         }
     }
     if (sing) det = cz(0, 0);
     r[(size_t)w * tb.n_str + s] = det;
     if (!want_b) return;
-    // B = A^-1 from P A = L U: column c solves L U x = P e_c.
-    T* B = reinterpret_cast<T*>(Bout) + 2 * (size_t)(tb.b_off[K] + (long long)w * K * K * ns);
+    // B = A^-1 from P A = L U: column c solves L U x = P e_c, in precision T.
+    T2 lu[K][K], di[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        di[i] = T2{(T)dinv[i].x, (T)dinv[i].y};
+#pragma unroll
+        for (int j = 0; j < K; ++j) lu[i][j] = T2{(T)a[i][j].x, (T)a[i][j].y};
+    }
+    T2* B = reinterpret_cast<T2*>(Bout) + (size_t)tb.b_off[K] + ((size_t)w * ns + sl) * (K * K);
 #pragma unroll
     for (int c = 0; c < K; ++c) {
-        double2 x[K];
+        T2 x[K];
 #pragma unroll
-        for (int i = 0; i < K; ++i) x[i] = cz(perm[i] == c ? 1 : 0, 0);
+        for (int i = 0; i < K; ++i) x[i] = T2{(T)(perm[i] == c ? 1 : 0), (T)0};
 #pragma unroll
         for (int i = 0; i < K; ++i)
 #pragma unroll
-            for (int k = 0; k < i; ++k) x[i] = cfms(a[i][k], x[k], x[i]);
+            for (int k = 0; k < i; ++k) {
+                x[i].x -= lu[i][k].x * x[k].x - lu[i][k].y * x[k].y;
+                x[i].y -= lu[i][k].x * x[k].y + lu[i][k].y * x[k].x;
+            }
 #pragma unroll
         for (int i = K - 1; i >= 0; --i) {
 #pragma unroll
-            for (int k = i + 1; k < K; ++k) x[i] = cfms(a[i][k], x[k], x[i]);
-            x[i] = sing ? cz(0, 0) : cdiv(x[i], a[i][i]);
+            for (int k = i + 1; k < K; ++k) {
+                x[i].x -= lu[i][k].x * x[k].x - lu[i][k].y * x[k].y;
+                x[i].y -= lu[i][k].x * x[k].y + lu[i][k].y * x[k].x;
+            }
+            const T2 t = x[i];
+            x[i] = T2{t.x * di[i].x - t.y * di[i].y, t.x * di[i].y + t.y * di[i].x};
         }
 #pragma unroll
-        for (int i = 0; i < K; ++i) {
-            const size_t e = (size_t)(i * K + c) * ns + sl;
-            B[2 * e] = (T)x[i].x;
-            B[2 * e + 1] = (T)x[i].y;
-        }
+        for (int i = 0; i < K; ++i) B[i * K + c] = x[i];
     }
 }
 
@@ -340,44 +355,76 @@ void launch_sum_slots(int nw, const double2* part, int nslot, int slot0, int n, 
 // ------------------------------------------------------------------------
 // Cofactor accumulation (reduce_CI): per (walker, spin)
 //   Cm[p][h] = sum_s w_s r_s B_s[i][j]  at (p_i, h_j),
-// so that G_T - G = (E_P - G[:, P]) Cm G[H, :] / R. Shared-memory
-// accumulation per walker replaces global atomics.
+// so that G_T - G = (E_P - G[:, P]) Cm G[H, :] / R. Each block takes a chunk
+// of strings of one walker and accumulates into warp-private shared copies
+// (few collisions, no global atomics); a second pass sums the chunks in a
+// fixed order. Accumulation precision T (double in FP64 mode, float in
+// mixed mode).
+#define CMAT_CHUNK 1024
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_cmat(SpinTables tb, const double2* __restrict__ r, const double2* __restrict__ wts,
-       const void* __restrict__ Bin, double2* __restrict__ Cm)
+       const void* __restrict__ Bin, double2* __restrict__ Cpart, int nchunk)
 {
-    __shared__ double acc[2 * MSD_XMAX];
-    const int w = blockIdx.x;
+    __shared__ T acc[8][2 * MSD_XMAX];
+    const int w = blockIdx.y, chunk = blockIdx.x;
     const int X = tb.nh * tb.np;
-    for (int e = threadIdx.x; e < 2 * X; e += blockDim.x) acc[e] = 0;
+    const int warp = threadIdx.x >> 5;
+    for (int e = threadIdx.x; e < 8 * 2 * MSD_XMAX; e += blockDim.x) (&acc[0][0])[e] = 0;
     __syncthreads();
     const T* Bb = reinterpret_cast<const T*>(Bin);
-    for (int s = tb.bucket[1] + threadIdx.x; s < tb.n_str; s += blockDim.x) {
+    const int s0 = max(tb.bucket[1], chunk * CMAT_CHUNK);
+    const int s1 = min(tb.n_str, (chunk + 1) * CMAT_CHUNK);
+    for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
         int k = 1;
         while (s >= tb.bucket[k + 1]) ++k;
         const int ns = tb.bucket[k + 1] - tb.bucket[k], sl = s - tb.bucket[k];
         const double2 f = cmul(r[(size_t)w * tb.n_str + s], wts[(size_t)w * tb.n_str + s]);
-        const T* B = Bb + 2 * (size_t)(tb.b_off[k] + (long long)w * k * k * ns);
-        for (int i = 0; i < k; ++i)
+        const T fr = (T)f.x, fi = (T)f.y;
+        const T* B = Bb + 2 * ((size_t)tb.b_off[k] + ((size_t)w * ns + sl) * (k * k));
+        const uint8_t* sh = tb.str_h + (size_t)s * MSD_KMAX;
+        const uint8_t* sp = tb.str_p + (size_t)s * MSD_KMAX;
+        for (int i = 0; i < k; ++i) {
+            const int row = sp[i] * tb.nh;
             for (int j = 0; j < k; ++j) {
-                const size_t e = (size_t)(i * k + j) * ns + sl;
-                const double2 b = cz((double)B[2 * e], (double)B[2 * e + 1]);
-                const double2 v = cmul(f, b);
-                const int pi = tb.str_p[(size_t)s * MSD_KMAX + i], hj = tb.str_h[(size_t)s * MSD_KMAX + j];
-                atomicAdd(&acc[2 * (pi * tb.nh + hj)], v.x);
-                atomicAdd(&acc[2 * (pi * tb.nh + hj) + 1], v.y);
+                const T br = B[2 * (i * k + j)], bi = B[2 * (i * k + j) + 1];
+                const int x = row + sh[j];
+                atomicAdd(&acc[warp][2 * x], fr * br - fi * bi);
+                atomicAdd(&acc[warp][2 * x + 1], fr * bi + fi * br);
             }
+        }
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < X; e += blockDim.x) Cm[(size_t)w * X + e] = cz(acc[2 * e], acc[2 * e + 1]);
+    for (int x = threadIdx.x; x < X; x += blockDim.x) {
+        double re = 0, im = 0;
+        for (int q = 0; q < 8; ++q) { re += (double)acc[q][2 * x]; im += (double)acc[q][2 * x + 1]; }
+        Cpart[((size_t)w * nchunk + chunk) * X + x] = cz(re, im);
+    }
 }
 
-void launch_cmat(const SpinTables& tb, int nw, const double2* r, const double2* wts, const void* B,
-                 bool fp32, double2* Cm, cudaStream_t st)
+__global__ void k_cmat_reduce(int nw, int X, int nchunk, const double2* __restrict__ Cpart, double2* __restrict__ Cm)
 {
-    if (fp32) k_cmat<float><<<nw, 256, 0, st>>>(tb, r, wts, B, Cm);
-    else k_cmat<double><<<nw, 256, 0, st>>>(tb, r, wts, B, Cm);
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nw * X) return;
+    const int w = e / X, x = e % X;
+    double2 a = cz(0, 0);
+    for (int c = 0; c < nchunk; ++c) a = cadd(a, Cpart[((size_t)w * nchunk + c) * X + x]);
+    Cm[e] = a;
+}
+
+int cmat_chunks(const SpinTables& tb) { return (tb.n_str + CMAT_CHUNK - 1) / CMAT_CHUNK; }
+
+void launch_cmat(const SpinTables& tb, int nw, const double2* r, const double2* wts, const void* B,
+                 bool fp32, double2* Cpart, double2* Cm, cudaStream_t st)
+{
+    const int X = tb.nh * tb.np;
+    if (X <= 0) return;
+    const int nchunk = cmat_chunks(tb);
+    dim3 grid(nchunk, nw);
+    if (fp32) k_cmat<float><<<grid, 256, 0, st>>>(tb, r, wts, B, Cpart, nchunk);
+    else k_cmat<double><<<grid, 256, 0, st>>>(tb, r, wts, B, Cpart, nchunk);
+    msd_note_launch();
+    k_cmat_reduce<<<(nw * X + 255) / 256, 256, 0, st>>>(nw, X, nchunk, Cpart, Cm);
     msd_note_launch();
 }
 

@@ -638,6 +638,301 @@ int begin_call(msd_ctx* ctx, int n_w, const double* pa, const double* pb, cudaSt
     return MSD_OK;
 }
 
+
+// ------------------------------------------------------------------ parts
+// Force-bias part for one chunk: cofactor matrix, G_T rows, contraction
+// with the half-rotated Cholesky vectors.
+struct FbWork {
+    void *GT = nullptr, *Rs = nullptr, *Cm[2] = {nullptr, nullptr}, *Cpart = nullptr;
+    void *Ah = nullptr, *Al = nullptr, *C32 = nullptr;
+    int ks = 1;
+};
+
+size_t fb_bytes_per_walker(msd_ctx* ctx, bool fp32)
+{
+    size_t b = sizeof(double2) * (ctx->Kd + 1);
+    for (int s = 0; s < 2; ++s) {
+        const SpinTables t = tables(ctx->sp[s], 1);
+        b += sizeof(double2) * (size_t)t.nh * t.np * (1 + cmat_chunks(t));
+    }
+    if (fp32) b += sizeof(float) * 2 * 2 * ctx->Kdp + sizeof(float) * 16 * 2 * ctx->n_chol;
+    return b;
+}
+
+int fb_alloc(msd_ctx* ctx, int cap, bool fp32, FbWork& f)
+{
+    int rc;
+    if ((rc = arena_get(ctx, "GT", sizeof(double2) * cap * ctx->Kd, &f.GT))) return rc;
+    if ((rc = arena_get(ctx, "Rsum", sizeof(double2) * cap, &f.Rs))) return rc;
+    size_t cp = 1;
+    for (int s = 0; s < 2; ++s) {
+        const SpinTables t = tables(ctx->sp[s], 1);
+        static const char* nm[2] = {"Cm_a", "Cm_b"};
+        if ((rc = arena_get(ctx, nm[s], sizeof(double2) * cap * std::max(1, t.nh * t.np), &f.Cm[s]))) return rc;
+        cp = std::max(cp, (size_t)cap * std::max(1, t.nh * t.np) * cmat_chunks(t));
+    }
+    if ((rc = arena_get(ctx, "Cpart", sizeof(double2) * cp, &f.Cpart))) return rc;
+    if (fp32) {
+        f.ks = std::max(1, std::min(16, (int)(ctx->Kdp / 32 / 64)));
+        if ((rc = arena_get(ctx, "Av_hi", sizeof(float) * 2 * cap * ctx->Kdp, &f.Ah))) return rc;
+        if ((rc = arena_get(ctx, "Av_lo", sizeof(float) * 2 * cap * ctx->Kdp, &f.Al))) return rc;
+        if ((rc = arena_get(ctx, "Cv32", sizeof(float) * f.ks * 2 * cap * ctx->n_chol, &f.C32))) return rc;
+    }
+    return MSD_OK;
+}
+
+int fb_chunk(msd_ctx* ctx, Chunk& c, FbWork& f, int w0, int nw, int cap, bool fp32, double2* vb_out,
+             double2* ov_out, cudaStream_t st)
+{
+    const TimerHook& th = ctx->hook;
+    int rc;
+    th.begin("k_sum_slots", st);
+    launch_sum_slots(nw, c.part, c.nslot, 0, c.nR, (double2*)f.Rs, c.O0[0], c.O0[1],
+                     ov_out ? ov_out + w0 : nullptr, st);
+    th.end(st);
+    long long off = 0;
+    for (int s = 0; s < 2; ++s) {
+        const SpinTables T = tables(ctx->sp[s], cap);
+        th.begin("k_cmat", st);
+        launch_cmat(T, nw, c.r[s], c.wts[s], c.B[s], fp32, (double2*)f.Cpart, (double2*)f.Cm[s], st);
+        th.end(st);
+        th.begin("k_gt", st);
+        launch_gt(T, nw, ctx->M, c.Gr[s], (double2*)f.Cm[s], (double2*)f.Rs, (double2*)f.GT, ctx->Kd, off, fp32,
+                  st);
+        th.end(st);
+        off += (long long)(T.N + T.np) * ctx->M;
+    }
+    CKLAUNCH();
+    double2* out = vb_out + (size_t)w0 * ctx->n_chol;
+    if (fp32) {
+        // vbias = c0_a + c0_b + (GT - D0 D0^T) . Lcat^T, the contraction on the
+        // tensor cores (3xTF32, rows (w, re/im), K split over CTAs, the splits
+        // summed in FP64)
+        th.begin("k_split_vbias", st);
+        launch_split_complex_rows(nw, 1, (int)ctx->Kd, (int)ctx->Kdp, (const double2*)f.GT, ctx->Kd, nullptr,
+                                  (float*)f.Ah, (float*)f.Al, st);
+        th.end(st);
+        th.begin("tc_gemm_vbias", st);
+        const long long sstride = (long long)2 * nw * ctx->n_chol;
+        rc = tc_gemm_3xtf32({(float*)f.Ah, (float*)f.Al, ctx->Kdp}, {ctx->Lv_hi, ctx->Lv_lo, ctx->Kdp}, 2 * nw,
+                            ctx->n_chol, (int)ctx->Kdp, (float*)f.C32, ctx->n_chol, ctx->d_err, st, f.ks, sstride);
+        th.end(st);
+        if (rc) return fail(ctx, MSD_ERR_CUDA, "tensor-core GEMM launch failed (force bias)");
+        th.begin("k_pack_vbias", st);
+        launch_pack_complex(nw, ctx->n_chol, (float*)f.C32, ctx->n_chol, f.ks, sstride, ctx->d_c0sum, out,
+                            ctx->n_chol, st);
+        th.end(st);
+    } else {
+        th.begin("k_gemm_vbias", st);
+        launch_gemm_zd(nw, ctx->n_chol, (int)ctx->Kd, (const double2*)f.GT, ctx->Kd, ctx->d_Lcat, ctx->Kd, out,
+                       ctx->n_chol, st);
+        th.end(st);
+    }
+    CKLAUNCH();
+    return MSD_OK;
+}
+
+// Energy part for one chunk.
+struct EnWork {
+    void *F[2] = {nullptr, nullptr}, *F32 = nullptr, *Ah = nullptr, *Al = nullptr;
+    void *v0[2], *xx[2], *La[2], *Xi[2], *Lh1[2], *e1[2], *Y[2], *Kaa, *Kbb, *Kab, *scal;
+};
+
+int energy_slots(msd_ctx* ctx)
+{
+    return string_energy_slots(tables(ctx->sp[0], 1)) + string_energy_slots(tables(ctx->sp[1], 1)) +
+           pair_cross_slots(pair_tables(ctx->pairs));
+}
+
+size_t en_bytes_per_walker(msd_ctx* ctx, bool fp32)
+{
+    const int G = ctx->n_chol;
+    SpinTables T1[2] = {tables(ctx->sp[0], 1), tables(ctx->sp[1], 1)};
+    const int X[2] = {T1[0].nh * T1[0].np, T1[1].nh * T1[1].np};
+    size_t e = 8 + 2;
+    for (int s = 0; s < 2; ++s) e += (size_t)G * (2 + 2 * X[s]) + 3 * X[s] + 1;
+    e += (size_t)X[0] * X[0] + (size_t)X[1] * X[1] + (size_t)X[0] * X[1];
+    size_t b = e * sizeof(double2);
+    if (fp32) {
+        size_t f = 0, a = 0;
+        for (int s = 0; s < 2; ++s) {
+            f = std::max(f, sizeof(float) * 2 * T1[s].N * (size_t)G * (T1[s].N + T1[s].np));
+            a = std::max(a, sizeof(float) * 2 * 2 * T1[s].N * (size_t)ctx->Kvp[s]);
+        }
+        b += f + a;
+    } else {
+        for (int s = 0; s < 2; ++s) b += sizeof(double2) * T1[s].N * (size_t)G * (T1[s].N + T1[s].np);
+    }
+    return b;
+}
+
+int en_alloc(msd_ctx* ctx, int cap, bool fp32, EnWork& E)
+{
+    const int G = ctx->n_chol;
+    SpinTables T1[2] = {tables(ctx->sp[0], 1), tables(ctx->sp[1], 1)};
+    const int X[2] = {T1[0].nh * T1[0].np, T1[1].nh * T1[1].np};
+    const int NC[2] = {T1[0].N + T1[0].np, T1[1].N + T1[1].np};
+    int rc;
+    static const char* nm[2][8] = {{"F_a", "v0_a", "xx_a", "Lact_a", "Xic_a", "Lh1_a", "e1_a", "Y_a"},
+                                   {"F_b", "v0_b", "xx_b", "Lact_b", "Xic_b", "Lh1_b", "e1_b", "Y_b"}};
+    if (fp32) {
+        size_t f = 0, a = 0;
+        for (int s = 0; s < 2; ++s) {
+            f = std::max(f, sizeof(float) * 2 * T1[s].N * (size_t)G * NC[s]);
+            a = std::max(a, sizeof(float) * 2 * T1[s].N * (size_t)ctx->Kvp[s]);
+        }
+        if ((rc = arena_get(ctx, "F32", f * cap, &E.F32))) return rc;
+        if ((rc = arena_get(ctx, "AF_hi", a * cap, &E.Ah))) return rc;
+        if ((rc = arena_get(ctx, "AF_lo", a * cap, &E.Al))) return rc;
+    }
+    for (int s = 0; s < 2; ++s) {
+        const size_t xs = std::max(1, X[s]);
+        if (!fp32 && (rc = arena_get(ctx, nm[s][0], sizeof(double2) * cap * T1[s].N * (size_t)G * NC[s], &E.F[s])))
+            return rc;
+        if ((rc = arena_get(ctx, nm[s][1], sizeof(double2) * cap * (size_t)G, &E.v0[s]))) return rc;
+        if ((rc = arena_get(ctx, nm[s][2], sizeof(double2) * cap * (size_t)G, &E.xx[s]))) return rc;
+        if ((rc = arena_get(ctx, nm[s][3], sizeof(double2) * cap * (size_t)G * xs, &E.La[s]))) return rc;
+        if ((rc = arena_get(ctx, nm[s][4], sizeof(double2) * cap * (size_t)G * xs, &E.Xi[s]))) return rc;
+        if ((rc = arena_get(ctx, nm[s][5], sizeof(double2) * cap * xs, &E.Lh1[s]))) return rc;
+        if ((rc = arena_get(ctx, nm[s][6], sizeof(double2) * cap, &E.e1[s]))) return rc;
+        if ((rc = arena_get(ctx, nm[s][7], sizeof(double2) * cap * xs, &E.Y[s]))) return rc;
+    }
+    if ((rc = arena_get(ctx, "K_aa", sizeof(double2) * cap * std::max(1, X[0] * X[0]), &E.Kaa))) return rc;
+    if ((rc = arena_get(ctx, "K_bb", sizeof(double2) * cap * std::max(1, X[1] * X[1]), &E.Kbb))) return rc;
+    if ((rc = arena_get(ctx, "K_ab", sizeof(double2) * cap * std::max(1, X[0] * X[1]), &E.Kab))) return rc;
+    if ((rc = arena_get(ctx, "scal", sizeof(double2) * cap * 8, &E.scal))) return rc;
+    return MSD_OK;
+}
+
+int en_chunk(msd_ctx* ctx, Chunk& c, EnWork& E, int w0, int nw, int cap, bool fp32, double2* e_out,
+             double2* ov_out, cudaStream_t st)
+{
+    const int M = ctx->M, G = ctx->n_chol;
+    const TimerHook& th = ctx->hook;
+    SpinTables T[2] = {tables(ctx->sp[0], cap), tables(ctx->sp[1], cap)};
+    const int X[2] = {T[0].nh * T[0].np, T[1].nh * T[1].np};
+    const int NC[2] = {T[0].N + T[0].np, T[1].N + T[1].np};
+    for (int s = 0; s < 2; ++s) {
+        const int N = T[s].N;
+        if (fp32) {
+            th.begin("k_split_F", st);
+            launch_split_complex_rows(nw, N, M - N, ctx->Kvp[s], c.Gr[s], M, ctx->d_virt[s], (float*)E.Ah,
+                                      (float*)E.Al, st);
+            th.end(st);
+            th.begin("tc_gemm_F", st);
+            const int g = tc_gemm_3xtf32({(float*)E.Ah, (float*)E.Al, ctx->Kvp[s]},
+                                         {ctx->LhF_hi[s], ctx->LhF_lo[s], ctx->Kvp[s]}, 2 * nw * N, G * NC[s],
+                                         ctx->Kvp[s], (float*)E.F32, (long long)G * NC[s], ctx->d_err, st);
+            th.end(st);
+            if (g) return fail(ctx, MSD_ERR_CUDA, "tensor-core GEMM launch failed (energy)");
+            th.begin("k_fepi_f32", st);
+            launch_fepi_f32(T[s], nw, M, G, (float*)E.F32, (long long)G * NC[s], c.Gr[s], ctx->sp[s].d_Lh,
+                            ctx->d_c0[s], ctx->d_x0[s], (double2*)E.v0[s], (double2*)E.xx[s], (float2*)E.La[s],
+                            (float2*)E.Xi[s], st);
+            th.end(st);
+        } else {
+            th.begin("k_gemm_F", st);
+            launch_gemm_zd(nw * N, G * NC[s], M, c.Gr[s], M, ctx->sp[s].d_Lh, M, (double2*)E.F[s],
+                           (long long)G * NC[s], st);
+            th.end(st);
+            th.begin("k_fepi", st);
+            launch_fepi(T[s], nw, M, G, (double2*)E.F[s], (long long)G * NC[s], c.Gr[s], (double2*)E.v0[s],
+                        (double2*)E.xx[s], (double2*)E.La[s], (double2*)E.Xi[s], st);
+            th.end(st);
+        }
+        th.begin("k_onebody", st);
+        launch_onebody(T[s], nw, M, ctx->d_h1 + (size_t)s * M * M, c.Gr[s], (double2*)E.e1[s],
+                       (double2*)E.Lh1[s], st);
+        th.end(st);
+        CKLAUNCH();
+    }
+    th.begin("k_gamma_reduce", st);
+    for (int s = 0; s < 2; ++s) {
+        if (fp32)
+            launch_gamma_reduce_f32(nw, X[s], G, s, (double2*)E.v0[0], (double2*)E.v0[1], (double2*)E.xx[s],
+                                    (float2*)E.La[s], (float2*)E.Xi[s], (double2*)E.Lh1[s], (float2*)E.Y[s],
+                                    (double2*)E.scal, st);
+        else
+            launch_gamma_reduce(nw, X[s], G, s, (double2*)E.v0[0], (double2*)E.v0[1], (double2*)E.xx[s],
+                                (double2*)E.La[s], (double2*)E.Xi[s], (double2*)E.Lh1[s], E.Y[s], false,
+                                (double2*)E.scal, st);
+    }
+    th.end(st);
+    th.begin("k_gram", st);
+    if (fp32) {
+        launch_gram_f32(nw, X[0], X[0], G, (float2*)E.La[0], (float2*)E.La[0], (float2*)E.Kaa, st);
+        launch_gram_f32(nw, X[1], X[1], G, (float2*)E.La[1], (float2*)E.La[1], (float2*)E.Kbb, st);
+        launch_gram_f32(nw, X[0], X[1], G, (float2*)E.La[0], (float2*)E.La[1], (float2*)E.Kab, st);
+    } else {
+        launch_gram(nw, X[0], X[0], G, (double2*)E.La[0], (double2*)E.La[0], E.Kaa, false, st);
+        launch_gram(nw, X[1], X[1], G, (double2*)E.La[1], (double2*)E.La[1], E.Kbb, false, st);
+        launch_gram(nw, X[0], X[1], G, (double2*)E.La[0], (double2*)E.La[1], E.Kab, false, st);
+    }
+    th.end(st);
+    CKLAUNCH();
+    int slot = c.nR;
+    void* Kss[2] = {E.Kaa, E.Kbb};
+    th.begin("k_string_energy", st);
+    for (int s = 0; s < 2; ++s) {
+        launch_string_energy(T[s], nw, c.r[s], c.wts[s], c.B[s], Kss[s], E.Y[s], fp32, c.part, c.nslot, slot, st);
+        slot += string_energy_slots(T[s]);
+    }
+    th.end(st);
+    CKLAUNCH();
+    th.begin("k_pair_cross", st);
+    launch_pair_cross(T[0], T[1], pair_tables(ctx->pairs), nw, c.r[0], c.r[1], c.B[0], c.B[1], E.Kab, fp32, c.part,
+                      c.nslot, slot, st);
+    th.end(st);
+    CKLAUNCH();
+    th.begin("k_final", st);
+    launch_final(nw, c.part, c.nslot, c.nR, ctx->e0, (double2*)E.e1[0], (double2*)E.e1[1], (double2*)E.scal,
+                 c.O0[0], c.O0[1], e_out + w0, ov_out ? ov_out + w0 : nullptr, st);
+    th.end(st);
+    CKLAUNCH();
+    return MSD_OK;
+}
+
+// Overlap (always), force bias (vbias != NULL) and local energy (e_loc !=
+// NULL) of n_w walkers, sharing the reference inverse, string minors and
+// CI weights between the last two.
+int evaluate(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b, double* ovlp, double* vbias,
+             double* e_loc, void* stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = begin_call(ctx, n_w, phi_a, phi_b, st);
+    if (rc) return rc;
+    if (n_w == 0) return MSD_OK;
+    const bool fp32 = ctx->prec == MSD_MIXED;
+    if (fp32 && (rc = prepare_mixed(ctx, st))) return rc;
+    Staged in;
+    if ((rc = stage_inputs(ctx, n_w, phi_a, phi_b, st, in))) return rc;
+    Out o_v, o_e, o_ov;
+    if ((rc = stage_output(ctx, "out_vbias", vbias, (size_t)n_w * ctx->n_chol, o_v))) return rc;
+    if ((rc = stage_output(ctx, "out_eloc", e_loc, n_w, o_e))) return rc;
+    if ((rc = stage_output(ctx, "out_ovlp", ovlp, n_w, o_ov))) return rc;
+    const bool want_v = vbias != nullptr, want_e = e_loc != nullptr;
+    const int nR = weights_blocks(tables(ctx->sp[0], 1));
+    const int nslot = nR + (want_e ? energy_slots(ctx) : 0);
+    size_t per = overlap_bytes_per_walker(ctx, true, nslot);
+    if (want_v) per += fb_bytes_per_walker(ctx, fp32);
+    if (want_e) per += en_bytes_per_walker(ctx, fp32);
+    const int cap = chunk_for(ctx, per, n_w);
+    Chunk c;
+    if ((rc = chunk_alloc(ctx, cap, true, nslot, c))) return rc;
+    FbWork f;
+    EnWork E;
+    if (want_v && (rc = fb_alloc(ctx, cap, fp32, f))) return rc;
+    if (want_e && (rc = en_alloc(ctx, cap, fp32, E))) return rc;
+    for (int w0 = 0; w0 < n_w; w0 += cap) {
+        const int nw = std::min(cap, n_w - w0);
+        if ((rc = run_overlap_part(ctx, in, w0, nw, cap, c, true, fp32, st))) return rc;
+        if (want_v && (rc = fb_chunk(ctx, c, f, w0, nw, cap, fp32, o_v.dev, want_e ? nullptr : o_ov.dev, st)))
+            return rc;
+        if (want_e && (rc = en_chunk(ctx, c, E, w0, nw, cap, fp32, o_e.dev, o_ov.dev, st))) return rc;
+    }
+    return finish(ctx, st, {&o_v, &o_e, &o_ov}, in.host_any);
+}
+
 }  // namespace
 
 // ========================================================================
@@ -848,246 +1143,22 @@ int msd_det_ratios(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi
 int msd_force_bias(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b, double* vbias,
                    double* ovlp, void* stream)
 {
-    cudaStream_t st = (cudaStream_t)stream;
-    int rc = begin_call(ctx, n_w, phi_a, phi_b, st);
-    if (rc) return rc;
-    if (n_w == 0) return MSD_OK;
-    if (!vbias) return fail(ctx, MSD_ERR_ARG, "vbias is NULL");
-    const bool fp32 = ctx->prec == MSD_MIXED;
-    if (fp32 && (rc = prepare_mixed(ctx, st))) return rc;
-    Staged in;
-    if ((rc = stage_inputs(ctx, n_w, phi_a, phi_b, st, in))) return rc;
-    Out o_v, o_ov;
-    if ((rc = stage_output(ctx, "out_vbias", vbias, (size_t)n_w * ctx->n_chol, o_v))) return rc;
-    if ((rc = stage_output(ctx, "out_ovlp", ovlp, n_w, o_ov))) return rc;
-    const int nR = weights_blocks(tables(ctx->sp[0], 1));
-    size_t per = overlap_bytes_per_walker(ctx, true, nR);
-    per += sizeof(double2) * (ctx->Kd + 1 + ctx->sp[0].nh * ctx->sp[0].np + ctx->sp[1].nh * ctx->sp[1].np);
-    const int cap = chunk_for(ctx, per, n_w);
-    Chunk c;
-    if ((rc = chunk_alloc(ctx, cap, true, nR, c))) return rc;
-    void *GT, *Rs, *Cm[2];
-    if ((rc = arena_get(ctx, "GT", sizeof(double2) * cap * ctx->Kd, &GT))) return rc;
-    if ((rc = arena_get(ctx, "Rsum", sizeof(double2) * cap, &Rs))) return rc;
-    if ((rc = arena_get(ctx, "Cm_a", sizeof(double2) * cap * std::max(1, ctx->sp[0].nh * ctx->sp[0].np), &Cm[0]))) return rc;
-    if ((rc = arena_get(ctx, "Cm_b", sizeof(double2) * cap * std::max(1, ctx->sp[1].nh * ctx->sp[1].np), &Cm[1]))) return rc;
-    for (int w0 = 0; w0 < n_w; w0 += cap) {
-        const int nw = std::min(cap, n_w - w0);
-        if ((rc = run_overlap_part(ctx, in, w0, nw, cap, c, true, fp32, st))) return rc;
-        const TimerHook& th = ctx->hook;
-        th.begin("k_sum_slots", st);
-        launch_sum_slots(nw, c.part, c.nslot, 0, c.nR, (double2*)Rs, c.O0[0], c.O0[1],
-                         o_ov.dev ? o_ov.dev + w0 : nullptr, st);
-        th.end(st);
-        long long off = 0;
-        for (int s = 0; s < 2; ++s) {
-            const SpinTables T = tables(ctx->sp[s], cap);
-            th.begin("k_cmat", st);
-            launch_cmat(T, nw, c.r[s], c.wts[s], c.B[s], fp32, (double2*)Cm[s], st);
-            th.end(st);
-            th.begin("k_gt", st);
-            launch_gt(T, nw, ctx->M, c.Gr[s], (double2*)Cm[s], (double2*)Rs, (double2*)GT, ctx->Kd, off, fp32,
-                      st);
-            th.end(st);
-            off += (long long)(T.N + T.np) * ctx->M;
-        }
-        CKLAUNCH();
-        if (fp32) {
-            // vbias = c0_a + c0_b + (GT - D0 D0^T) . Lcat^T, the contraction on
-            // the tensor cores (3xTF32, rows (w, re/im), K split over CTAs and
-            // the splits summed in FP64)
-            const int ks = std::max(1, std::min(16, (int)(ctx->Kdp / 32 / 64)));
-            void *Ah, *Al, *C32;
-            if ((rc = arena_get(ctx, "Av_hi", sizeof(float) * 2 * cap * ctx->Kdp, &Ah))) return rc;
-            if ((rc = arena_get(ctx, "Av_lo", sizeof(float) * 2 * cap * ctx->Kdp, &Al))) return rc;
-            if ((rc = arena_get(ctx, "Cv32", sizeof(float) * ks * 2 * cap * ctx->n_chol, &C32))) return rc;
-            th.begin("k_split_vbias", st);
-            launch_split_complex_rows(nw, 1, (int)ctx->Kd, (int)ctx->Kdp, (const double2*)GT, ctx->Kd, nullptr,
-                                      (float*)Ah, (float*)Al, st);
-            th.end(st);
-            th.begin("tc_gemm_vbias", st);
-            const long long sstride = (long long)2 * nw * ctx->n_chol;
-            const int g = tc_gemm_3xtf32({(float*)Ah, (float*)Al, ctx->Kdp}, {ctx->Lv_hi, ctx->Lv_lo, ctx->Kdp},
-                                         2 * nw, ctx->n_chol, (int)ctx->Kdp, (float*)C32, ctx->n_chol,
-                                         ctx->d_err, st, ks, sstride);
-            th.end(st);
-            if (g) return fail(ctx, MSD_ERR_CUDA, "tensor-core GEMM launch failed (force bias)");
-            th.begin("k_pack_vbias", st);
-            launch_pack_complex(nw, ctx->n_chol, (float*)C32, ctx->n_chol, ks, sstride, ctx->d_c0sum,
-                                o_v.dev + (size_t)w0 * ctx->n_chol, ctx->n_chol, st);
-            th.end(st);
-        } else {
-            th.begin("k_gemm_vbias", st);
-            launch_gemm_zd(nw, ctx->n_chol, (int)ctx->Kd, (const double2*)GT, ctx->Kd, ctx->d_Lcat,
-                           ctx->Kd, o_v.dev + (size_t)w0 * ctx->n_chol, ctx->n_chol, st);
-            th.end(st);
-        }
-        CKLAUNCH();
-    }
-    return finish(ctx, st, {&o_v, &o_ov}, in.host_any);
+    if (ctx && n_w > 0 && !vbias) return fail(ctx, MSD_ERR_ARG, "vbias is NULL");
+    return evaluate(ctx, n_w, phi_a, phi_b, ovlp, vbias, nullptr, stream);
 }
 
 int msd_local_energy(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b, double* e_loc,
                      double* ovlp, void* stream)
 {
-    cudaStream_t st = (cudaStream_t)stream;
-    int rc = begin_call(ctx, n_w, phi_a, phi_b, st);
-    if (rc) return rc;
-    if (n_w == 0) return MSD_OK;
-    if (!e_loc) return fail(ctx, MSD_ERR_ARG, "e_loc is NULL");
-    const bool fp32 = ctx->prec == MSD_MIXED;
-    if (fp32 && (rc = prepare_mixed(ctx, st))) return rc;
-    const int M = ctx->M, G = ctx->n_chol;
-    Staged in;
-    if ((rc = stage_inputs(ctx, n_w, phi_a, phi_b, st, in))) return rc;
-    Out o_e, o_ov;
-    if ((rc = stage_output(ctx, "out_eloc", e_loc, n_w, o_e))) return rc;
-    if ((rc = stage_output(ctx, "out_ovlp", ovlp, n_w, o_ov))) return rc;
-    SpinTables T1[2] = {tables(ctx->sp[0], 1), tables(ctx->sp[1], 1)};
-    const int nR = weights_blocks(T1[0]);
-    const int nE = string_energy_slots(T1[0]) + string_energy_slots(T1[1]) +
-                   pair_cross_slots(pair_tables(ctx->pairs));
-    const int nslot = nR + nE;
-    const int X[2] = {T1[0].nh * T1[0].np, T1[1].nh * T1[1].np};
-    const int NC[2] = {T1[0].N + T1[0].np, T1[1].N + T1[1].np};
-    // per-walker footprint (complex units unless noted)
-    size_t per = overlap_bytes_per_walker(ctx, true, nslot);
-    size_t e_per = 8 + 2;
-    for (int s = 0; s < 2; ++s) e_per += (size_t)G * (2 + 2 * X[s]) + 3 * X[s] + 1;
-    e_per += (size_t)X[0] * X[0] + (size_t)X[1] * X[1] + (size_t)X[0] * X[1];
-    per += e_per * sizeof(double2);
-    size_t fbytes_per_walker;   // dense F buffer per walker
-    if (fp32) {
-        size_t f = 0, a = 0;
-        for (int s = 0; s < 2; ++s) {
-            f = std::max(f, sizeof(float) * 2 * T1[s].N * (size_t)G * NC[s]);
-            a = std::max(a, sizeof(float) * 2 * 2 * T1[s].N * (size_t)ctx->Kvp[s]);
-        }
-        fbytes_per_walker = f + a;
-    } else {
-        fbytes_per_walker = 0;
-        for (int s = 0; s < 2; ++s) fbytes_per_walker += sizeof(double2) * T1[s].N * (size_t)G * NC[s];
-    }
-    per += fbytes_per_walker;
-    const int cap = chunk_for(ctx, per, n_w);
-    Chunk c;
-    if ((rc = chunk_alloc(ctx, cap, true, nslot, c))) return rc;
-    void *F[2] = {nullptr, nullptr}, *F32 = nullptr, *Ah = nullptr, *Al = nullptr;
-    void *v0[2], *xx[2], *La[2], *Xi[2], *Lh1[2], *e1[2], *Y[2], *Kaa, *Kbb, *Kab, *scal;
-    static const char* nm[2][8] = {{"F_a", "v0_a", "xx_a", "Lact_a", "Xic_a", "Lh1_a", "e1_a", "Y_a"},
-                                   {"F_b", "v0_b", "xx_b", "Lact_b", "Xic_b", "Lh1_b", "e1_b", "Y_b"}};
-    if (fp32) {
-        size_t f = 0, a = 0;
-        for (int s = 0; s < 2; ++s) {
-            f = std::max(f, sizeof(float) * 2 * T1[s].N * (size_t)G * NC[s]);
-            a = std::max(a, sizeof(float) * 2 * T1[s].N * (size_t)ctx->Kvp[s]);
-        }
-        if ((rc = arena_get(ctx, "F32", f * cap, &F32))) return rc;
-        if ((rc = arena_get(ctx, "AF_hi", a * cap, &Ah))) return rc;
-        if ((rc = arena_get(ctx, "AF_lo", a * cap, &Al))) return rc;
-    }
-    for (int s = 0; s < 2; ++s) {
-        const size_t xs = std::max(1, X[s]);
-        if (!fp32 && (rc = arena_get(ctx, nm[s][0], sizeof(double2) * cap * T1[s].N * (size_t)G * NC[s], &F[s])))
-            return rc;
-        if ((rc = arena_get(ctx, nm[s][1], sizeof(double2) * cap * (size_t)G, &v0[s]))) return rc;
-        if ((rc = arena_get(ctx, nm[s][2], sizeof(double2) * cap * (size_t)G, &xx[s]))) return rc;
-        if ((rc = arena_get(ctx, nm[s][3], sizeof(double2) * cap * (size_t)G * xs, &La[s]))) return rc;
-        if ((rc = arena_get(ctx, nm[s][4], sizeof(double2) * cap * (size_t)G * xs, &Xi[s]))) return rc;
-        if ((rc = arena_get(ctx, nm[s][5], sizeof(double2) * cap * xs, &Lh1[s]))) return rc;
-        if ((rc = arena_get(ctx, nm[s][6], sizeof(double2) * cap, &e1[s]))) return rc;
-        if ((rc = arena_get(ctx, nm[s][7], sizeof(double2) * cap * xs, &Y[s]))) return rc;
-    }
-    if ((rc = arena_get(ctx, "K_aa", sizeof(double2) * cap * std::max(1, X[0] * X[0]), &Kaa))) return rc;
-    if ((rc = arena_get(ctx, "K_bb", sizeof(double2) * cap * std::max(1, X[1] * X[1]), &Kbb))) return rc;
-    if ((rc = arena_get(ctx, "K_ab", sizeof(double2) * cap * std::max(1, X[0] * X[1]), &Kab))) return rc;
-    if ((rc = arena_get(ctx, "scal", sizeof(double2) * cap * 8, &scal))) return rc;
-    const TimerHook& th = ctx->hook;
-    for (int w0 = 0; w0 < n_w; w0 += cap) {
-        const int nw = std::min(cap, n_w - w0);
-        if ((rc = run_overlap_part(ctx, in, w0, nw, cap, c, true, fp32, st))) return rc;
-        SpinTables T[2] = {tables(ctx->sp[0], cap), tables(ctx->sp[1], cap)};
-        for (int s = 0; s < 2; ++s) {
-            const int N = T[s].N;
-            if (fp32) {
-                th.begin("k_split_F", st);
-                const int Kv = M - N;
-                launch_split_complex_rows(nw, N, Kv, ctx->Kvp[s], c.Gr[s], M, ctx->d_virt[s], (float*)Ah,
-                                          (float*)Al, st);
-                th.end(st);
-                th.begin("tc_gemm_F", st);
-                const int g = tc_gemm_3xtf32({(float*)Ah, (float*)Al, ctx->Kvp[s]},
-                                             {ctx->LhF_hi[s], ctx->LhF_lo[s], ctx->Kvp[s]}, 2 * nw * N, G * NC[s],
-                                             ctx->Kvp[s], (float*)F32, (long long)G * NC[s], ctx->d_err, st);
-                th.end(st);
-                if (g) return fail(ctx, MSD_ERR_CUDA, "tensor-core GEMM launch failed (energy)");
-                th.begin("k_fepi_f32", st);
-                launch_fepi_f32(T[s], nw, M, G, (float*)F32, (long long)G * NC[s], c.Gr[s], ctx->sp[s].d_Lh,
-                                ctx->d_c0[s], ctx->d_x0[s], (double2*)v0[s], (double2*)xx[s], (float2*)La[s],
-                                (float2*)Xi[s], st);
-                th.end(st);
-            } else {
-                th.begin("k_gemm_F", st);
-                launch_gemm_zd(nw * N, G * NC[s], M, c.Gr[s], M, ctx->sp[s].d_Lh, M, (double2*)F[s],
-                               (long long)G * NC[s], st);
-                th.end(st);
-                th.begin("k_fepi", st);
-                launch_fepi(T[s], nw, M, G, (double2*)F[s], (long long)G * NC[s], c.Gr[s], (double2*)v0[s],
-                            (double2*)xx[s], (double2*)La[s], (double2*)Xi[s], st);
-                th.end(st);
-            }
-            th.begin("k_onebody", st);
-            launch_onebody(T[s], nw, M, ctx->d_h1 + (size_t)s * M * M, c.Gr[s], (double2*)e1[s],
-                           (double2*)Lh1[s], st);
-            th.end(st);
-            CKLAUNCH();
-        }
-        th.begin("k_gamma_reduce", st);
-        for (int s = 0; s < 2; ++s) {
-            if (fp32)
-                launch_gamma_reduce_f32(nw, X[s], G, s, (double2*)v0[0], (double2*)v0[1], (double2*)xx[s],
-                                        (float2*)La[s], (float2*)Xi[s], (double2*)Lh1[s], (float2*)Y[s],
-                                        (double2*)scal, st);
-            else
-                launch_gamma_reduce(nw, X[s], G, s, (double2*)v0[0], (double2*)v0[1], (double2*)xx[s],
-                                    (double2*)La[s], (double2*)Xi[s], (double2*)Lh1[s], Y[s], false,
-                                    (double2*)scal, st);
-        }
-        th.end(st);
-        th.begin("k_gram", st);
-        if (fp32) {
-            launch_gram_f32(nw, X[0], X[0], G, (float2*)La[0], (float2*)La[0], (float2*)Kaa, st);
-            launch_gram_f32(nw, X[1], X[1], G, (float2*)La[1], (float2*)La[1], (float2*)Kbb, st);
-            launch_gram_f32(nw, X[0], X[1], G, (float2*)La[0], (float2*)La[1], (float2*)Kab, st);
-        } else {
-            launch_gram(nw, X[0], X[0], G, (double2*)La[0], (double2*)La[0], Kaa, false, st);
-            launch_gram(nw, X[1], X[1], G, (double2*)La[1], (double2*)La[1], Kbb, false, st);
-            launch_gram(nw, X[0], X[1], G, (double2*)La[0], (double2*)La[1], Kab, false, st);
-        }
-        th.end(st);
-        CKLAUNCH();
-        int slot = nR;
-        void* Kss[2] = {Kaa, Kbb};
-        th.begin("k_string_energy", st);
-        for (int s = 0; s < 2; ++s) {
-            launch_string_energy(T[s], nw, c.r[s], c.wts[s], c.B[s], Kss[s], Y[s], fp32, c.part,
-                                 c.nslot, slot, st);
-            slot += string_energy_slots(T[s]);
-        }
-        th.end(st);
-        CKLAUNCH();
-        th.begin("k_pair_cross", st);
-        launch_pair_cross(T[0], T[1], pair_tables(ctx->pairs), nw, c.r[0], c.r[1], c.B[0], c.B[1],
-                          Kab, fp32, c.part, c.nslot, slot, st);
-        th.end(st);
-        CKLAUNCH();
-        th.begin("k_final", st);
-        launch_final(nw, c.part, c.nslot, c.nR, ctx->e0, (double2*)e1[0], (double2*)e1[1],
-                     (double2*)scal, c.O0[0], c.O0[1], o_e.dev + w0, o_ov.dev ? o_ov.dev + w0 : nullptr, st);
-        th.end(st);
-        CKLAUNCH();
-    }
-    return finish(ctx, st, {&o_e, &o_ov}, in.host_any);
+    if (ctx && n_w > 0 && !e_loc) return fail(ctx, MSD_ERR_ARG, "e_loc is NULL");
+    return evaluate(ctx, n_w, phi_a, phi_b, ovlp, nullptr, e_loc, stream);
+}
+
+int msd_evaluate(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b, double* ovlp,
+                 double* vbias, double* e_loc, void* stream)
+{
+    if (ctx && n_w > 0 && !ovlp && !vbias && !e_loc) return fail(ctx, MSD_ERR_ARG, "no output requested");
+    return evaluate(ctx, n_w, phi_a, phi_b, ovlp, vbias, e_loc, stream);
 }
 
 int msd_info(const msd_ctx* ctx, int key, long long* value)

@@ -231,9 +231,15 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
             tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
             if (row < Mr) {
                 float* dst = C + (size_t)row * ldc + n0 + c;
+                if (n0 + c + 16 <= Nc && ((uintptr_t)dst & 15) == 0) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i)
-                    if (n0 + c + i < Nc) dst[i] = v[i];
+                    for (int i = 0; i < 16; i += 4)
+                        *reinterpret_cast<float4*>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        if (n0 + c + i < Nc) dst[i] = v[i];
+                }
             }
         }
     } else if (threadIdx.x == 0) {

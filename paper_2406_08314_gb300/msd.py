@@ -21,7 +21,7 @@ _ERRORS = {-1: "MSD_ERR_ARG", -2: "MSD_ERR_SHAPE", -3: "MSD_ERR_CUDA", -4: "MSD_
            -5: "MSD_ERR_REF_SINGULAR", -6: "MSD_ERR_STATE", -7: "MSD_ERR_NOMEM"}
 EXPORTS = ["msd_create", "msd_destroy", "msd_last_error", "msd_set_hamiltonian", "msd_set_trial",
            "msd_set_precision", "msd_overlap", "msd_det_ratios", "msd_force_bias",
-           "msd_local_energy", "msd_info", "msd_set_timing", "msd_reset_stats",
+           "msd_local_energy", "msd_evaluate", "msd_info", "msd_set_timing", "msd_reset_stats",
            "msd_kernel_count", "msd_kernel_stat", "msd_set_workspace_limit", "msd_set_sync",
            "msd_launch_count"]
 INFO = {"n_det": 1, "n_chol": 2, "n_strings_a": 3, "n_strings_b": 4, "n_holes_a": 5,
@@ -52,6 +52,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.msd_set_precision.argtypes = [vp, ci]
     for f in ("msd_overlap", "msd_det_ratios", "msd_force_bias", "msd_local_energy"):
         getattr(lib, f).argtypes = [vp, ci, vp, vp, vp, vp, vp]
+    lib.msd_evaluate.argtypes = [vp, ci, vp, vp, vp, vp, vp, vp]
     lib.msd_info.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_longlong)]
     lib.msd_set_timing.argtypes = [vp, ci]
     lib.msd_reset_stats.argtypes = [vp]
@@ -202,6 +203,18 @@ class Context:
         self._check(_lib.msd_local_energy(self._h, n_w, _ptr(phi_a), _ptr(phi_b), _ptr(e), _ptr(o),
                                           self._stream(phi_a, stream)))
         return (e, o) if ovlp else e
+
+    def evaluate(self, phi_a, phi_b, stream=None, out=None):
+        """(ovlp, vbias, e_loc) in one pass; `out` may give the three
+        output arrays."""
+        n_w = self._walkers(phi_a, phi_b)
+        if out is None:
+            out = (self._alloc(phi_a, (n_w,)), self._alloc(phi_a, (n_w, self.n_chol)),
+                   self._alloc(phi_a, (n_w,)))
+        o, v, e = out
+        self._check(_lib.msd_evaluate(self._h, n_w, _ptr(phi_a), _ptr(phi_b), _ptr(o), _ptr(v), _ptr(e),
+                                      self._stream(phi_a, stream)))
+        return o, v, e
 
     # --------------------------------------------------------------- timing
     def set_timing(self, enable=True):

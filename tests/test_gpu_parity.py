@@ -66,6 +66,10 @@ def _check_all(m, sys_, pa, pb, ref, precision="fp64", tol=TOL, tol_e=None):
     te = (tol_e or tol) * ref["scale_e"]
     assert np.all(np.abs(e - ref["e_loc"]) <= te), np.max(np.abs(e - ref["e_loc"]) / ref["scale_e"])
     assert np.all(np.abs(_np(o2) - ref["ovlp"]) <= tol * ref["scale_o"])
+    # the combined entry point shares the overlap part; same results
+    o3, v3, e3 = (_np(x) for x in ctx.evaluate(da, db))
+    assert np.allclose(e3, e, rtol=1e-14, atol=0) and np.allclose(o3, ov, rtol=1e-14, atol=0)
+    assert np.allclose(v3, v, rtol=1e-13, atol=1e-15 * np.abs(v).max())
     ctx.close()
     return dict(e=e, v=v, ov=ov)
 
