@@ -199,8 +199,9 @@ def algorithmic_work(s, n_w):
     w = {}
     # reference inverse: LU + inverse + Theta product + active block, both spins
     w["k_ref"] = sum(8 * (4 / 3 * sp["N"] ** 3 + M * sp["N"] ** 2 + sp["X"] * sp["N"]) for sp in spins) * n_w
-    # string minors: LU (k^3/3) + inverse (k^3) complex MACs
-    w["k_strings"] = sum(float(np.sum(sp["lv"] * 8 * (4 / 3) * k ** 3)) for sp in spins) * n_w
+    # string minors: the FP64 part, LU with partial pivoting (k^3/3 complex
+    # MACs); the inverse from the factors runs in the working precision
+    w["k_strings"] = sum(float(np.sum(sp["lv"] * 8 * k ** 3 / 3)) for sp in spins) * n_w
     w["k_gemm_F"] = sum(4.0 * sp["N"] * M * G * sp["NC"] for sp in spins) * n_w
     w["k_fepi"] = sum(8.0 * (sp["N"] ** 2 + sp["N"] ** 2 * sp["np"] + sp["nh"] * sp["N"] * sp["np"]) * G
                       for sp in spins) * n_w

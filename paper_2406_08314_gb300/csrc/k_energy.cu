@@ -309,8 +309,10 @@ void launch_gram(int nw, int Xp, int Xq, int n_chol, const double2* P, const dou
 // arithmetic; the block sum is FP64. The outer (i, j) loop runs at run
 // time (its operands are read once); the inner (k, l) loop is unrolled over
 // the string's inverse minor held in registers.
+#define SE_THREADS 256
+#define SE_PER_THREAD 4
 template <int KL, typename T>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(SE_THREADS)
 k_string_energy(SpinTables tb, const double2* __restrict__ r, const double2* __restrict__ wts,
                 const void* __restrict__ Bin, const void* __restrict__ Kin, const void* __restrict__ Yin,
                 double2* __restrict__ part, int nslot, int slot0)
@@ -320,7 +322,7 @@ k_string_energy(SpinTables tb, const double2* __restrict__ r, const double2* __r
     const int X = tb.nh * tb.np, np = tb.np;
     T2* ks = reinterpret_cast<T2*>(smraw);   // [X][X]
     T2* ys = ks + X * X;                     // [X]
-    __shared__ double2 red[128];
+    __shared__ double2 red[SE_THREADS];
     const int w = blockIdx.y, t = threadIdx.x;
     const T2* Kw = reinterpret_cast<const T2*>(Kin) + (size_t)w * X * X;
     for (int e = t; e < X * X; e += blockDim.x) ks[e] = Kw[e];
@@ -328,9 +330,10 @@ k_string_energy(SpinTables tb, const double2* __restrict__ r, const double2* __r
     for (int e = t; e < X; e += blockDim.x) ys[e] = Yw[e];
     __syncthreads();
     const int ns = tb.bucket[KL + 1] - tb.bucket[KL];
-    const int sl = blockIdx.x * blockDim.x + t;
     double2 contrib = cz(0, 0);
-    if (sl < ns) {
+    for (int it = 0; it < SE_PER_THREAD; ++it) {
+        const int sl = blockIdx.x * (SE_THREADS * SE_PER_THREAD) + it * SE_THREADS + t;
+        if (sl >= ns) break;
         const int s = tb.bucket[KL] + sl;
         const uint8_t* sh = tb.str_h + (size_t)s * MSD_KMAX;
         const uint8_t* sp = tb.str_p + (size_t)s * MSD_KMAX;
@@ -377,11 +380,11 @@ k_string_energy(SpinTables tb, const double2* __restrict__ r, const double2* __r
         }
         const double2 e_s = cz((double)lr + 0.5 * (double)qr, (double)li + 0.5 * (double)qi);
         const double2 rw = cmul(r[(size_t)w * tb.n_str + s], wts[(size_t)w * tb.n_str + s]);
-        contrib = cmul(rw, e_s);
+        contrib = cadd(contrib, cmul(rw, e_s));
     }
     red[t] = contrib;
     __syncthreads();
-    for (int o = 64; o; o >>= 1) {
+    for (int o = SE_THREADS / 2; o; o >>= 1) {
         if (t < o) red[t] = cadd(red[t], red[t + o]);
         __syncthreads();
     }
@@ -391,7 +394,7 @@ k_string_energy(SpinTables tb, const double2* __restrict__ r, const double2* __r
 int string_energy_blocks(const SpinTables& tb, int k)
 {
     const int ns = tb.bucket[k + 1] - tb.bucket[k];
-    return ns > 0 ? (ns + 127) / 128 : 0;
+    return ns > 0 ? (ns + SE_THREADS * SE_PER_THREAD - 1) / (SE_THREADS * SE_PER_THREAD) : 0;
 }
 
 size_t string_energy_smem(const SpinTables& tb, bool fp32)
@@ -411,10 +414,10 @@ static void launch_se_k(const SpinTables& tb, int nw, const double2* r, const do
     const size_t smem = string_energy_smem(tb, fp32);
     if (fp32) {
         cudaFuncSetAttribute(k_string_energy<KL, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_string_energy<KL, float><<<grid, 128, smem, st>>>(tb, r, wts, B, K, Y, part, nslot, slot); msd_note_launch();
+        k_string_energy<KL, float><<<grid, SE_THREADS, smem, st>>>(tb, r, wts, B, K, Y, part, nslot, slot); msd_note_launch();
     } else {
         cudaFuncSetAttribute(k_string_energy<KL, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_string_energy<KL, double><<<grid, 128, smem, st>>>(tb, r, wts, B, K, Y, part, nslot, slot); msd_note_launch();
+        k_string_energy<KL, double><<<grid, SE_THREADS, smem, st>>>(tb, r, wts, B, K, Y, part, nslot, slot); msd_note_launch();
     }
     slot += nb;
 }
@@ -445,8 +448,10 @@ int string_energy_slots(const SpinTables& tb)
 //   X_ab = sum_ij Ba_ij sum_kl Bb_kl K^{ab}[(ha_j,pa_i)][(hb_l,pb_k)].
 // The beta level KB is a template parameter (its inverse minor is held in
 // registers); the alpha level runs at run time.
+#define PC_THREADS 256
+#define PC_PER_THREAD 8
 template <int KB, typename T>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(PC_THREADS)
 k_pair_cross(SpinTables ta, SpinTables tbb, PairTables pt, int ka, int lo, int n,
              const double2* __restrict__ ra, const double2* __restrict__ rb,
              const void* __restrict__ Ba_in, const void* __restrict__ Bb_in,
@@ -456,14 +461,17 @@ k_pair_cross(SpinTables ta, SpinTables tbb, PairTables pt, int ka, int lo, int n
     extern __shared__ __align__(16) unsigned char smraw[];
     const int Xa = ta.nh * ta.np, Xb = tbb.nh * tbb.np;
     T2* ks = reinterpret_cast<T2*>(smraw);   // [Xa][Xb]
-    __shared__ double2 red[128];
+    __shared__ double2 red[PC_THREADS];
     const int w = blockIdx.y, t = threadIdx.x;
     const T2* Kw = reinterpret_cast<const T2*>(Kin) + (size_t)w * Xa * Xb;
     for (int e = t; e < Xa * Xb; e += blockDim.x) ks[e] = Kw[e];
     __syncthreads();
-    const int i0 = blockIdx.x * blockDim.x + t;
     double2 contrib = cz(0, 0);
-    if (i0 < n) {
+    // the shared Gram matrix is filled once per block and reused by
+    // PC_PER_THREAD determinants per thread
+    for (int it = 0; it < PC_PER_THREAD; ++it) {
+        const int i0 = blockIdx.x * (PC_THREADS * PC_PER_THREAD) + it * PC_THREADS + t;
+        if (i0 >= n) break;
         const int I = lo + i0;
         const int a = pt.a[I], b = pt.b[I];
         const int nsa = ta.bucket[ka + 1] - ta.bucket[ka], sa = a - ta.bucket[ka];
@@ -503,11 +511,11 @@ k_pair_cross(SpinTables ta, SpinTables tbb, PairTables pt, int ka, int lo, int n
                 xim += ba.x * zi + ba.y * zr;
             }
         const double2 rr = cscale(cmul(ra[(size_t)w * ta.n_str + a], rb[(size_t)w * tbb.n_str + b]), pt.c[I]);
-        contrib = cmul(rr, cz((double)xr, (double)xim));
+        contrib = cadd(contrib, cmul(rr, cz((double)xr, (double)xim)));
     }
     red[t] = contrib;
     __syncthreads();
-    for (int o = 64; o; o >>= 1) {
+    for (int o = PC_THREADS / 2; o; o >>= 1) {
         if (t < o) red[t] = cadd(red[t], red[t + o]);
         __syncthreads();
     }
@@ -523,15 +531,15 @@ static void launch_pc_k(const SpinTables& ta, const SpinTables& tb, const PairTa
     const int idx = ka * (MSD_KMAX + 1) + KB;
     const int lo = pt.bucket[idx], n = pt.bucket[idx + 1] - lo;
     if (n <= 0) return;
-    const int nb = (n + 127) / 128;
+    const int nb = (n + PC_THREADS * PC_PER_THREAD - 1) / (PC_THREADS * PC_PER_THREAD);
     dim3 grid(nb, nw);
     const size_t smem = (fp32 ? sizeof(float2) : sizeof(double2)) * (size_t)(ta.nh * ta.np) * (tb.nh * tb.np);
     if (fp32) {
         cudaFuncSetAttribute(k_pair_cross<KB, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_pair_cross<KB, float><<<grid, 128, smem, st>>>(ta, tb, pt, ka, lo, n, ra, rb, Ba, Bb, K, part, nslot, slot); msd_note_launch();
+        k_pair_cross<KB, float><<<grid, PC_THREADS, smem, st>>>(ta, tb, pt, ka, lo, n, ra, rb, Ba, Bb, K, part, nslot, slot); msd_note_launch();
     } else {
         cudaFuncSetAttribute(k_pair_cross<KB, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_pair_cross<KB, double><<<grid, 128, smem, st>>>(ta, tb, pt, ka, lo, n, ra, rb, Ba, Bb, K, part, nslot, slot); msd_note_launch();
+        k_pair_cross<KB, double><<<grid, PC_THREADS, smem, st>>>(ta, tb, pt, ka, lo, n, ra, rb, Ba, Bb, K, part, nslot, slot); msd_note_launch();
     }
     slot += nb;
 }
@@ -559,7 +567,7 @@ int pair_cross_slots(const PairTables& pt)
         for (int kb = 1; kb <= MSD_KMAX; ++kb) {
             const int idx = ka * (MSD_KMAX + 1) + kb;
             const int c = pt.bucket[idx + 1] - pt.bucket[idx];
-            if (c > 0) n += (c + 127) / 128;
+            if (c > 0) n += (c + PC_THREADS * PC_PER_THREAD - 1) / (PC_THREADS * PC_PER_THREAD);
         }
     return n;
 }

@@ -16,7 +16,8 @@ __device__ __forceinline__ float2 fcfms(float2 b, float2 c, float2 a)
 }
 
 // F = F0 + dF with F[j][col] = (G L_g)[occ0_j][col] (col over occ0 then P):
-//   F0[j][col] = L_g[occ0_j][col]   (the reference part D0 D0^T, exact, from L)
+//   F0[j][col] = L_g[occ0_j][col]   (the reference part D0 D0^T, exact, from L;
+//                                    F0T[g][j][col], FP32)
 //   dF         real rows [(w, c, j)][g * NC + col] of the tensor-core GEMM over
 //              the columns outside occ0 (c = 0 real, 1 imaginary part).
 // With T = F[:, occ0] = T0 + dT:
@@ -24,9 +25,10 @@ __device__ __forceinline__ float2 fcfms(float2 b, float2 c, float2 a)
 //   x  = tr(T T) = x0_g + 2 tr(T0 dT) + tr(dT dT)     (c0, x0 in FP64)
 //   Lambda[j][p] = F[j][P_p] - sum_l T[j][l] G[occ0_l][P_p]
 //   Lact[(h,p)] = Lambda[pos(h)][p],  Xic[(h,p)] = sum_l T[pos(h)][l] Lambda[l][p]
+#define FEPI_G 4   // Cholesky vectors per block
 __global__ void __launch_bounds__(128)
 k_fepi_f32(SpinTables tb, int M, int n_chol, const float* __restrict__ dF, long long ldf,
-           const double2* __restrict__ Gr, const double* __restrict__ Lh, const double* __restrict__ c0,
+           const double2* __restrict__ Gr, const float* __restrict__ F0T, const double* __restrict__ c0,
            const double* __restrict__ x0, double2* __restrict__ v0, double2* __restrict__ xx,
            float2* __restrict__ Lact, float2* __restrict__ Xic)
 {
@@ -37,68 +39,73 @@ k_fepi_f32(SpinTables tb, int M, int n_chol, const float* __restrict__ dF, long 
     float2* lam = gp + N * np;       // [N][np]
     float* f0 = reinterpret_cast<float*>(lam + N * np);   // [N][NC] F0 (real)
     __shared__ float2 red[2][128];
-    const int g = blockIdx.x, w = blockIdx.y, t = threadIdx.x;
-    const float* Fre = dF + (size_t)w * 2 * N * ldf + (size_t)g * NC;
-    const float* Fim = Fre + (size_t)N * ldf;
-    const double* Lg = Lh + (size_t)g * NC * M;     // Lg[col][r] = L_g[col_orbital][r]
-    for (int e = t; e < N * NC; e += blockDim.x) {
-        const int j = e / NC, cc = e % NC;
-        const size_t o = (size_t)j * ldf + cc;
-        d[e] = make_float2(Fre[o], Fim[o]);
-        f0[e] = (float)Lg[(size_t)cc * M + tb.occ0[j]];
-    }
+    const int w = blockIdx.y, t = threadIdx.x;
     const double2* gr = Gr + (size_t)w * N * M;
     for (int e = t; e < N * np; e += blockDim.x) {
         const double2 v = gr[(size_t)(e / np) * M + tb.part_orb[e % np]];
         gp[e] = make_float2((float)v.x, (float)v.y);
     }
-    __syncthreads();
-    float2 a0 = make_float2(0, 0), a1 = make_float2(0, 0);
-    for (int e = t; e < N * N; e += blockDim.x) {
-        const int j = e / N, l = e % N;
-        const float2 dlj = d[l * NC + j];
-        // 2 T0[j][l] dT[l][j] + dT[j][l] dT[l][j]
-        a1 = fcfma(d[j * NC + l], dlj, a1);
-        a1.x += 2.f * f0[j * NC + l] * dlj.x;
-        a1.y += 2.f * f0[j * NC + l] * dlj.y;
-        if (j == l) { a0.x += d[j * NC + j].x; a0.y += d[j * NC + j].y; }
-    }
-    for (int e = t; e < N * np; e += blockDim.x) {
-        const int j = e / np, p = e % np;
-        float2 v = d[j * NC + N + p];
-        v.x += f0[j * NC + N + p];
-        for (int l = 0; l < N; ++l) {
-            float2 tjl = d[j * NC + l];
-            tjl.x += f0[j * NC + l];
-            v = fcfms(tjl, gp[l * np + p], v);
-        }
-        lam[e] = v;
-    }
-    red[0][t] = a0;
-    red[1][t] = a1;
-    __syncthreads();
-    for (int o = 64; o; o >>= 1) {
-        if (t < o) {
-            red[0][t].x += red[0][t + o].x; red[0][t].y += red[0][t + o].y;
-            red[1][t].x += red[1][t + o].x; red[1][t].y += red[1][t + o].y;
+    for (int gi = 0; gi < FEPI_G; ++gi) {
+        const int g = blockIdx.x * FEPI_G + gi;
+        if (g >= n_chol) break;
+        const float* Fre = dF + (size_t)w * 2 * N * ldf + (size_t)g * NC;
+        const float* Fim = Fre + (size_t)N * ldf;
+        const float* f0g = F0T + (size_t)g * N * NC;
+        __syncthreads();   // previous vector's shared data fully consumed
+        for (int e = t; e < N * NC; e += blockDim.x) {
+            const int j = e / NC, cc = e % NC;
+            const size_t o = (size_t)j * ldf + cc;
+            d[e] = make_float2(Fre[o], Fim[o]);
+            f0[e] = f0g[e];
         }
         __syncthreads();
-    }
-    const size_t wg = (size_t)w * n_chol + g;
-    if (t == 0) {
-        v0[wg] = make_double2(c0[g] + (double)red[0][0].x, (double)red[0][0].y);
-        xx[wg] = make_double2(x0[g] + (double)red[1][0].x, (double)red[1][0].y);
-    }
-    for (int e = t; e < X; e += blockDim.x) {
-        const int h = e / np, p = e % np, j = tb.hole_pos[h];
-        float2 xi = make_float2(0, 0);
-        for (int l = 0; l < N; ++l) {
-            float2 tjl = d[j * NC + l];
-            tjl.x += f0[j * NC + l];
-            xi = fcfma(tjl, lam[l * np + p], xi);
+        float2 a0 = make_float2(0, 0), a1 = make_float2(0, 0);
+        for (int e = t; e < N * N; e += blockDim.x) {
+            const int j = e / N, l = e % N;
+            const float2 dlj = d[l * NC + j];
+            // 2 T0[j][l] dT[l][j] + dT[j][l] dT[l][j]
+            a1 = fcfma(d[j * NC + l], dlj, a1);
+            a1.x += 2.f * f0[j * NC + l] * dlj.x;
+            a1.y += 2.f * f0[j * NC + l] * dlj.y;
+            if (j == l) { a0.x += d[j * NC + j].x; a0.y += d[j * NC + j].y; }
         }
-        Lact[wg * X + e] = lam[j * np + p];
-        Xic[wg * X + e] = xi;
+        for (int e = t; e < N * np; e += blockDim.x) {
+            const int j = e / np, p = e % np;
+            float2 v = d[j * NC + N + p];
+            v.x += f0[j * NC + N + p];
+            for (int l = 0; l < N; ++l) {
+                float2 tjl = d[j * NC + l];
+                tjl.x += f0[j * NC + l];
+                v = fcfms(tjl, gp[l * np + p], v);
+            }
+            lam[e] = v;
+        }
+        red[0][t] = a0;
+        red[1][t] = a1;
+        __syncthreads();
+        for (int o = 64; o; o >>= 1) {
+            if (t < o) {
+                red[0][t].x += red[0][t + o].x; red[0][t].y += red[0][t + o].y;
+                red[1][t].x += red[1][t + o].x; red[1][t].y += red[1][t + o].y;
+            }
+            __syncthreads();
+        }
+        const size_t wg = (size_t)w * n_chol + g;
+        if (t == 0) {
+            v0[wg] = make_double2(c0[g] + (double)red[0][0].x, (double)red[0][0].y);
+            xx[wg] = make_double2(x0[g] + (double)red[1][0].x, (double)red[1][0].y);
+        }
+        for (int e = t; e < X; e += blockDim.x) {
+            const int h = e / np, p = e % np, j = tb.hole_pos[h];
+            float2 xi = make_float2(0, 0);
+            for (int l = 0; l < N; ++l) {
+                float2 tjl = d[j * NC + l];
+                tjl.x += f0[j * NC + l];
+                xi = fcfma(tjl, lam[l * np + p], xi);
+            }
+            Lact[wg * X + e] = lam[j * np + p];
+            Xic[wg * X + e] = xi;
+        }
     }
 }
 
@@ -109,27 +116,29 @@ size_t fepi_f32_smem(const SpinTables& tb)
 }
 
 void launch_fepi_f32(const SpinTables& tb, int nw, int M, int n_chol, const float* dF, long long ldf,
-                     const double2* Gr, const double* Lh, const double* c0, const double* x0, double2* v0,
+                     const double2* Gr, const float* F0T, const double* c0, const double* x0, double2* v0,
                      double2* xx, float2* Lact, float2* Xic, cudaStream_t st)
 {
-    dim3 grid(n_chol, nw);
+    dim3 grid((n_chol + FEPI_G - 1) / FEPI_G, nw);
     const size_t smem = fepi_f32_smem(tb);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_fepi_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_fepi_f32<<<grid, 128, smem, st>>>(tb, M, n_chol, dF, ldf, Gr, Lh, c0, x0, v0, xx, Lact, Xic);
+    k_fepi_f32<<<grid, 128, smem, st>>>(tb, M, n_chol, dF, ldf, Gr, F0T, c0, x0, v0, xx, Lact, Xic);
     msd_note_launch();
 }
 
-// Y[x] = Lh[x] + sum_g V0_g Lact_g[x] - sum_g Xic_g[x] (FP32 sums of FP32
-// terms, V0 in FP64), and the FP64 scalar sums of the FP64 kernel.
-__global__ void __launch_bounds__(128)
+// Y[x] = Lh[x] + sum_g V0_g Lact_g[x] - sum_g Xic_g[x] (FP32 terms, V0 in
+// FP64), and the FP64 scalar sums of the FP64 kernel. Warps split the
+// Cholesky vectors, lanes the active entries; the warp sums are added in a
+// fixed order.
+__global__ void __launch_bounds__(256)
 k_gamma_reduce_f32(int X, int n_chol, int spin, const double2* __restrict__ v0a,
                    const double2* __restrict__ v0b, const double2* __restrict__ xx,
                    const float2* __restrict__ Lact, const float2* __restrict__ Xic,
                    const double2* __restrict__ Lh, float2* __restrict__ Y, double2* __restrict__ scal)
 {
-    __shared__ double2 red[2][128];
-    __shared__ float2 V0s[1024];
-    const int w = blockIdx.x, t = threadIdx.x;
+    __shared__ float2 part[8][MSD_XMAX];
+    __shared__ double2 red[2][256];
+    const int w = blockIdx.x, t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const size_t base = (size_t)w * n_chol;
     double2 s0 = cz(0, 0), s1 = cz(0, 0);
     for (int g = t; g < n_chol; g += blockDim.x) {
@@ -137,35 +146,39 @@ k_gamma_reduce_f32(int X, int n_chol, int spin, const double2* __restrict__ v0a,
         const double2 V0 = cadd(v0a[base + g], v0b[base + g]);
         s1 = cfma(V0, V0, s1);
     }
-    // one x per thread (X <= MSD_XMAX <= blockDim); every thread takes part
-    // in the staging barriers
-    const bool active = t < X;
-    float2 y = make_float2(0, 0);
-    if (active) {
-        const double2 l = Lh[(size_t)w * X + t];
-        y = make_float2((float)l.x, (float)l.y);
-    }
-    for (int g0 = 0; g0 < n_chol; g0 += 1024) {
-        const int gn = min(1024, n_chol - g0);
-        __syncthreads();
-        for (int g = t; g < gn; g += blockDim.x) {
-            const double2 V0 = cadd(v0a[base + g0 + g], v0b[base + g0 + g]);
-            V0s[g] = make_float2((float)V0.x, (float)V0.y);
-        }
-        __syncthreads();
-        if (active)
-            for (int g = 0; g < gn; ++g) {
-                y = fcfma(V0s[g], Lact[(base + g0 + g) * X + t], y);
-                const float2 xi = Xic[(base + g0 + g) * X + t];
-                y.x -= xi.x;
-                y.y -= xi.y;
+    float2 acc[(MSD_XMAX + 31) / 32];
+#pragma unroll
+    for (int q = 0; q < (MSD_XMAX + 31) / 32; ++q) acc[q] = make_float2(0, 0);
+    for (int g = warp; g < n_chol; g += 8) {
+        const double2 V0d = cadd(v0a[base + g], v0b[base + g]);
+        const float2 V0 = make_float2((float)V0d.x, (float)V0d.y);
+        const float2* la = Lact + (base + g) * X;
+        const float2* xi = Xic + (base + g) * X;
+#pragma unroll
+        for (int q = 0; q < (MSD_XMAX + 31) / 32; ++q) {
+            const int x = q * 32 + lane;
+            if (x < X) {
+                acc[q] = fcfma(V0, la[x], acc[q]);
+                acc[q].x -= xi[x].x;
+                acc[q].y -= xi[x].y;
             }
+        }
     }
-    if (active) Y[(size_t)w * X + t] = y;
+#pragma unroll
+    for (int q = 0; q < (MSD_XMAX + 31) / 32; ++q) {
+        const int x = q * 32 + lane;
+        if (x < X) part[warp][x] = acc[q];
+    }
     red[0][t] = s0;
     red[1][t] = s1;
     __syncthreads();
-    for (int o = 64; o; o >>= 1) {
+    for (int x = t; x < X; x += blockDim.x) {
+        const double2 l = Lh[(size_t)w * X + x];
+        float2 y = make_float2((float)l.x, (float)l.y);
+        for (int q = 0; q < 8; ++q) { y.x += part[q][x].x; y.y += part[q][x].y; }
+        Y[(size_t)w * X + x] = y;
+    }
+    for (int o = 128; o; o >>= 1) {
         if (t < o) { red[0][t] = cadd(red[0][t], red[0][t + o]); red[1][t] = cadd(red[1][t], red[1][t + o]); }
         __syncthreads();
     }
@@ -179,8 +192,7 @@ void launch_gamma_reduce_f32(int nw, int X, int n_chol, int spin, const double2*
                              const double2* xx, const float2* Lact, const float2* Xic, const double2* Lh,
                              float2* Y, double2* scal, cudaStream_t st)
 {
-    static_assert(MSD_XMAX <= 128, "one active-block entry per thread");
-    k_gamma_reduce_f32<<<nw, 128, 0, st>>>(X, n_chol, spin, v0a, v0b, xx, Lact, Xic, Lh, Y, scal);
+    k_gamma_reduce_f32<<<nw, 256, 0, st>>>(X, n_chol, spin, v0a, v0b, xx, Lact, Xic, Lh, Y, scal);
     msd_note_launch();
 }
 

@@ -80,7 +80,7 @@ void launch_pack_complex(int nw, int n, const float* C, long long ldc, int split
 // k_mixed.cu
 size_t fepi_f32_smem(const SpinTables& tb);
 void launch_fepi_f32(const SpinTables& tb, int nw, int M, int n_chol, const float* dF, long long ldf,
-                     const double2* Gr, const double* Lh, const double* c0, const double* x0, double2* v0,
+                     const double2* Gr, const float* F0T, const double* c0, const double* x0, double2* v0,
                      double2* xx, float2* Lact, float2* Xic, cudaStream_t st);
 void launch_gamma_reduce_f32(int nw, int X, int n_chol, int spin, const double2* v0a, const double2* v0b,
                              const double2* xx, const float2* Lact, const float2* Xic, const double2* Lh,

@@ -94,6 +94,7 @@ struct msd_ctx {
     int Kvp[2] = {0, 0};        // virtual orbitals (not in occ0) padded to 32
     int* d_virt[2] = {nullptr, nullptr};
     double *d_c0[2] = {nullptr, nullptr}, *d_x0[2] = {nullptr, nullptr}, *d_c0sum = nullptr;
+    float* d_F0T[2] = {nullptr, nullptr};   // [n_chol][N][N + np] = L_g[occ0_j][col]
 };
 
 namespace {
@@ -402,8 +403,8 @@ void free_mixed(msd_ctx* ctx)
     cudaFree(ctx->Lv_hi); cudaFree(ctx->Lv_lo);
     ctx->Lv_hi = ctx->Lv_lo = nullptr;
     for (int s = 0; s < 2; ++s) {
-        cudaFree(ctx->d_virt[s]); cudaFree(ctx->d_c0[s]); cudaFree(ctx->d_x0[s]);
-        ctx->d_virt[s] = nullptr; ctx->d_c0[s] = ctx->d_x0[s] = nullptr;
+        cudaFree(ctx->d_virt[s]); cudaFree(ctx->d_c0[s]); cudaFree(ctx->d_x0[s]); cudaFree(ctx->d_F0T[s]);
+        ctx->d_virt[s] = nullptr; ctx->d_c0[s] = ctx->d_x0[s] = nullptr; ctx->d_F0T[s] = nullptr;
     }
     cudaFree(ctx->d_c0sum);
     ctx->d_c0sum = nullptr;
@@ -451,6 +452,15 @@ int prepare_mixed(msd_ctx* ctx, cudaStream_t st)
         }
         if ((rc = upload(ctx, &ctx->d_c0[s], c0))) return rc;
         if ((rc = upload(ctx, &ctx->d_x0[s], x0))) return rc;
+        const int NC = S.N + S.np;
+        std::vector<float> f0t((size_t)G * S.N * NC);
+        for (int g = 0; g < G; ++g)
+            for (int j = 0; j < S.N; ++j)
+                for (int cc = 0; cc < NC; ++cc) {
+                    const int col = cc < S.N ? S.occ0[cc] : S.part_orb[cc - S.N];
+                    f0t[((size_t)g * S.N + j) * NC + cc] = (float)ctx->h_L[((size_t)g * M + S.occ0[j]) * M + col];
+                }
+        if ((rc = upload(ctx, &ctx->d_F0T[s], f0t))) return rc;
         const long long R = (long long)G * (S.N + S.np);
         CK(cudaMalloc(&ctx->LhF_hi[s], sizeof(float) * R * ctx->Kvp[s]));
         CK(cudaMalloc(&ctx->LhF_lo[s], sizeof(float) * R * ctx->Kvp[s]));
@@ -826,7 +836,7 @@ int en_chunk(msd_ctx* ctx, Chunk& c, EnWork& E, int w0, int nw, int cap, bool fp
             th.end(st);
             if (g) return fail(ctx, MSD_ERR_CUDA, "tensor-core GEMM launch failed (energy)");
             th.begin("k_fepi_f32", st);
-            launch_fepi_f32(T[s], nw, M, G, (float*)E.F32, (long long)G * NC[s], c.Gr[s], ctx->sp[s].d_Lh,
+            launch_fepi_f32(T[s], nw, M, G, (float*)E.F32, (long long)G * NC[s], c.Gr[s], ctx->d_F0T[s],
                             ctx->d_c0[s], ctx->d_x0[s], (double2*)E.v0[s], (double2*)E.xx[s], (float2*)E.La[s],
                             (float2*)E.Xi[s], st);
             th.end(st);
