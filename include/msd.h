@@ -8,7 +8,7 @@
  *
  *   overlap      O_T = <Psi_T|phi>                                (Sec. II A-B)
  *   force bias   vbias_g = <Psi_T| L_g-hat |phi> / <Psi_T|phi>,
- *                L_g-hat = sum_{pq,s} L^g_pq a+_ps a_qs             (Eq. 8)
+ *                L_g-hat = sum_{pq,s} L^g_pq a+_ps a_qs             (Eq. 7)
  *   local energy E_L = <Psi_T|H|phi> / <Psi_T|phi>                (Sec. II A, III)
  *
  * for H = e0 + sum_{pq,s} h^s_pq a+_ps a_qs
@@ -126,7 +126,7 @@ int msd_overlap(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b,
 int msd_det_ratios(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b,
                    double* ratios, double* ref_ovlp, void* stream);
 
-/* Force-bias numerators (Eq. 8 without its -sqrt(dt) prefactor, which the
+/* Force-bias numerators (Eq. 7 without its -sqrt(dt) prefactor, which the
    propagator applies):
      vbias [n_w][n_chol]  sum_s tr(L_g G_T^s), complex, where G_T^s is the
                           mixed Green's function <Psi_T|a+_ps a_qs|phi>/O_T

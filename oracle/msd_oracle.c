@@ -10,10 +10,10 @@
  * in the number of determinants) in plain complex double precision:
  *
  *   overlap     O_I = <D_I|phi> = det(D_I^dag phi_a) det(D_I^dag phi_b)
- *               (Sec. II A, overlap of two Slater determinants), computed as
+ *               (Eq. 13, overlap of two Slater determinants), computed as
  *               a full N x N determinant by LU with partial pivoting;
  *   Green's fn  G_I[p][q] = <D_I|a+_p a_q|phi> / <D_I|phi>
- *               = [phi (D_I^dag phi)^-1 D_I^dag]_{qp}   (Sec. II A);
+ *               = [phi (D_I^dag phi)^-1 D_I^dag]_{qp}   (Eq. 14);
  *   energy      E_I = <D_I|H|phi> / <D_I|phi> from G_I by the generalized
  *               Wick theorem (Sec. II A), for
  *               H = e0 + sum_{pq,s} h_pq a+_ps a_qs
@@ -24,8 +24,8 @@
  *                                   - sum_s tr(L_g G_I^s L_g G_I^s) ],
  *               with tr(X G) = sum_pq X_pq G_pq;
  *   trial sums  O_T = sum_I c_I O_I,  E_L = sum_I c_I O_I E_I / O_T,
- *               G_T = sum_I c_I O_I G_I / O_T (Sec. II B, Psi_T = sum c_I D_I),
- *               force-bias numerator vbias_g = sum_s tr(L_g G_T^s) (Eq. 8
+ *               G_T = sum_I c_I O_I G_I / O_T (Eq. 15, Psi_T = sum c_I D_I),
+ *               force-bias numerator vbias_g = sum_s tr(L_g G_T^s) (Eq. 7
  *               without its -sqrt(dt) prefactor).
  *
  * Since D_I^dag has non-zero columns only at the occupied orbitals occ_I,

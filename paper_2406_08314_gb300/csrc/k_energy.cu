@@ -1,5 +1,5 @@
 // Local-energy and force-bias contractions (Sec. III: fill_os / get_ss, and
-// the force bias of Eq. 8), FP64 path.
+// the force bias of Eq. 7), FP64 path.
 //
 // With G = G0^T (rows occ0 non-zero), B_s = A_s^-1 for an excitation string s
 // with holes h_1..h_k and particles p_1..p_k, and

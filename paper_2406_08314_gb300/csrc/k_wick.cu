@@ -429,7 +429,7 @@ void launch_cmat(const SpinTables& tb, int nw, const double2* r, const double2* 
 }
 
 // ------------------------------------------------------------------------
-// Rows of the mixed Green's function G_T (Eq. 8 numerator), per (walker,
+// Rows of the mixed Green's function G_T (Eq. 7 numerator), per (walker,
 // spin), restricted to the rows that can be non-zero (occ0 then P):
 //   Y[p][c] = sum_h Cm[p][h] G[H_h][c]
 //   G_T[occ0_l][c] = G[occ0_l][c] - sum_p G[occ0_l][P_p] Y[p][c] / R
