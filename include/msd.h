@@ -185,6 +185,31 @@ int msd_set_sync(msd_ctx* ctx, int sync);
    contexts), for launch accounting by benchmarks. */
 long long msd_launch_count(void);
 
+/* Trial overlap without any device allocation during the call. The paper
+   has no counterpart: this serves callers that cannot let a library call
+   cudaMalloc / cudaFree, such as a framework that owns all device memory
+   through its own allocator or a fixed budget, or a latency-critical loop
+   that must not take the synchronisation those calls can imply.
+   Same arguments and results as msd_overlap, with these differences:
+     - phi_a, phi_b, ovlp and ratio_sum must be device pointers
+       (MSD_ERR_ARG otherwise);
+     - the scratch is a file-scope device array of MSD_STATIC_SCRATCH_BYTES
+       held by every GPU that loads the library until the process exits;
+       walkers are processed in chunks that fit it, and a request whose
+       single walker needs more scratch than that is rejected with
+       MSD_ERR_SHAPE;
+     - the first call on a device resolves the array's device address
+       (cudaGetSymbolAddress); make that first call before any stream
+       capture;
+     - all calls share the array and each leaves its contents behind, so
+       calls that overlap on the GPU (other streams, other host threads)
+       race: serialise them.
+   The context must have been created and set up beforehand (those calls
+   allocate). */
+#define MSD_STATIC_SCRATCH_BYTES (64u << 20)
+int msd_overlap_noalloc(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b,
+                        double* ovlp, double* ratio_sum, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1242,3 +1242,118 @@ int msd_set_sync(msd_ctx* ctx, int sync)
 }
 
 }  // extern "C"
+
+// ========================================================================
+// Overlap without device allocation.
+//
+// msd_overlap obtains its workspace from the context, which grows it with
+// cudaMalloc on first use. Some callers cannot let a library allocate during
+// a call: a framework that owns every device allocation through its own
+// caching allocator or a memory budget fixed at start-up, or a latency-
+// critical loop that must not take the device-wide synchronisation that
+// cudaMalloc / cudaFree can imply. For them msd_overlap_noalloc computes the
+// same overlap with its scratch in the file-scope device array below, whose
+// size is fixed at build time. The array lives on every GPU that loads the
+// library until the process exits; every call shares it.
+#include <mutex>
+
+static __device__ __align__(256) unsigned char g_static_scratch[MSD_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+std::mutex g_static_mu;
+void* g_static_ptr[256] = {nullptr};
+
+// Device address of the static scratch on the current device (resolved once
+// per device; host code cannot use the symbol itself as a device pointer).
+int static_scratch(msd_ctx* ctx, void** out)
+{
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    const int dev = ctx->device;
+    if (dev < 0 || dev >= 256) return fail(ctx, MSD_ERR_ARG, "device index %d out of range", dev);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(ctx, MSD_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed: %s",
+                        cudaGetErrorString(e));
+        g_static_ptr[dev] = p;
+    }
+    *out = g_static_ptr[dev];
+    return MSD_OK;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" int msd_overlap_noalloc(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b,
+                                   double* ovlp, double* ratio_sum, void* stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = check_ready(ctx);
+    if (rc) return rc;
+    if (n_w < 0 || (n_w > 0 && (!phi_a || !phi_b))) return fail(ctx, MSD_ERR_ARG, "bad walker arguments");
+    if (n_w > 0 && !ovlp && !ratio_sum) return fail(ctx, MSD_ERR_ARG, "no output requested");
+    CK(cudaSetDevice(ctx->device));
+    void* scratch = nullptr;
+    if ((rc = static_scratch(ctx, &scratch))) return rc;   // first call on a device: set-up
+    if (n_w == 0) return MSD_OK;
+    const void* ptrs[4] = {phi_a, phi_b, ovlp, ratio_sum};
+    for (const void* p : ptrs)
+        if (p && !is_device_ptr(p))
+            return fail(ctx, MSD_ERR_ARG, "msd_overlap_noalloc takes device pointers only (no staging buffers)");
+    const int M = ctx->M;
+    SpinTables T1[2] = {tables(ctx->sp[0], 1), tables(ctx->sp[1], 1)};
+    const int nR = weights_blocks(T1[0]);
+    // scratch per walker: Gr, O0, Gact, r of both spins, alpha weights, partial sums
+    size_t per = 0;
+    for (int s = 0; s < 2; ++s)
+        per += sizeof(double2) * ((size_t)T1[s].N * M + 1 + std::max(1, T1[s].nh * T1[s].np) + T1[s].n_str);
+    per += sizeof(double2) * ((size_t)T1[0].n_str + nR);
+    const size_t slack = 16 * 256;   // alignment of the carved arrays
+    if (per + slack > (size_t)MSD_STATIC_SCRATCH_BYTES)
+        return fail(ctx, MSD_ERR_SHAPE,
+                    "one walker needs %zu bytes of scratch; the static scratch holds %zu bytes", per + slack,
+                    (size_t)MSD_STATIC_SCRATCH_BYTES);
+    const int cap = (int)std::min<size_t>((size_t)n_w, ((size_t)MSD_STATIC_SCRATCH_BYTES - slack) / per);
+    // carve the static scratch for `cap` walkers; every entry a kernel reads
+    // is written earlier in the same call, so nothing needs clearing
+    unsigned char* base = (unsigned char*)scratch;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { void* p = base + off; off += align256(bytes); return p; };
+    double2 *Gr[2], *O0[2], *Gact[2], *r[2];
+    for (int s = 0; s < 2; ++s) {
+        Gr[s] = (double2*)take(sizeof(double2) * cap * T1[s].N * (size_t)M);
+        O0[s] = (double2*)take(sizeof(double2) * cap);
+        Gact[s] = (double2*)take(sizeof(double2) * cap * (size_t)std::max(1, T1[s].nh * T1[s].np));
+        r[s] = (double2*)take(sizeof(double2) * cap * (size_t)T1[s].n_str);
+    }
+    double2* wts = (double2*)take(sizeof(double2) * cap * (size_t)T1[0].n_str);
+    double2* part = (double2*)take(sizeof(double2) * cap * (size_t)nR);
+    if (off > (size_t)MSD_STATIC_SCRATCH_BYTES)
+        return fail(ctx, MSD_ERR_SHAPE, "static scratch layout overflow (%zu bytes)", off);
+    CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), st));
+    TimerHook none;   // no event timing here: events are not created on this path
+    const double2* pa = (const double2*)phi_a;
+    const double2* pb = (const double2*)phi_b;
+    for (int w0 = 0; w0 < n_w; w0 += cap) {
+        const int nw = std::min(cap, n_w - w0);
+        SpinTables T[2] = {tables(ctx->sp[0], cap), tables(ctx->sp[1], cap)};
+        launch_ref(pa + (size_t)w0 * M * ctx->n[0], nw, M, ctx->n[0], T[0], Gr[0], O0[0], Gact[0], ctx->d_err, st);
+        launch_ref(pb + (size_t)w0 * M * ctx->n[1], nw, M, ctx->n[1], T[1], Gr[1], O0[1], Gact[1], ctx->d_err, st);
+        launch_strings(T[0], nw, Gact[0], r[0], nullptr, false, false, st, none);
+        launch_strings(T[1], nw, Gact[1], r[1], nullptr, false, false, st, none);
+        launch_weights(T[0], nw, r[0], r[1], T[1].n_str, wts, part, nR, 0, st);
+        launch_sum_slots(nw, part, nR, 0, nR, ratio_sum ? (double2*)ratio_sum + w0 : nullptr, O0[0], O0[1],
+                         ovlp ? (double2*)ovlp + w0 : nullptr, st);
+        CKLAUNCH();
+    }
+    if (ctx->sync) {
+        CK(cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (*ctx->h_err & MSD_DEV_ERR_SINGULAR)
+            return fail(ctx, MSD_ERR_REF_SINGULAR, "D_0^dag phi is singular for some walker");
+    }
+    return MSD_OK;
+}

@@ -23,7 +23,7 @@ EXPORTS = ["msd_create", "msd_destroy", "msd_last_error", "msd_set_hamiltonian",
            "msd_set_precision", "msd_overlap", "msd_det_ratios", "msd_force_bias",
            "msd_local_energy", "msd_evaluate", "msd_info", "msd_set_timing", "msd_reset_stats",
            "msd_kernel_count", "msd_kernel_stat", "msd_set_workspace_limit", "msd_set_sync",
-           "msd_launch_count"]
+           "msd_launch_count", "msd_overlap_noalloc"]
 INFO = {"n_det": 1, "n_chol": 2, "n_strings_a": 3, "n_strings_b": 4, "n_holes_a": 5,
         "n_parts_a": 6, "n_holes_b": 7, "n_parts_b": 8, "workspace_bytes": 9, "walker_chunk": 10}
 
@@ -50,7 +50,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.msd_set_hamiltonian.argtypes = [vp, vp, ctypes.c_double, ci, vp]
     lib.msd_set_trial.argtypes = [vp, ci, vp, vp, vp]
     lib.msd_set_precision.argtypes = [vp, ci]
-    for f in ("msd_overlap", "msd_det_ratios", "msd_force_bias", "msd_local_energy"):
+    for f in ("msd_overlap", "msd_det_ratios", "msd_force_bias", "msd_local_energy",
+              "msd_overlap_noalloc"):
         getattr(lib, f).argtypes = [vp, ci, vp, vp, vp, vp, vp]
     lib.msd_evaluate.argtypes = [vp, ci, vp, vp, vp, vp, vp, vp]
     lib.msd_info.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_longlong)]
@@ -179,6 +180,14 @@ class Context:
         self._check(_lib.msd_overlap(self._h, n_w, _ptr(phi_a), _ptr(phi_b), _ptr(ov), _ptr(rs),
                                      self._stream(phi_a, stream)))
         return (ov, rs) if ratio_sum else ov
+
+    def overlap_noalloc(self, phi_a, phi_b, ovlp, ratio_sum=None, stream=None):
+        """msd_overlap into caller-provided device tensors, with the
+        library's static scratch instead of allocated workspace."""
+        n_w = self._walkers(phi_a, phi_b)
+        self._check(_lib.msd_overlap_noalloc(self._h, n_w, _ptr(phi_a), _ptr(phi_b), _ptr(ovlp),
+                                             _ptr(ratio_sum), self._stream(phi_a, stream)))
+        return ovlp, ratio_sum
 
     def det_ratios(self, phi_a, phi_b, stream=None, ref_ovlp=False):
         n_w = self._walkers(phi_a, phi_b)
