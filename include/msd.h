@@ -185,6 +185,45 @@ int msd_set_sync(msd_ctx* ctx, int sync);
    contexts), for launch accounting by benchmarks. */
 long long msd_launch_count(void);
 
+/* ---- Batched independent systems ---------------------------------------
+   Many systems (each its own context: uneven orbital, electron and
+   determinant counts; one device and one precision for all) evaluated
+   together. msd_batch_evaluate runs, for every system i, the overlap, force
+   bias and dense energy steps of msd_evaluate (systems spread over eight
+   concurrent streams, branches of the recorded graph), then the per-determinant
+   energy terms of all systems in one persistent kernel that takes
+   (system, walker, excitation bucket, block) work items from a queue, then
+   the final sums. The first call with a given set of buffers runs eagerly and
+   records the whole sequence as a CUDA graph; later calls with the same
+   buffers (and no change to any context) replay it with one graph launch.
+   Arrays are indexed by system: n_w[i] walkers, device pointers phi_a[i],
+   phi_b[i], e_loc[i] (required), ovlp[i], vbias[i] (arrays or entries may be
+   NULL). Every system's walkers must fit one workspace chunk (MSD_ERR_SHAPE
+   otherwise). The contexts must outlive the batch. */
+typedef struct msd_batch msd_batch;
+int msd_batch_create(msd_batch** out, msd_ctx* const* ctxs, int n_sys);
+void msd_batch_destroy(msd_batch* b);
+const char* msd_batch_last_error(const msd_batch* b);
+int msd_batch_evaluate(msd_batch* b, const int* n_w, const double* const* phi_a,
+                       const double* const* phi_b, double* const* ovlp, double* const* vbias,
+                       double* const* e_loc, void* stream);
+/* Autotuner: times every combination of the tensor-core output tile width
+   (128, 256), resident CTAs per SM of the persistent kernel (1, 2, 4) and
+   work-item order (0: by system, 1: largest work first, 2: walkers
+   interleaved across systems) on the given inputs, keeps the fastest, and
+   appends "key tile ctas order ms" to cache_path (a text file; may be NULL).
+   A later call whose system shapes match a cached key applies it without
+   timing. */
+int msd_batch_autotune(msd_batch* b, const int* n_w, const double* const* phi_a,
+                       const double* const* phi_b, double* const* ovlp, double* const* vbias,
+                       double* const* e_loc, void* stream, const char* cache_path);
+int msd_batch_config(const msd_batch* b, int* tile_n, int* ctas_per_sm, int* order);
+int msd_batch_set_config(msd_batch* b, int tile_n, int ctas_per_sm, int order);
+/* 1 once a graph has been recorded for the current buffers, else 0. */
+int msd_batch_graph_ready(const msd_batch* b);
+/* Kernel nodes in the recorded graph (kernels one replay launches), or 0. */
+long long msd_batch_graph_kernels(const msd_batch* b);
+
 /* Trial overlap without any device allocation during the call. The paper
    has no counterpart: this serves callers that cannot let a library call
    cudaMalloc / cudaFree, such as a framework that owns all device memory

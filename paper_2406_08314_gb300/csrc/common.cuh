@@ -10,6 +10,14 @@
 #define MSD_NMAX 64         // electrons per spin
 #define MSD_XMAX 112        // n_h * n_p per spin (active hole x particle block)
 
+// Work decomposition of the per-determinant kernels: threads per block and
+// strings (determinants) per thread. One block writes one partial-sum slot.
+#define SE_THREADS 256
+#define SE_PER_THREAD 4
+#define PC_THREADS 256
+#define PC_PER_THREAD 8
+
+
 // ---------------------------------------------------------------- complex
 __host__ __device__ __forceinline__ double2 cz(double r, double i) { return make_double2(r, i); }
 __host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }

@@ -1,0 +1,130 @@
+// Per-determinant energy terms shared by the per-system kernels
+// (k_energy.cu) and the persistent batched kernel (k_batch.cu).
+//
+// string_energy_term: same-spin term of one excitation string s (level KL,
+// index sl in its bucket) of walker w:
+//   r_s w_s e_s,  e_s = sum_ij B_ij Y[h_j][p_i] + 1/2 (Qc - Qx),
+//   Qc = sum_ijkl B_ij B_kl K[(h_j,p_i)][(h_l,p_k)],
+//   Qx = sum_ijkl B_ij B_kl K[(h_j,p_k)][(h_l,p_i)]
+// (K = the walker's same-spin Gram matrix and Y its linear coefficients, in
+// shared memory). The outer (i, j) loop runs at run time; the inner (k, l)
+// loop is unrolled over the inverse minor held in registers.
+//
+// pair_cross_term: opposite-spin term of determinant I = (a, b) with levels
+// (ka, KB) of walker w:
+//   c_I r_a r_b X_ab,  X_ab = sum_ij Ba_ij sum_kl Bb_kl K^{ab}[(ha_j,pa_i)][(hb_l,pb_k)]
+// (K^{ab} in shared memory).
+#pragma once
+
+#include <type_traits>
+
+#include "common.cuh"
+
+template <typename T>
+using cplx_t = typename std::conditional<std::is_same<T, float>::value, float2, double2>::type;
+
+template <int KL, typename T>
+__device__ __forceinline__ double2 string_energy_term(const SpinTables& tb, int w, int sl, int ns,
+                                                      const void* __restrict__ Bin, const cplx_t<T>* ks,
+                                                      const cplx_t<T>* ys, const double2* __restrict__ r,
+                                                      const double2* __restrict__ wts)
+{
+    using T2 = cplx_t<T>;
+    const int X = tb.nh * tb.np, np = tb.np;
+    const int s = tb.bucket[KL] + sl;
+    const uint8_t* sh = tb.str_h + (size_t)s * MSD_KMAX;
+    const uint8_t* sp = tb.str_p + (size_t)s * MSD_KMAX;
+    int hx[KL], px[KL];   // hole row offset h*np, particle index p
+#pragma unroll
+    for (int i = 0; i < KL; ++i) { hx[i] = sh[i] * np; px[i] = sp[i]; }
+    const T2* B = reinterpret_cast<const T2*>(Bin) + (size_t)tb.b_off[KL] + ((size_t)w * ns + sl) * (KL * KL);
+    T2 b[KL][KL];
+#pragma unroll
+    for (int i = 0; i < KL; ++i)
+#pragma unroll
+        for (int j = 0; j < KL; ++j) b[i][j] = B[i * KL + j];
+    T lr = 0, li = 0;      // linear part
+    T qr = 0, qi = 0;      // Qc - Qx
+#pragma unroll 1
+    for (int i = 0; i < KL; ++i) {
+        const int pi = sp[i];
+#pragma unroll 1
+        for (int j = 0; j < KL; ++j) {
+            const int hj = sh[j] * np;
+            const int xij = hj + pi;
+            const T2 bij = B[i * KL + j];
+            const T2 y = ys[xij];
+            lr += bij.x * y.x - bij.y * y.y;
+            li += bij.x * y.y + bij.y * y.x;
+            const T2* kc_row = ks + (size_t)xij * X;
+            T zr = 0, zi = 0;
+#pragma unroll
+            for (int k = 0; k < KL; ++k) {
+                const T2* kx_row = ks + (size_t)(hj + px[k]) * X + pi;
+#pragma unroll
+                for (int l = 0; l < KL; ++l) {
+                    // K[(h_j,p_i)][(h_l,p_k)] - K[(h_j,p_k)][(h_l,p_i)]
+                    const T2 kc = kc_row[hx[l] + px[k]];
+                    const T2 kx = kx_row[hx[l]];
+                    const T dr = kc.x - kx.x, di = kc.y - kx.y;
+                    zr += b[k][l].x * dr - b[k][l].y * di;
+                    zi += b[k][l].x * di + b[k][l].y * dr;
+                }
+            }
+            qr += bij.x * zr - bij.y * zi;
+            qi += bij.x * zi + bij.y * zr;
+        }
+    }
+    const double2 e_s = cz((double)lr + 0.5 * (double)qr, (double)li + 0.5 * (double)qi);
+    const double2 rw = cmul(r[(size_t)w * tb.n_str + s], wts[(size_t)w * tb.n_str + s]);
+    return cmul(rw, e_s);
+}
+
+template <int KB, typename T>
+__device__ __forceinline__ double2 pair_cross_term(const SpinTables& ta, const SpinTables& tbb, const PairTables& pt,
+                                                   int ka, int I, int w, const void* __restrict__ Ba_in,
+                                                   const void* __restrict__ Bb_in, const cplx_t<T>* ks,
+                                                   const double2* __restrict__ ra, const double2* __restrict__ rb)
+{
+    using T2 = cplx_t<T>;
+    const int Xb = tbb.nh * tbb.np;
+    const int a = pt.a[I], b = pt.b[I];
+    const int nsa = ta.bucket[ka + 1] - ta.bucket[ka], sa = a - ta.bucket[ka];
+    const int nsb = tbb.bucket[KB + 1] - tbb.bucket[KB], sb = b - tbb.bucket[KB];
+    int xb[KB][KB];
+#pragma unroll
+    for (int k = 0; k < KB; ++k)
+#pragma unroll
+        for (int l = 0; l < KB; ++l)
+            xb[k][l] = tbb.str_h[(size_t)b * MSD_KMAX + l] * tbb.np + tbb.str_p[(size_t)b * MSD_KMAX + k];
+    const T2* Ba = reinterpret_cast<const T2*>(Ba_in) + (size_t)ta.b_off[ka] + ((size_t)w * nsa + sa) * (ka * ka);
+    const T2* Bb = reinterpret_cast<const T2*>(Bb_in) + (size_t)tbb.b_off[KB] + ((size_t)w * nsb + sb) * (KB * KB);
+    T2 bb[KB][KB];
+#pragma unroll
+    for (int k = 0; k < KB; ++k)
+#pragma unroll
+        for (int l = 0; l < KB; ++l) bb[k][l] = Bb[k * KB + l];
+    const uint8_t* ah = ta.str_h + (size_t)a * MSD_KMAX;
+    const uint8_t* ap = ta.str_p + (size_t)a * MSD_KMAX;
+    T xr = 0, xim = 0;
+#pragma unroll 1
+    for (int i = 0; i < ka; ++i)
+#pragma unroll 1
+        for (int j = 0; j < ka; ++j) {
+            const T2 ba = Ba[i * ka + j];
+            const T2* krow = ks + (size_t)(ah[j] * ta.np + ap[i]) * Xb;
+            T zr = 0, zi = 0;
+#pragma unroll
+            for (int k = 0; k < KB; ++k)
+#pragma unroll
+                for (int l = 0; l < KB; ++l) {
+                    const T2 kv = krow[xb[k][l]];
+                    zr += bb[k][l].x * kv.x - bb[k][l].y * kv.y;
+                    zi += bb[k][l].x * kv.y + bb[k][l].y * kv.x;
+                }
+            xr += ba.x * zr - ba.y * zi;
+            xim += ba.x * zi + ba.y * zr;
+        }
+    const double2 rr = cscale(cmul(ra[(size_t)w * ta.n_str + a], rb[(size_t)w * tbb.n_str + b]), pt.c[I]);
+    return cmul(rr, cz((double)xr, (double)xim));
+}

@@ -17,6 +17,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "det_terms.cuh"
 #include "kernels.h"
 
 // ------------------------------------------------------------------------
@@ -309,8 +310,6 @@ void launch_gram(int nw, int Xp, int Xq, int n_chol, const double2* P, const dou
 // arithmetic; the block sum is FP64. The outer (i, j) loop runs at run
 // time (its operands are read once); the inner (k, l) loop is unrolled over
 // the string's inverse minor held in registers.
-#define SE_THREADS 256
-#define SE_PER_THREAD 4
 template <int KL, typename T>
 __global__ void __launch_bounds__(SE_THREADS)
 k_string_energy(SpinTables tb, const double2* __restrict__ r, const double2* __restrict__ wts,
@@ -334,53 +333,7 @@ k_string_energy(SpinTables tb, const double2* __restrict__ r, const double2* __r
     for (int it = 0; it < SE_PER_THREAD; ++it) {
         const int sl = blockIdx.x * (SE_THREADS * SE_PER_THREAD) + it * SE_THREADS + t;
         if (sl >= ns) break;
-        const int s = tb.bucket[KL] + sl;
-        const uint8_t* sh = tb.str_h + (size_t)s * MSD_KMAX;
-        const uint8_t* sp = tb.str_p + (size_t)s * MSD_KMAX;
-        int hx[KL], px[KL];   // hole row offset h*np, particle index p
-#pragma unroll
-        for (int i = 0; i < KL; ++i) { hx[i] = sh[i] * np; px[i] = sp[i]; }
-        const T2* B = reinterpret_cast<const T2*>(Bin) + (size_t)tb.b_off[KL] + ((size_t)w * ns + sl) * (KL * KL);
-        T2 b[KL][KL];
-#pragma unroll
-        for (int i = 0; i < KL; ++i)
-#pragma unroll
-            for (int j = 0; j < KL; ++j) b[i][j] = B[i * KL + j];
-        T lr = 0, li = 0;      // linear part
-        T qr = 0, qi = 0;      // Qc - Qx
-#pragma unroll 1
-        for (int i = 0; i < KL; ++i) {
-            const int pi = sp[i];
-#pragma unroll 1
-            for (int j = 0; j < KL; ++j) {
-                const int hj = sh[j] * np;
-                const int xij = hj + pi;
-                const T2 bij = B[i * KL + j];
-                const T2 y = ys[xij];
-                lr += bij.x * y.x - bij.y * y.y;
-                li += bij.x * y.y + bij.y * y.x;
-                const T2* kc_row = ks + (size_t)xij * X;
-                T zr = 0, zi = 0;
-#pragma unroll
-                for (int k = 0; k < KL; ++k) {
-                    const T2* kx_row = ks + (size_t)(hj + px[k]) * X + pi;
-#pragma unroll
-                    for (int l = 0; l < KL; ++l) {
-                        // K[(h_j,p_i)][(h_l,p_k)] - K[(h_j,p_k)][(h_l,p_i)]
-                        const T2 kc = kc_row[hx[l] + px[k]];
-                        const T2 kx = kx_row[hx[l]];
-                        const T dr = kc.x - kx.x, di = kc.y - kx.y;
-                        zr += b[k][l].x * dr - b[k][l].y * di;
-                        zi += b[k][l].x * di + b[k][l].y * dr;
-                    }
-                }
-                qr += bij.x * zr - bij.y * zi;
-                qi += bij.x * zi + bij.y * zr;
-            }
-        }
-        const double2 e_s = cz((double)lr + 0.5 * (double)qr, (double)li + 0.5 * (double)qi);
-        const double2 rw = cmul(r[(size_t)w * tb.n_str + s], wts[(size_t)w * tb.n_str + s]);
-        contrib = cadd(contrib, cmul(rw, e_s));
+        contrib = cadd(contrib, string_energy_term<KL, T>(tb, w, sl, ns, Bin, ks, ys, r, wts));
     }
     red[t] = contrib;
     __syncthreads();
@@ -448,8 +401,6 @@ int string_energy_slots(const SpinTables& tb)
 //   X_ab = sum_ij Ba_ij sum_kl Bb_kl K^{ab}[(ha_j,pa_i)][(hb_l,pb_k)].
 // The beta level KB is a template parameter (its inverse minor is held in
 // registers); the alpha level runs at run time.
-#define PC_THREADS 256
-#define PC_PER_THREAD 8
 template <int KB, typename T>
 __global__ void __launch_bounds__(PC_THREADS)
 k_pair_cross(SpinTables ta, SpinTables tbb, PairTables pt, int ka, int lo, int n,
@@ -472,46 +423,7 @@ k_pair_cross(SpinTables ta, SpinTables tbb, PairTables pt, int ka, int lo, int n
     for (int it = 0; it < PC_PER_THREAD; ++it) {
         const int i0 = blockIdx.x * (PC_THREADS * PC_PER_THREAD) + it * PC_THREADS + t;
         if (i0 >= n) break;
-        const int I = lo + i0;
-        const int a = pt.a[I], b = pt.b[I];
-        const int nsa = ta.bucket[ka + 1] - ta.bucket[ka], sa = a - ta.bucket[ka];
-        const int nsb = tbb.bucket[KB + 1] - tbb.bucket[KB], sb = b - tbb.bucket[KB];
-        int xb[KB][KB];
-#pragma unroll
-        for (int k = 0; k < KB; ++k)
-#pragma unroll
-            for (int l = 0; l < KB; ++l)
-                xb[k][l] = tbb.str_h[(size_t)b * MSD_KMAX + l] * tbb.np + tbb.str_p[(size_t)b * MSD_KMAX + k];
-        const T2* Ba = reinterpret_cast<const T2*>(Ba_in) + (size_t)ta.b_off[ka] + ((size_t)w * nsa + sa) * (ka * ka);
-        const T2* Bb = reinterpret_cast<const T2*>(Bb_in) + (size_t)tbb.b_off[KB] + ((size_t)w * nsb + sb) * (KB * KB);
-        T2 bb[KB][KB];
-#pragma unroll
-        for (int k = 0; k < KB; ++k)
-#pragma unroll
-            for (int l = 0; l < KB; ++l) bb[k][l] = Bb[k * KB + l];
-        const uint8_t* ah = ta.str_h + (size_t)a * MSD_KMAX;
-        const uint8_t* ap = ta.str_p + (size_t)a * MSD_KMAX;
-        T xr = 0, xim = 0;
-#pragma unroll 1
-        for (int i = 0; i < ka; ++i)
-#pragma unroll 1
-            for (int j = 0; j < ka; ++j) {
-                const T2 ba = Ba[i * ka + j];
-                const T2* krow = ks + (size_t)(ah[j] * ta.np + ap[i]) * Xb;
-                T zr = 0, zi = 0;
-#pragma unroll
-                for (int k = 0; k < KB; ++k)
-#pragma unroll
-                    for (int l = 0; l < KB; ++l) {
-                        const T2 kv = krow[xb[k][l]];
-                        zr += bb[k][l].x * kv.x - bb[k][l].y * kv.y;
-                        zi += bb[k][l].x * kv.y + bb[k][l].y * kv.x;
-                    }
-                xr += ba.x * zr - ba.y * zi;
-                xim += ba.x * zi + ba.y * zr;
-            }
-        const double2 rr = cscale(cmul(ra[(size_t)w * ta.n_str + a], rb[(size_t)w * tbb.n_str + b]), pt.c[I]);
-        contrib = cadd(contrib, cmul(rr, cz((double)xr, (double)xim)));
+        contrib = cadd(contrib, pair_cross_term<KB, T>(ta, tbb, pt, ka, lo + i0, w, Ba_in, Bb_in, ks, ra, rb));
     }
     red[t] = contrib;
     __syncthreads();

@@ -68,8 +68,9 @@ struct TcOperand {
     long long ld;
 };
 // K is split over `splits` CTAs along grid.z; split z writes C + z * c_split_stride.
+// bn: output tile width (128 or 256; 0 picks by Nc).
 int tc_gemm_3xtf32(const TcOperand& A, const TcOperand& B, int Mr, int Nc, int K, float* C, long long ldc,
-                   unsigned* err, cudaStream_t st, int splits = 1, long long c_split_stride = 0);
+                   unsigned* err, cudaStream_t st, int splits = 1, long long c_split_stride = 0, int bn = 0);
 void launch_split_complex_rows(int nb, int R, int Kg, int Kp, const double2* src, long long src_ld,
                                const int* cols, float* hi, float* lo, cudaStream_t st);
 void launch_split_real_rows(long long R, int Kg, int Kp, const double* src, long long src_ld, const int* cols,
@@ -87,3 +88,27 @@ void launch_gamma_reduce_f32(int nw, int X, int n_chol, int spin, const double2*
                              float2* Y, double2* scal, cudaStream_t st);
 void launch_gram_f32(int nw, int Xp, int Xq, int n_chol, const float2* P, const float2* Q, float2* K,
                      cudaStream_t st);
+
+// k_batch.cu: per-determinant energy terms of many systems in one
+// persistent launch.
+struct BatchSys {
+    SpinTables t[2];
+    PairTables pt;
+    const double2* r[2];
+    const double2* wts[2];
+    const void* B[2];
+    const void* K[3];   // same-spin alpha, same-spin beta, opposite-spin Gram matrices
+    const void* Y[2];
+    double2* part;
+    int nslot;
+    int pad_;
+};
+struct BatchItem {
+    int sys, w;
+    int kind;           // 0: same-spin string block, 1: opposite-spin determinant block
+    int spin;           // kind 0
+    int ka, kb;         // level (kind 0: ka); level pair (kind 1)
+    int blk, slot;      // block within the bucket, partial-sum slot
+};
+int launch_det_batched(const BatchSys* systems, const BatchItem* items, int n_items, unsigned* counter,
+                       size_t smem, bool fp32, int grid, cudaStream_t st);

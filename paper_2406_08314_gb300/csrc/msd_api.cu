@@ -95,6 +95,8 @@ struct msd_ctx {
     int* d_virt[2] = {nullptr, nullptr};
     double *d_c0[2] = {nullptr, nullptr}, *d_x0[2] = {nullptr, nullptr}, *d_c0sum = nullptr;
     float* d_F0T[2] = {nullptr, nullptr};   // [n_chol][N][N + np] = L_g[occ0_j][col]
+    int tc_bn = 0;                // tensor-core output tile width (0 = by shape)
+    long long gen = 0;            // bumped whenever a device buffer may move
 };
 
 namespace {
@@ -189,6 +191,7 @@ int arena_get(msd_ctx* ctx, const char* name, size_t bytes, void** out)
     if (b.bytes < bytes) {
         if (b.p) { cudaDeviceSynchronize(); cudaFree(b.p); b.p = nullptr; b.bytes = 0; }
         bytes = (bytes + 255) & ~(size_t)255;
+        ctx->gen++;
         cudaError_t e = cudaMalloc(&b.p, bytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -396,6 +399,7 @@ int build_half_rotated(msd_ctx* ctx)
 
 void free_mixed(msd_ctx* ctx)
 {
+    ctx->gen++;
     for (int s = 0; s < 2; ++s) {
         cudaFree(ctx->LhF_hi[s]); cudaFree(ctx->LhF_lo[s]);
         ctx->LhF_hi[s] = ctx->LhF_lo[s] = nullptr;
@@ -815,7 +819,7 @@ int en_alloc(msd_ctx* ctx, int cap, bool fp32, EnWork& E)
 }
 
 int en_chunk(msd_ctx* ctx, Chunk& c, EnWork& E, int w0, int nw, int cap, bool fp32, double2* e_out,
-             double2* ov_out, cudaStream_t st)
+             double2* ov_out, cudaStream_t st, bool defer_det = false)
 {
     const int M = ctx->M, G = ctx->n_chol;
     const TimerHook& th = ctx->hook;
@@ -832,7 +836,8 @@ int en_chunk(msd_ctx* ctx, Chunk& c, EnWork& E, int w0, int nw, int cap, bool fp
             th.begin("tc_gemm_F", st);
             const int g = tc_gemm_3xtf32({(float*)E.Ah, (float*)E.Al, ctx->Kvp[s]},
                                          {ctx->LhF_hi[s], ctx->LhF_lo[s], ctx->Kvp[s]}, 2 * nw * N, G * NC[s],
-                                         ctx->Kvp[s], (float*)E.F32, (long long)G * NC[s], ctx->d_err, st);
+                                         ctx->Kvp[s], (float*)E.F32, (long long)G * NC[s], ctx->d_err, st, 1, 0,
+                                         ctx->tc_bn);
             th.end(st);
             if (g) return fail(ctx, MSD_ERR_CUDA, "tensor-core GEMM launch failed (energy)");
             th.begin("k_fepi_f32", st);
@@ -880,6 +885,7 @@ int en_chunk(msd_ctx* ctx, Chunk& c, EnWork& E, int w0, int nw, int cap, bool fp
     }
     th.end(st);
     CKLAUNCH();
+    if (defer_det) return MSD_OK;   // the batched kernel and the final sum follow
     int slot = c.nR;
     void* Kss[2] = {E.Kaa, E.Kbb};
     th.begin("k_string_energy", st);
@@ -905,8 +911,14 @@ int en_chunk(msd_ctx* ctx, Chunk& c, EnWork& E, int w0, int nw, int cap, bool fp
 // Overlap (always), force bias (vbias != NULL) and local energy (e_loc !=
 // NULL) of n_w walkers, sharing the reference inverse, string minors and
 // CI weights between the last two.
-int evaluate(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b, double* ovlp, double* vbias,
-             double* e_loc, void* stream)
+struct Deferred {
+    Chunk c;
+    EnWork E;
+    int cap = 0;
+};
+
+int evaluate_impl(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b, double* ovlp, double* vbias,
+                  double* e_loc, void* stream, Deferred* defer)
 {
     cudaStream_t st = (cudaStream_t)stream;
     int rc = begin_call(ctx, n_w, phi_a, phi_b, st);
@@ -933,14 +945,31 @@ int evaluate(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b, do
     EnWork E;
     if (want_v && (rc = fb_alloc(ctx, cap, fp32, f))) return rc;
     if (want_e && (rc = en_alloc(ctx, cap, fp32, E))) return rc;
+    if (defer && (cap < n_w || !want_e || in.host_any || o_e.host || o_v.host || o_ov.host))
+        return fail(ctx, MSD_ERR_SHAPE, "batched evaluation needs device buffers, the energy output and all "
+                                        "walkers in one chunk (%d walkers, %d fit)", n_w, cap);
     for (int w0 = 0; w0 < n_w; w0 += cap) {
         const int nw = std::min(cap, n_w - w0);
         if ((rc = run_overlap_part(ctx, in, w0, nw, cap, c, true, fp32, st))) return rc;
         if (want_v && (rc = fb_chunk(ctx, c, f, w0, nw, cap, fp32, o_v.dev, want_e ? nullptr : o_ov.dev, st)))
             return rc;
-        if (want_e && (rc = en_chunk(ctx, c, E, w0, nw, cap, fp32, o_e.dev, o_ov.dev, st))) return rc;
+        if (want_e && (rc = en_chunk(ctx, c, E, w0, nw, cap, fp32, o_e.dev, o_ov.dev, st, defer != nullptr)))
+            return rc;
+    }
+    if (defer) {
+        defer->c = c;
+        defer->E = E;
+        defer->cap = cap;
+        CKLAUNCH();
+        return MSD_OK;
     }
     return finish(ctx, st, {&o_v, &o_e, &o_ov}, in.host_any);
+}
+
+int evaluate(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b, double* ovlp, double* vbias,
+             double* e_loc, void* stream)
+{
+    return evaluate_impl(ctx, n_w, phi_a, phi_b, ovlp, vbias, e_loc, stream, nullptr);
 }
 
 }  // namespace
@@ -1087,6 +1116,7 @@ int msd_set_precision(msd_ctx* ctx, int precision)
     if (!ctx) return MSD_ERR_ARG;
     if (precision != MSD_FP64 && precision != MSD_MIXED)
         return fail(ctx, MSD_ERR_ARG, "unknown precision %d", precision);
+    if (ctx->prec != precision) ctx->gen++;
     ctx->prec = precision;
     return MSD_OK;
 }
@@ -1357,3 +1387,426 @@ extern "C" int msd_overlap_noalloc(msd_ctx* ctx, int n_w, const double* phi_a, c
     }
     return MSD_OK;
 }
+
+// ========================================================================
+// Batched independent systems (uneven orbital, electron and determinant
+// counts) evaluated together: every system's overlap, force-bias and dense
+// energy steps, then the per-determinant energy terms of all systems in one
+// persistent launch (k_det_batched), then the final sums. The first call with
+// a given set of buffers runs eagerly and records the whole sequence as a
+// CUDA graph; later calls with the same buffers replay it with one graph
+// launch.
+#include <cinttypes>
+#include <fstream>
+#include <sstream>
+
+struct msd_batch {
+    std::vector<msd_ctx*> ctx;
+    int device = 0;
+    int n_sm = 152;
+    std::string err;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<long long> sig;
+    BatchSys* d_sys = nullptr;
+    size_t sys_cap = 0;
+    BatchItem* d_items = nullptr;
+    size_t items_cap = 0;
+    int n_items = 0;
+    unsigned* d_counter = nullptr;
+    size_t smem = 0;
+    bool fp32 = false;
+    int ctas_per_sm = 2, order = 0, bn = 0;
+    bool sync = true;
+    // systems run concurrently on these streams (graph branches when recorded)
+    static const int NSTREAM = 8;
+    cudaStream_t aux[NSTREAM] = {};
+    cudaEvent_t fork = nullptr, join[NSTREAM] = {};
+    long long graph_kernels = 0;
+};
+
+namespace {
+
+int bfail(msd_batch* b, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    b->err = buf;
+    return code;
+}
+
+#define BCK(call)                                                                         \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return bfail(b, MSD_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// Work items of one system in the slot layout of the per-system kernels
+// (same-spin strings of alpha then beta by level, then determinant buckets).
+void system_items(msd_ctx* ctx, int sys, int n_w, std::vector<BatchItem>& out, std::vector<double>& cost)
+{
+    SpinTables T[2] = {tables(ctx->sp[0], 1), tables(ctx->sp[1], 1)};
+    const PairTables pt = pair_tables(ctx->pairs);
+    const int nR = weights_blocks(T[0]);
+    for (int w = 0; w < n_w; ++w) {
+        int slot = nR;
+        for (int s = 0; s < 2; ++s)
+            for (int k = 1; k <= MSD_KMAX; ++k) {
+                const int ns = T[s].bucket[k + 1] - T[s].bucket[k];
+                const int nb = string_energy_blocks(T[s], k);
+                for (int blk = 0; blk < nb; ++blk) {
+                    out.push_back({sys, w, 0, s, k, 0, blk, slot++});
+                    const int cnt = std::min(SE_THREADS * SE_PER_THREAD, ns - blk * SE_THREADS * SE_PER_THREAD);
+                    cost.push_back((double)cnt * (2.0 * k * k * k * k + 2.0 * k * k));
+                }
+            }
+        for (int ka = 1; ka <= MSD_KMAX; ++ka)
+            for (int kb = 1; kb <= MSD_KMAX; ++kb) {
+                const int idx = ka * (MSD_KMAX + 1) + kb;
+                const int n = pt.bucket[idx + 1] - pt.bucket[idx];
+                if (n <= 0) continue;
+                const int nb = (n + PC_THREADS * PC_PER_THREAD - 1) / (PC_THREADS * PC_PER_THREAD);
+                for (int blk = 0; blk < nb; ++blk) {
+                    out.push_back({sys, w, 1, 0, ka, kb, blk, slot++});
+                    const int cnt = std::min(PC_THREADS * PC_PER_THREAD, n - blk * PC_THREADS * PC_PER_THREAD);
+                    cost.push_back((double)cnt * (ka * ka * kb * kb + ka * ka));
+                }
+            }
+    }
+}
+
+// Enqueue the whole batched evaluation on `st`. With upload, the system
+// descriptors and work items are (re)built and copied to the device first
+// (not done while recording a graph: the copies there are already current).
+int batch_run(msd_batch* b, const int* n_w, const double* const* pa, const double* const* pb,
+              double* const* ovlp, double* const* vbias, double* const* e_loc, cudaStream_t st, bool upload)
+{
+    const int n = (int)b->ctx.size();
+    std::vector<Deferred> d(n);
+    // fork: system i runs on aux[i % NSTREAM] after everything queued on st
+    BCK(cudaEventRecord(b->fork, st));
+    for (int k = 0; k < msd_batch::NSTREAM; ++k) BCK(cudaStreamWaitEvent(b->aux[k], b->fork, 0));
+    for (int i = 0; i < n; ++i) {
+        msd_ctx* ctx = b->ctx[i];
+        const bool saved = ctx->sync;
+        ctx->sync = false;
+        ctx->tc_bn = b->bn;
+        const int rc = evaluate_impl(ctx, n_w[i], pa[i], pb[i], ovlp ? ovlp[i] : nullptr,
+                                     vbias ? vbias[i] : nullptr, e_loc[i], b->aux[i % msd_batch::NSTREAM], &d[i]);
+        ctx->sync = saved;
+        if (rc) return bfail(b, rc, "system %d: %s", i, ctx->err.c_str());
+    }
+    // join
+    for (int k = 0; k < msd_batch::NSTREAM; ++k) {
+        BCK(cudaEventRecord(b->join[k], b->aux[k]));
+        BCK(cudaStreamWaitEvent(st, b->join[k], 0));
+    }
+    if (upload) {
+        std::vector<BatchSys> sys(n);
+        std::vector<BatchItem> items;
+        std::vector<double> cost;
+        size_t smem = 0;
+        for (int i = 0; i < n; ++i) {
+            msd_ctx* ctx = b->ctx[i];
+            const int cap = d[i].cap;
+            BatchSys& S = sys[i];
+            memset(&S, 0, sizeof S);
+            S.t[0] = tables(ctx->sp[0], cap);
+            S.t[1] = tables(ctx->sp[1], cap);
+            S.pt = pair_tables(ctx->pairs);
+            for (int s = 0; s < 2; ++s) {
+                S.r[s] = d[i].c.r[s];
+                S.wts[s] = d[i].c.wts[s];
+                S.B[s] = d[i].c.B[s];
+                S.Y[s] = d[i].E.Y[s];
+            }
+            S.K[0] = d[i].E.Kaa; S.K[1] = d[i].E.Kbb; S.K[2] = d[i].E.Kab;
+            S.part = d[i].c.part;
+            S.nslot = d[i].c.nslot;
+            const size_t X0 = (size_t)S.t[0].nh * S.t[0].np, X1 = (size_t)S.t[1].nh * S.t[1].np;
+            smem = std::max(smem, std::max(std::max(X0 * X0 + X0, X1 * X1 + X1), X0 * X1));
+            system_items(ctx, i, n_w[i], items, cost);
+        }
+        if (b->order == 1) {          // largest work first
+            std::vector<size_t> idx(items.size());
+            for (size_t k = 0; k < idx.size(); ++k) idx[k] = k;
+            std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+            std::vector<BatchItem> o(items.size());
+            for (size_t k = 0; k < idx.size(); ++k) o[k] = items[idx[k]];
+            items.swap(o);
+        } else if (b->order == 2) {   // walkers interleaved across systems
+            std::stable_sort(items.begin(), items.end(),
+                             [](const BatchItem& x, const BatchItem& y) { return x.w < y.w; });
+        }
+        b->smem = smem * (b->fp32 ? sizeof(float2) : sizeof(double2));
+        if (b->sys_cap < (size_t)n) {
+            cudaFree(b->d_sys);
+            BCK(cudaMalloc(&b->d_sys, sizeof(BatchSys) * n));
+            b->sys_cap = n;
+        }
+        if (b->items_cap < items.size()) {
+            cudaFree(b->d_items);
+            BCK(cudaMalloc(&b->d_items, sizeof(BatchItem) * items.size()));
+            b->items_cap = items.size();
+        }
+        BCK(cudaMemcpy(b->d_sys, sys.data(), sizeof(BatchSys) * n, cudaMemcpyHostToDevice));
+        BCK(cudaMemcpy(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice));
+        b->n_items = (int)items.size();
+    }
+    if (launch_det_batched(b->d_sys, b->d_items, b->n_items, b->d_counter, b->smem, b->fp32,
+                           b->ctas_per_sm * b->n_sm, st))
+        return bfail(b, MSD_ERR_CUDA, "persistent batched launch failed");
+    for (int i = 0; i < n; ++i) {
+        msd_ctx* ctx = b->ctx[i];
+        launch_final(n_w[i], d[i].c.part, d[i].c.nslot, d[i].c.nR, ctx->e0, (double2*)d[i].E.e1[0],
+                     (double2*)d[i].E.e1[1], (double2*)d[i].E.scal, d[i].c.O0[0], d[i].c.O0[1],
+                     (double2*)e_loc[i], ovlp && ovlp[i] ? (double2*)ovlp[i] : nullptr, st);
+    }
+    BCK(cudaGetLastError());
+    return MSD_OK;
+}
+
+int batch_check(msd_batch* b, cudaStream_t st)
+{
+    BCK(cudaStreamSynchronize(st));
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        msd_ctx* ctx = b->ctx[i];
+        unsigned e = 0;
+        BCK(cudaMemcpy(&e, ctx->d_err, sizeof e, cudaMemcpyDeviceToHost));
+        if (e & MSD_DEV_ERR_SINGULAR) return bfail(b, MSD_ERR_REF_SINGULAR, "system %zu: singular reference", i);
+        if (e & MSD_DEV_ERR_TIMEOUT) return bfail(b, MSD_ERR_TIMEOUT, "system %zu: a device wait expired", i);
+    }
+    return MSD_OK;
+}
+
+std::vector<long long> batch_signature(msd_batch* b, const int* n_w, const double* const* pa,
+                                       const double* const* pb, double* const* ovlp, double* const* vbias,
+                                       double* const* e_loc)
+{
+    std::vector<long long> s;
+    s.push_back(b->bn); s.push_back(b->ctas_per_sm); s.push_back(b->order);
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        s.push_back(n_w[i]);
+        s.push_back((long long)(uintptr_t)pa[i]);
+        s.push_back((long long)(uintptr_t)pb[i]);
+        s.push_back((long long)(uintptr_t)(ovlp ? ovlp[i] : nullptr));
+        s.push_back((long long)(uintptr_t)(vbias ? vbias[i] : nullptr));
+        s.push_back((long long)(uintptr_t)e_loc[i]);
+        s.push_back(b->ctx[i]->gen);
+    }
+    return s;
+}
+
+void drop_graph(msd_batch* b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    b->sig.clear();
+}
+
+std::string batch_key(msd_batch* b, const int* n_w)
+{
+    uint64_t h = 1469598103934665603ull;   // FNV-1a over the shapes
+    auto mix = [&](long long v) {
+        for (int k = 0; k < 8; ++k) { h ^= (uint64_t)((v >> (8 * k)) & 0xff); h *= 1099511628211ull; }
+    };
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        msd_ctx* c = b->ctx[i];
+        mix(c->M); mix(c->n[0]); mix(c->n[1]); mix(c->pairs.n_det); mix(c->n_chol); mix(n_w[i]); mix(c->prec);
+        mix(c->sp[0].n_str); mix(c->sp[1].n_str);
+    }
+    char buf[32];
+    snprintf(buf, sizeof buf, "%016" PRIx64, h);
+    return buf;
+}
+
+}  // namespace
+
+extern "C" {
+
+int msd_batch_create(msd_batch** out, msd_ctx* const* ctxs, int n_sys)
+{
+    if (!out || !ctxs || n_sys <= 0) return MSD_ERR_ARG;
+    *out = nullptr;
+    msd_batch* b = new msd_batch();
+    for (int i = 0; i < n_sys; ++i) {
+        if (!ctxs[i] || !ctxs[i]->have_ham || !ctxs[i]->have_trial) {
+            delete b;
+            return fail(nullptr, MSD_ERR_STATE, "batch: system %d is not set up", i);
+        }
+        if (i && (ctxs[i]->device != ctxs[0]->device || ctxs[i]->prec != ctxs[0]->prec)) {
+            delete b;
+            return fail(nullptr, MSD_ERR_ARG, "batch: all systems need one device and one precision");
+        }
+        b->ctx.push_back(ctxs[i]);
+    }
+    b->device = ctxs[0]->device;
+    b->fp32 = ctxs[0]->prec == MSD_MIXED;
+    cudaSetDevice(b->device);
+    cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, b->device);
+    bool ok = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaMalloc(&b->d_counter, sizeof(unsigned)) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; ok && k < msd_batch::NSTREAM; ++k)
+        ok = cudaStreamCreateWithFlags(&b->aux[k], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        delete b;
+        return fail(nullptr, MSD_ERR_CUDA, "batch: stream or counter allocation failed");
+    }
+    *out = b;
+    return MSD_OK;
+}
+
+void msd_batch_destroy(msd_batch* b)
+{
+    if (!b) return;
+    cudaSetDevice(b->device);
+    cudaDeviceSynchronize();
+    drop_graph(b);
+    cudaFree(b->d_sys); cudaFree(b->d_items); cudaFree(b->d_counter);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    for (int k = 0; k < msd_batch::NSTREAM; ++k) {
+        if (b->aux[k]) cudaStreamDestroy(b->aux[k]);
+        if (b->join[k]) cudaEventDestroy(b->join[k]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
+    delete b;
+}
+
+const char* msd_batch_last_error(const msd_batch* b) { return b ? b->err.c_str() : g_create_error.c_str(); }
+
+int msd_batch_evaluate(msd_batch* b, const int* n_w, const double* const* phi_a, const double* const* phi_b,
+                       double* const* ovlp, double* const* vbias, double* const* e_loc, void* stream)
+{
+    if (!b || !n_w || !phi_a || !phi_b || !e_loc) return b ? bfail(b, MSD_ERR_ARG, "null argument") : MSD_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    BCK(cudaSetDevice(b->device));
+    const std::vector<long long> sig = batch_signature(b, n_w, phi_a, phi_b, ovlp, vbias, e_loc);
+    if (b->exec && sig == b->sig) {
+        BCK(cudaGraphLaunch(b->exec, st));
+        return b->sync ? batch_check(b, st) : MSD_OK;
+    }
+    drop_graph(b);
+    std::vector<bool> timing(b->ctx.size());
+    int rc = batch_run(b, n_w, phi_a, phi_b, ovlp, vbias, e_loc, st, true);
+    if (rc) return rc;
+    if (b->sync && (rc = batch_check(b, st))) return rc;
+    // record the same sequence (no allocation can happen now: every buffer
+    // has its size) for replay by the next calls with these buffers
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        timing[i] = b->ctx[i]->timing;
+        msd_set_timing(b->ctx[i], 0);
+    }
+    BCK(cudaStreamSynchronize(st));
+    cudaGraph_t g = nullptr;
+    BCK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
+    rc = batch_run(b, n_w, phi_a, phi_b, ovlp, vbias, e_loc, b->cap, false);
+    const cudaError_t ce = cudaStreamEndCapture(b->cap, &g);
+    for (size_t i = 0; i < b->ctx.size(); ++i) msd_set_timing(b->ctx[i], timing[i] ? 1 : 0);
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    if (ce != cudaSuccess) return bfail(b, MSD_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+    size_t n_nodes = 0;
+    cudaGraphGetNodes(g, nullptr, &n_nodes);
+    std::vector<cudaGraphNode_t> nodes(n_nodes);
+    if (n_nodes) cudaGraphGetNodes(g, nodes.data(), &n_nodes);
+    b->graph_kernels = 0;
+    for (auto nd : nodes) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) b->graph_kernels++;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&b->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) { b->exec = nullptr; return bfail(b, MSD_ERR_CUDA, "graph instantiate failed"); }
+    b->sig = sig;
+    return MSD_OK;
+}
+
+int msd_batch_autotune(msd_batch* b, const int* n_w, const double* const* phi_a, const double* const* phi_b,
+                       double* const* ovlp, double* const* vbias, double* const* e_loc, void* stream,
+                       const char* cache_path)
+{
+    if (!b || !n_w || !phi_a || !phi_b || !e_loc) return b ? bfail(b, MSD_ERR_ARG, "null argument") : MSD_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    BCK(cudaSetDevice(b->device));
+    const std::string key = batch_key(b, n_w);
+    if (cache_path && *cache_path) {
+        std::ifstream f(cache_path);
+        std::string line;
+        while (std::getline(f, line)) {
+            std::istringstream is(line);
+            std::string k;
+            int bn, cps, ord;
+            if (is >> k >> bn >> cps >> ord && k == key) {
+                b->bn = bn; b->ctas_per_sm = cps; b->order = ord;
+                drop_graph(b);
+                return MSD_OK;
+            }
+        }
+    }
+    const int bns[2] = {128, 256}, cpss[3] = {1, 2, 4}, ords[3] = {0, 1, 2};
+    float best = 1e30f;
+    int bb = 0, bc = 2, bo = 0;
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0));
+    BCK(cudaEventCreate(&e1));
+    const bool saved_sync = b->sync;
+    b->sync = false;
+    int rc = MSD_OK;
+    for (int bn : bns)
+        for (int cps : cpss)
+            for (int ord : ords) {
+                b->bn = bn; b->ctas_per_sm = cps; b->order = ord;
+                if ((rc = batch_run(b, n_w, phi_a, phi_b, ovlp, vbias, e_loc, st, true))) goto done;
+                cudaEventRecord(e0, st);
+                for (int rep = 0; rep < 2; ++rep)
+                    if ((rc = batch_run(b, n_w, phi_a, phi_b, ovlp, vbias, e_loc, st, false))) goto done;
+                cudaEventRecord(e1, st);
+                if ((rc = batch_check(b, st))) goto done;
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) { best = ms; bb = bn; bc = cps; bo = ord; }
+            }
+done:
+    b->sync = saved_sync;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    b->bn = bb; b->ctas_per_sm = bc; b->order = bo;
+    drop_graph(b);
+    if (cache_path && *cache_path) {
+        std::ofstream f(cache_path, std::ios::app);
+        f << key << " " << bb << " " << bc << " " << bo << " " << best / 2 << "\n";
+    }
+    return MSD_OK;
+}
+
+int msd_batch_config(const msd_batch* b, int* tile_n, int* ctas_per_sm, int* order)
+{
+    if (!b) return MSD_ERR_ARG;
+    if (tile_n) *tile_n = b->bn;
+    if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
+    if (order) *order = b->order;
+    return MSD_OK;
+}
+
+int msd_batch_set_config(msd_batch* b, int tile_n, int ctas_per_sm, int order)
+{
+    if (!b || (tile_n != 0 && tile_n != 128 && tile_n != 256) || ctas_per_sm < 1 || ctas_per_sm > 8 ||
+        order < 0 || order > 2)
+        return b ? bfail(b, MSD_ERR_ARG, "bad batch configuration") : MSD_ERR_ARG;
+    b->bn = tile_n; b->ctas_per_sm = ctas_per_sm; b->order = order;
+    drop_graph(b);
+    return MSD_OK;
+}
+
+int msd_batch_graph_ready(const msd_batch* b) { return b && b->exec ? 1 : 0; }
+
+long long msd_batch_graph_kernels(const msd_batch* b) { return b && b->exec ? b->graph_kernels : 0; }
+
+}  // extern "C"

@@ -385,12 +385,14 @@ int grid_for(long long n) { return (int)((n + 255) / 256 < 152 * 16 ? (n + 255) 
 }  // namespace
 
 int tc_gemm_3xtf32(const TcOperand& A, const TcOperand& B, int Mr, int Nc, int K, float* C, long long ldc,
-                   unsigned* err, cudaStream_t st, int splits, long long c_split_stride)
+                   unsigned* err, cudaStream_t st, int splits, long long c_split_stride, int bn)
 {
     if (K <= 0 || K % 32 || A.ld % 4 || B.ld % 4 || Mr <= 0 || Nc <= 0) return -1;
     if (splits < 1 || splits > K / 32) return -1;
-    if (Nc >= 256) return launch_bn<256>(A, B, Mr, Nc, K, C, ldc, splits, c_split_stride, err, st);
-    return launch_bn<128>(A, B, Mr, Nc, K, C, ldc, splits, c_split_stride, err, st);
+    if (bn == 0) bn = Nc >= 256 ? 256 : 128;
+    if (bn == 256) return launch_bn<256>(A, B, Mr, Nc, K, C, ldc, splits, c_split_stride, err, st);
+    if (bn == 128) return launch_bn<128>(A, B, Mr, Nc, K, C, ldc, splits, c_split_stride, err, st);
+    return -1;
 }
 
 void launch_split_complex_rows(int nb, int R, int Kg, int Kp, const double2* src, long long src_ld,

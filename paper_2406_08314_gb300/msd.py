@@ -23,7 +23,9 @@ EXPORTS = ["msd_create", "msd_destroy", "msd_last_error", "msd_set_hamiltonian",
            "msd_set_precision", "msd_overlap", "msd_det_ratios", "msd_force_bias",
            "msd_local_energy", "msd_evaluate", "msd_info", "msd_set_timing", "msd_reset_stats",
            "msd_kernel_count", "msd_kernel_stat", "msd_set_workspace_limit", "msd_set_sync",
-           "msd_launch_count", "msd_overlap_noalloc"]
+           "msd_launch_count", "msd_overlap_noalloc", "msd_batch_create", "msd_batch_destroy",
+           "msd_batch_last_error", "msd_batch_evaluate", "msd_batch_autotune", "msd_batch_config",
+           "msd_batch_set_config", "msd_batch_graph_ready", "msd_batch_graph_kernels"]
 INFO = {"n_det": 1, "n_chol": 2, "n_strings_a": 3, "n_strings_b": 4, "n_holes_a": 5,
         "n_parts_a": 6, "n_holes_b": 7, "n_parts_b": 8, "workspace_bytes": 9, "walker_chunk": 10}
 
@@ -67,6 +69,19 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         if f not in ("msd_destroy", "msd_last_error"):
             getattr(lib, f).restype = ci
     lib.msd_launch_count.restype = ctypes.c_longlong
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    lib.msd_batch_create.argtypes = [ctypes.POINTER(vp), pp, ci]
+    lib.msd_batch_destroy.argtypes = [vp]
+    lib.msd_batch_destroy.restype = None
+    lib.msd_batch_last_error.argtypes = [vp]
+    lib.msd_batch_last_error.restype = ctypes.c_char_p
+    lib.msd_batch_evaluate.argtypes = [vp, ctypes.POINTER(ci), pp, pp, pp, pp, pp, vp]
+    lib.msd_batch_autotune.argtypes = [vp, ctypes.POINTER(ci), pp, pp, pp, pp, pp, vp, ctypes.c_char_p]
+    lib.msd_batch_config.argtypes = [vp, ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(ci)]
+    lib.msd_batch_set_config.argtypes = [vp, ci, ci, ci]
+    lib.msd_batch_graph_ready.argtypes = [vp]
+    lib.msd_batch_graph_kernels.argtypes = [vp]
+    lib.msd_batch_graph_kernels.restype = ctypes.c_longlong
     return lib
 
 
@@ -248,3 +263,78 @@ class Context:
 
     def set_sync(self, sync: bool):
         self._check(_lib.msd_set_sync(self._h, int(bool(sync))))
+
+
+class Batch:
+    """Independent systems evaluated together (msd_batch_*): one persistent
+    launch for the per-determinant terms of all systems, recorded as a CUDA
+    graph and replayed while the buffers stay the same."""
+
+    def __init__(self, contexts):
+        self.contexts = list(contexts)
+        arr = (ctypes.c_void_p * len(self.contexts))(*[c._h.value for c in self.contexts])
+        h = ctypes.c_void_p()
+        rc = _lib.msd_batch_create(ctypes.byref(h), arr, len(self.contexts))
+        if rc:
+            raise MSDError(rc, _lib.msd_last_error(None).decode())
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.msd_batch_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def _check(self, rc):
+        if rc:
+            raise MSDError(rc, _lib.msd_batch_last_error(self._h).decode())
+
+    def _args(self, walkers, outs):
+        n = len(self.contexts)
+        nw = (ctypes.c_int * n)(*[int(a.shape[0]) for a, _ in walkers])
+        P = ctypes.c_void_p * n
+        pa = P(*[a.data_ptr() for a, _ in walkers])
+        pb = P(*[b.data_ptr() for _, b in walkers])
+        ov = P(*[o.data_ptr() for o, _, _ in outs])
+        vb = P(*[v.data_ptr() for _, v, _ in outs])
+        el = P(*[e.data_ptr() for _, _, e in outs])
+        return nw, pa, pb, ov, vb, el
+
+    def outputs(self, walkers):
+        import torch
+        return [(torch.empty((a.shape[0],), dtype=torch.complex128, device=a.device),
+                 torch.empty((a.shape[0], c.n_chol), dtype=torch.complex128, device=a.device),
+                 torch.empty((a.shape[0],), dtype=torch.complex128, device=a.device))
+                for (a, _), c in zip(walkers, self.contexts)]
+
+    def evaluate(self, walkers, outs=None, stream=None):
+        """walkers: [(phi_a, phi_b)] device tensors per system; returns
+        [(ovlp, vbias, e_loc)] per system."""
+        import torch
+        outs = outs if outs is not None else self.outputs(walkers)
+        st = ctypes.c_void_p(int(stream) if stream is not None else torch.cuda.current_stream().cuda_stream)
+        self._check(_lib.msd_batch_evaluate(self._h, *self._args(walkers, outs), st))
+        return outs
+
+    def autotune(self, walkers, outs=None, cache_path=None, stream=None):
+        import torch
+        outs = outs if outs is not None else self.outputs(walkers)
+        st = ctypes.c_void_p(int(stream) if stream is not None else torch.cuda.current_stream().cuda_stream)
+        cp = cache_path.encode() if cache_path else None
+        self._check(_lib.msd_batch_autotune(self._h, *self._args(walkers, outs), st, cp))
+        return self.config()
+
+    def config(self):
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(_lib.msd_batch_config(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"tile_n": a.value, "ctas_per_sm": b.value, "order": c.value}
+
+    def set_config(self, tile_n=0, ctas_per_sm=2, order=0):
+        self._check(_lib.msd_batch_set_config(self._h, tile_n, ctas_per_sm, order))
+
+    def graph_ready(self) -> bool:
+        return bool(_lib.msd_batch_graph_ready(self._h))
+
+    def graph_kernels(self) -> int:
+        return int(_lib.msd_batch_graph_kernels(self._h))
