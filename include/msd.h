@@ -224,6 +224,50 @@ int msd_batch_graph_ready(const msd_batch* b);
 /* Kernel nodes in the recorded graph (kernels one replay launches), or 0. */
 long long msd_batch_graph_kernels(const msd_batch* b);
 
+/* ---- Learned control variate --------------------------------------------
+   (The paper has no counterpart.) A small MLP predicts the real part of the
+   local energy from active-space features of the reference Green's function;
+   evaluated on every walker it serves as a control variate: the estimator
+   mean_i f(x_i) + mean_{i in S}(E_L,i - f(x_i)) over a random subsample S
+   stays unbiased while the exact path runs only on S. */
+
+/* Features per walker: feat[w][s][p][q][c] = (Re, Im) of
+   G^s[n_core + p][n_core + q], p, q < n_act (G = <a+_p a_q> of the reference
+   determinant, Eq. 14), FP32, 4 * n_act^2 floats per walker; feat must be
+   device memory. */
+int msd_features(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b, int n_core,
+                 int n_act, float* feat, void* stream);
+
+/* Features per walker: the non-zero rows of G (the rows of the reference
+   determinant's occupied orbitals, all M columns), alpha then beta:
+   feat[w * ld + 2 (j M + q) + c], 2 (N_a + N_b) M floats, the rest of the
+   row (up to ld) zero. feat must be device memory. */
+int msd_features_rows(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b, int ld,
+                      float* feat, void* stream);
+
+/* Network x (n_in) -> 3 hidden layers of `width` with GELU -> scalar; BF16
+   weights and activations, FP32 accumulation on the tensor cores, FP32 master
+   parameters. n_in and width must be multiples of 64 (MSD_ERR_SHAPE).
+   Parameter layout (FP32): W0 [width][n_in], b0 [width], W1 [width][width],
+   b1, W2 [width][width], b2, w3 [width], b3 [1]. */
+typedef struct msd_mlp msd_mlp;
+int msd_mlp_create(msd_mlp** out, int n_in, int width, int device);
+void msd_mlp_destroy(msd_mlp* m);
+const char* msd_mlp_last_error(const msd_mlp* m);
+long long msd_mlp_param_count(const msd_mlp* m);
+/* Host parameter copies; setting resets the optimiser state. */
+int msd_mlp_set_params(msd_mlp* m, const float* params);
+int msd_mlp_get_params(msd_mlp* m, float* params);
+/* y[b] = f(x[b]) for x [batch][n_in] (device FP32) -> y [batch] (device). */
+int msd_mlp_forward(msd_mlp* m, int batch, const float* x, float* y, void* stream);
+/* Loss (1/B) sum_b (f(x_b) - t_b)^2 and its gradient with respect to every
+   parameter (kept for msd_mlp_adam_step; copied to grads, device, if not
+   NULL; loss a device scalar, may be NULL). batch <= 65536. */
+int msd_mlp_grad(msd_mlp* m, int batch, const float* x, const float* target, float* grads,
+                 float* loss, void* stream);
+/* One Adam step (Kingma and Ba) with the last gradients. */
+int msd_mlp_adam_step(msd_mlp* m, float lr, float beta1, float beta2, float eps, void* stream);
+
 /* Trial overlap without any device allocation during the call. The paper
    has no counterpart: this serves callers that cannot let a library call
    cudaMalloc / cudaFree, such as a framework that owns all device memory

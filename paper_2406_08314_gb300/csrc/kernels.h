@@ -71,6 +71,10 @@ struct TcOperand {
 // bn: output tile width (128 or 256; 0 picks by Nc).
 int tc_gemm_3xtf32(const TcOperand& A, const TcOperand& B, int Mr, int Nc, int K, float* C, long long ldc,
                    unsigned* err, cudaStream_t st, int splits = 1, long long c_split_stride = 0, int bn = 0);
+// BF16 tensor-core GEMM C[m][n] = sum_k A[m][k] B[n][k] (FP32 accumulation;
+// A, B row-major BF16 with K contiguous, K a multiple of 64).
+int tc_gemm_bf16(const void* A, long long lda, const void* B, long long ldb, int Mr, int Nc, int K, float* C,
+                 long long ldc, unsigned* err, cudaStream_t st);
 void launch_split_complex_rows(int nb, int R, int Kg, int Kp, const double2* src, long long src_ld,
                                const int* cols, float* hi, float* lo, cudaStream_t st);
 void launch_split_real_rows(long long R, int Kg, int Kp, const double* src, long long src_ld, const int* cols,
@@ -112,3 +116,9 @@ struct BatchItem {
 };
 int launch_det_batched(const BatchSys* systems, const BatchItem* items, int n_items, unsigned* counter,
                        size_t smem, bool fp32, int grid, cudaStream_t st);
+
+// mlp.cu
+void launch_features(int nw, int M, int N, int n_core, int n_act, const int* pos0, const double2* Gr, float* feat,
+                     int spin, cudaStream_t st);
+void launch_features_rows(int nw, int M, int N, const double2* Gr, float* feat, long long ld, long long off,
+                          cudaStream_t st);

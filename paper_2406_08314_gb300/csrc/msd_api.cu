@@ -38,6 +38,7 @@ struct SpinHost {
     int *d_csr_off = nullptr, *d_csr_other = nullptr;
     double* d_csr_c = nullptr;
     double* d_Lh = nullptr;   // [n_chol][N + np][M]
+    int* d_pos0 = nullptr;    // [M] position of an orbital in occ0, or -1
 };
 
 struct PairHost {
@@ -351,6 +352,9 @@ int upload_spin(msd_ctx* ctx, SpinHost& S)
     if ((rc = upload(ctx, &S.d_csr_off, S.csr_off))) return rc;
     if ((rc = upload(ctx, &S.d_csr_other, S.csr_other))) return rc;
     if ((rc = upload(ctx, &S.d_csr_c, S.csr_c))) return rc;
+    std::vector<int> pos0(ctx->M, -1);
+    for (int j = 0; j < S.N; ++j) pos0[S.occ0[j]] = j;
+    if ((rc = upload(ctx, &S.d_pos0, pos0))) return rc;
     return MSD_OK;
 }
 
@@ -358,7 +362,8 @@ void free_spin(SpinHost& S)
 {
     cudaFree(S.d_occ0); cudaFree(S.d_hole_pos); cudaFree(S.d_part_orb); cudaFree(S.d_str_h);
     cudaFree(S.d_str_p); cudaFree(S.d_str_sign); cudaFree(S.d_csr_off); cudaFree(S.d_csr_other);
-    cudaFree(S.d_csr_c); cudaFree(S.d_Lh);
+    cudaFree(S.d_csr_c); cudaFree(S.d_Lh); cudaFree(S.d_pos0);
+    S.d_pos0 = nullptr;
     S.d_occ0 = S.d_hole_pos = S.d_part_orb = nullptr;
     S.d_str_h = S.d_str_p = nullptr;
     S.d_str_sign = nullptr;
@@ -1199,6 +1204,72 @@ int msd_evaluate(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b
 {
     if (ctx && n_w > 0 && !ovlp && !vbias && !e_loc) return fail(ctx, MSD_ERR_ARG, "no output requested");
     return evaluate(ctx, n_w, phi_a, phi_b, ovlp, vbias, e_loc, stream);
+}
+
+int msd_features(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b, int n_core, int n_act,
+                 float* feat, void* stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = begin_call(ctx, n_w, phi_a, phi_b, st);
+    if (rc) return rc;
+    if (n_core < 0 || n_act <= 0 || n_core + n_act > ctx->M)
+        return fail(ctx, MSD_ERR_ARG, "active window [%d, %d) outside the %d orbitals", n_core, n_core + n_act, ctx->M);
+    if (n_w == 0) return MSD_OK;
+    if (!feat || !is_device_ptr(feat)) return fail(ctx, MSD_ERR_ARG, "feat must be a device pointer");
+    Staged in;
+    if ((rc = stage_inputs(ctx, n_w, phi_a, phi_b, st, in))) return rc;
+    const int nR = weights_blocks(tables(ctx->sp[0], 1));
+    const int cap = chunk_for(ctx, overlap_bytes_per_walker(ctx, false, nR), n_w);
+    Chunk c;
+    if ((rc = chunk_alloc(ctx, cap, false, nR, c))) return rc;
+    const int M = ctx->M;
+    for (int w0 = 0; w0 < n_w; w0 += cap) {
+        const int nw = std::min(cap, n_w - w0);
+        const double2* phi[2] = {in.pa + (size_t)w0 * M * ctx->n[0], in.pb + (size_t)w0 * M * ctx->n[1]};
+        for (int s = 0; s < 2; ++s) {
+            const SpinTables T = tables(ctx->sp[s], cap);
+            launch_ref(phi[s], nw, M, ctx->n[s], T, c.Gr[s], c.O0[s], c.Gact[s], ctx->d_err, st);
+            launch_features(nw, M, ctx->n[s], n_core, n_act, ctx->sp[s].d_pos0, c.Gr[s],
+                            feat + (size_t)w0 * 2 * 2 * n_act * n_act, s, st);
+        }
+        CKLAUNCH();
+    }
+    Out none;
+    return finish(ctx, st, {&none}, in.host_any);
+}
+
+int msd_features_rows(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b, int ld, float* feat,
+                      void* stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = begin_call(ctx, n_w, phi_a, phi_b, st);
+    if (rc) return rc;
+    const long long need = 2LL * (ctx->n[0] + ctx->n[1]) * ctx->M;
+    if (ld < need) return fail(ctx, MSD_ERR_ARG, "ld = %d below the %lld features per walker", ld, need);
+    if (n_w == 0) return MSD_OK;
+    if (!feat || !is_device_ptr(feat)) return fail(ctx, MSD_ERR_ARG, "feat must be a device pointer");
+    Staged in;
+    if ((rc = stage_inputs(ctx, n_w, phi_a, phi_b, st, in))) return rc;
+    const int nR = weights_blocks(tables(ctx->sp[0], 1));
+    const int cap = chunk_for(ctx, overlap_bytes_per_walker(ctx, false, nR), n_w);
+    Chunk c;
+    if ((rc = chunk_alloc(ctx, cap, false, nR, c))) return rc;
+    const int M = ctx->M;
+    if (ld > need) CK(cudaMemsetAsync(feat, 0, sizeof(float) * (size_t)n_w * ld, st));
+    for (int w0 = 0; w0 < n_w; w0 += cap) {
+        const int nw = std::min(cap, n_w - w0);
+        const double2* phi[2] = {in.pa + (size_t)w0 * M * ctx->n[0], in.pb + (size_t)w0 * M * ctx->n[1]};
+        long long off = 0;
+        for (int s = 0; s < 2; ++s) {
+            const SpinTables T = tables(ctx->sp[s], cap);
+            launch_ref(phi[s], nw, M, ctx->n[s], T, c.Gr[s], c.O0[s], c.Gact[s], ctx->d_err, st);
+            launch_features_rows(nw, M, ctx->n[s], c.Gr[s], feat + (size_t)w0 * ld, ld, off, st);
+            off += 2LL * ctx->n[s] * M;
+        }
+        CKLAUNCH();
+    }
+    Out none;
+    return finish(ctx, st, {&none}, in.host_any);
 }
 
 int msd_info(const msd_ctx* ctx, int key, long long* value)

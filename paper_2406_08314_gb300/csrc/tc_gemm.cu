@@ -125,25 +125,46 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <int BN>
+// SPLIT: 3xTF32 (hi/lo operands, three products per K step) or a single
+// BF16 product. One k-block is 128 bytes of K per row in both cases
+// (32 FP32 or 64 BF16 elements); one MMA covers 32 bytes of K.
+template <int BN, bool SPLIT>
 struct TcCfg {
-    static constexpr int BM = 128, BK = 32;
-    static constexpr int STAGES = BN >= 256 ? 2 : 3;
-    static constexpr uint32_t A_BYTES = BM * BK * 4;
-    static constexpr uint32_t B_BYTES = BN * BK * 4;
-    static constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+    static constexpr int BM = 128;
+    static constexpr int BK = SPLIT ? 32 : 64;   // elements per k-block
+    static constexpr int NOPS = SPLIT ? 2 : 1;   // hi/lo copies of each operand
+    static constexpr int STAGES = SPLIT ? (BN >= 256 ? 2 : 3) : (BN >= 256 ? 4 : 6);
+    static constexpr uint32_t A_BYTES = BM * 128;
+    static constexpr uint32_t B_BYTES = BN * 128;
+    static constexpr uint32_t STAGE_BYTES = NOPS * (A_BYTES + B_BYTES);
     static constexpr uint32_t TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
     static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
 };
 
-template <int BN>
+// Instruction descriptor of kind::f16 with BF16 A and B, FP32 accumulator.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+template <int BN, bool SPLIT>
 __global__ void __launch_bounds__(128, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
           const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
           int Mr, int Nc, int K, float* __restrict__ C, long long ldc, long long c_split_stride,
           unsigned* err)
 {
-    using Cfg = TcCfg<BN>;
+    using Cfg = TcCfg<BN, SPLIT>;
     constexpr int BM = Cfg::BM, BK = Cfg::BK, STAGES = Cfg::STAGES;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -188,9 +209,11 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
             mbar_expect_tx(&full_bar[s], Cfg::STAGE_BYTES);
             const int kx = (kb0 + kb) * BK;
             tma_load_2d(st, &ta_hi, &full_bar[s], kx, m0);
-            tma_load_2d(st + Cfg::A_BYTES, &ta_lo, &full_bar[s], kx, m0);
-            tma_load_2d(st + 2 * Cfg::A_BYTES, &tb_hi, &full_bar[s], kx, n0);
-            tma_load_2d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, &tb_lo, &full_bar[s], kx, n0);
+            tma_load_2d(st + Cfg::NOPS * Cfg::A_BYTES, &tb_hi, &full_bar[s], kx, n0);
+            if (SPLIT) {
+                tma_load_2d(st + Cfg::A_BYTES, &ta_lo, &full_bar[s], kx, m0);
+                tma_load_2d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, &tb_lo, &full_bar[s], kx, n0);
+            }
             issued = kb + 1;
         }
         if (fail) {
@@ -200,7 +223,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
-        constexpr uint32_t idesc = idesc_tf32(BM, BN);
+        constexpr uint32_t idesc = SPLIT ? idesc_tf32(BM, BN) : idesc_bf16(BM, BN);
         for (int kb = 0; kb < nkb; ++kb) {
             const int s = kb % STAGES;
             const uint32_t ph = (kb / STAGES) & 1;
@@ -208,14 +231,18 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
             tc_fence_after();
             const uint32_t sa = su32(smem + (size_t)s * Cfg::STAGE_BYTES);
 #pragma unroll
-            for (int kk = 0; kk < BK / 8; ++kk) {
+            for (int kk = 0; kk < 4; ++kk) {   // 4 x 32 bytes of K per k-block
                 const uint64_t ah = sw128_desc(sa + kk * 32);
-                const uint64_t al = sw128_desc(sa + Cfg::A_BYTES + kk * 32);
-                const uint64_t bh = sw128_desc(sa + 2 * Cfg::A_BYTES + kk * 32);
-                const uint64_t bl = sw128_desc(sa + 2 * Cfg::A_BYTES + Cfg::B_BYTES + kk * 32);
-                mma_tf32(tmem, ah, bh, idesc, (kb | kk) != 0);
-                mma_tf32(tmem, ah, bl, idesc, 1u);
-                mma_tf32(tmem, al, bh, idesc, 1u);
+                const uint64_t bh = sw128_desc(sa + Cfg::NOPS * Cfg::A_BYTES + kk * 32);
+                if (SPLIT) {
+                    const uint64_t al = sw128_desc(sa + Cfg::A_BYTES + kk * 32);
+                    const uint64_t bl = sw128_desc(sa + 2 * Cfg::A_BYTES + Cfg::B_BYTES + kk * 32);
+                    mma_tf32(tmem, ah, bh, idesc, (kb | kk) != 0);
+                    mma_tf32(tmem, ah, bl, idesc, 1u);
+                    mma_tf32(tmem, al, bh, idesc, 1u);
+                } else {
+                    mma_bf16(tmem, ah, bh, idesc, (kb | kk) != 0);
+                }
             }
             mma_commit(&empty_bar[s]);
         }
@@ -265,40 +292,47 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-// 2-D FP32 tensor [outer][inner] with row pitch `ld` elements; 32 x box_outer
-// boxes with 128-byte swizzle.
-int make_map(CUtensorMap* map, const float* base, int inner, int outer, long long ld, int box_outer)
+// 2-D tensor [outer][inner] (FP32 or BF16) with row pitch `ld` elements;
+// boxes of 128 bytes x box_outer rows with 128-byte swizzle.
+int make_map(CUtensorMap* map, const void* base, int inner, int outer, long long ld, int box_outer, bool bf16)
 {
     auto fn = encode_fn();
     if (!fn) return -1;
+    const int esz = bf16 ? 2 : 4;
     cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
-    cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
-    cuuint32_t box[2] = {32, (cuuint32_t)box_outer};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * esz};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_outer};
     cuuint32_t es[2] = {1, 1};
-    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, es,
+    CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base,
+                    dims, strides, box, es,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? 0 : -1;
 }
 
-template <int BN>
-int launch_bn(const TcOperand& A, const TcOperand& B, int Mr, int Nc, int K, float* C, long long ldc,
-              int splits, long long c_split_stride, unsigned* err, cudaStream_t st)
+template <int BN, bool SPLIT>
+int launch_bn(const void* a_hi, const void* a_lo, long long lda, const void* b_hi, const void* b_lo, long long ldb,
+              int Mr, int Nc, int K, float* C, long long ldc, int splits, long long c_split_stride, unsigned* err,
+              cudaStream_t st)
 {
     CUtensorMap ah, al, bh, bl;
-    if (make_map(&ah, A.hi, K, Mr, A.ld, 128) || make_map(&al, A.lo, K, Mr, A.ld, 128) ||
-        make_map(&bh, B.hi, K, Nc, B.ld, BN) || make_map(&bl, B.lo, K, Nc, B.ld, BN))
-        return -1;
-    using Cfg = TcCfg<BN>;
+    if (make_map(&ah, a_hi, K, Mr, lda, 128, !SPLIT) || make_map(&bh, b_hi, K, Nc, ldb, BN, !SPLIT)) return -1;
+    if (SPLIT) {
+        if (make_map(&al, a_lo, K, Mr, lda, 128, false) || make_map(&bl, b_lo, K, Nc, ldb, BN, false)) return -1;
+    } else {
+        al = ah;
+        bl = bh;
+    }
+    using Cfg = TcCfg<BN, SPLIT>;
     static bool attr = false;
     if (!attr) {
-        if (cudaFuncSetAttribute(k_tc_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM) !=
-            cudaSuccess)
+        if (cudaFuncSetAttribute(k_tc_gemm<BN, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Cfg::SMEM) != cudaSuccess)
             return -1;
         attr = true;
     }
     dim3 grid((Nc + BN - 1) / BN, (Mr + 127) / 128, splits);
-    k_tc_gemm<BN><<<grid, 128, Cfg::SMEM, st>>>(ah, al, bh, bl, Mr, Nc, K, C, ldc, c_split_stride, err);
+    k_tc_gemm<BN, SPLIT><<<grid, 128, Cfg::SMEM, st>>>(ah, al, bh, bl, Mr, Nc, K, C, ldc, c_split_stride, err);
     msd_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -390,9 +424,21 @@ int tc_gemm_3xtf32(const TcOperand& A, const TcOperand& B, int Mr, int Nc, int K
     if (K <= 0 || K % 32 || A.ld % 4 || B.ld % 4 || Mr <= 0 || Nc <= 0) return -1;
     if (splits < 1 || splits > K / 32) return -1;
     if (bn == 0) bn = Nc >= 256 ? 256 : 128;
-    if (bn == 256) return launch_bn<256>(A, B, Mr, Nc, K, C, ldc, splits, c_split_stride, err, st);
-    if (bn == 128) return launch_bn<128>(A, B, Mr, Nc, K, C, ldc, splits, c_split_stride, err, st);
+    if (bn == 256)
+        return launch_bn<256, true>(A.hi, A.lo, A.ld, B.hi, B.lo, B.ld, Mr, Nc, K, C, ldc, splits, c_split_stride,
+                                    err, st);
+    if (bn == 128)
+        return launch_bn<128, true>(A.hi, A.lo, A.ld, B.hi, B.lo, B.ld, Mr, Nc, K, C, ldc, splits, c_split_stride,
+                                    err, st);
     return -1;
+}
+
+int tc_gemm_bf16(const void* A, long long lda, const void* B, long long ldb, int Mr, int Nc, int K, float* C,
+                 long long ldc, unsigned* err, cudaStream_t st)
+{
+    if (K <= 0 || K % 64 || lda % 8 || ldb % 8 || Mr <= 0 || Nc <= 0) return -1;
+    if (Nc > 128) return launch_bn<256, false>(A, nullptr, lda, B, nullptr, ldb, Mr, Nc, K, C, ldc, 1, 0, err, st);
+    return launch_bn<128, false>(A, nullptr, lda, B, nullptr, ldb, Mr, Nc, K, C, ldc, 1, 0, err, st);
 }
 
 void launch_split_complex_rows(int nb, int R, int Kg, int Kp, const double2* src, long long src_ld,

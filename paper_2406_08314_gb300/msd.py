@@ -25,7 +25,9 @@ EXPORTS = ["msd_create", "msd_destroy", "msd_last_error", "msd_set_hamiltonian",
            "msd_kernel_count", "msd_kernel_stat", "msd_set_workspace_limit", "msd_set_sync",
            "msd_launch_count", "msd_overlap_noalloc", "msd_batch_create", "msd_batch_destroy",
            "msd_batch_last_error", "msd_batch_evaluate", "msd_batch_autotune", "msd_batch_config",
-           "msd_batch_set_config", "msd_batch_graph_ready", "msd_batch_graph_kernels"]
+           "msd_batch_set_config", "msd_batch_graph_ready", "msd_batch_graph_kernels", "msd_features", "msd_features_rows",
+           "msd_mlp_create", "msd_mlp_destroy", "msd_mlp_last_error", "msd_mlp_param_count",
+           "msd_mlp_set_params", "msd_mlp_get_params", "msd_mlp_forward", "msd_mlp_grad", "msd_mlp_adam_step"]
 INFO = {"n_det": 1, "n_chol": 2, "n_strings_a": 3, "n_strings_b": 4, "n_holes_a": 5,
         "n_parts_a": 6, "n_holes_b": 7, "n_parts_b": 8, "workspace_bytes": 9, "walker_chunk": 10}
 
@@ -82,6 +84,20 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.msd_batch_graph_ready.argtypes = [vp]
     lib.msd_batch_graph_kernels.argtypes = [vp]
     lib.msd_batch_graph_kernels.restype = ctypes.c_longlong
+    lib.msd_features.argtypes = [vp, ci, vp, vp, ci, ci, vp, vp]
+    lib.msd_features_rows.argtypes = [vp, ci, vp, vp, ci, vp, vp]
+    lib.msd_mlp_create.argtypes = [ctypes.POINTER(vp), ci, ci, ci]
+    lib.msd_mlp_destroy.argtypes = [vp]
+    lib.msd_mlp_destroy.restype = None
+    lib.msd_mlp_last_error.argtypes = [vp]
+    lib.msd_mlp_last_error.restype = ctypes.c_char_p
+    lib.msd_mlp_param_count.argtypes = [vp]
+    lib.msd_mlp_param_count.restype = ctypes.c_longlong
+    lib.msd_mlp_set_params.argtypes = [vp, vp]
+    lib.msd_mlp_get_params.argtypes = [vp, vp]
+    lib.msd_mlp_forward.argtypes = [vp, ci, vp, vp, vp]
+    lib.msd_mlp_grad.argtypes = [vp, ci, vp, vp, vp, vp, vp]
+    lib.msd_mlp_adam_step.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, vp]
     return lib
 
 
@@ -203,6 +219,29 @@ class Context:
         self._check(_lib.msd_overlap_noalloc(self._h, n_w, _ptr(phi_a), _ptr(phi_b), _ptr(ovlp),
                                              _ptr(ratio_sum), self._stream(phi_a, stream)))
         return ovlp, ratio_sum
+
+    def features(self, phi_a, phi_b, n_core, n_act, stream=None):
+        """Active-space reference Green's function features, FP32
+        [n_w][2][n_act][n_act][2] (device)."""
+        import torch
+        n_w = self._walkers(phi_a, phi_b)
+        f = torch.empty((n_w, 2, n_act, n_act, 2), dtype=torch.float32, device=phi_a.device)
+        self._check(_lib.msd_features(self._h, n_w, _ptr(phi_a), _ptr(phi_b), int(n_core), int(n_act),
+                                      ctypes.c_void_p(f.data_ptr()), self._stream(phi_a, stream)))
+        return f
+
+    def features_rows(self, phi_a, phi_b, stream=None):
+        """Non-zero rows of the reference Green's function, FP32
+        [n_w][ld], ld = 2 (N_a + N_b) M rounded up to a multiple of 64
+        (zero padded)."""
+        import torch
+        n_w = self._walkers(phi_a, phi_b)
+        need = 2 * (self.n_alpha + self.n_beta) * self.M
+        ld = (need + 63) // 64 * 64
+        f = torch.empty((n_w, ld), dtype=torch.float32, device=phi_a.device)
+        self._check(_lib.msd_features_rows(self._h, n_w, _ptr(phi_a), _ptr(phi_b), ld,
+                                           ctypes.c_void_p(f.data_ptr()), self._stream(phi_a, stream)))
+        return f
 
     def det_ratios(self, phi_a, phi_b, stream=None, ref_ovlp=False):
         n_w = self._walkers(phi_a, phi_b)

@@ -308,3 +308,19 @@ def batched_systems(n_systems: int = 32, seed0: int = 0, n_w: int = 128,
         sys.meta["name"] = f"batched[{i}]"
         out.append((sys, w))
     return out
+
+
+def make_walkers_varied(rng: np.random.Generator, M: int, n_alpha: int, n_beta: int,
+                        n_w: int, noise_range=(0.05, 0.35)) -> Walkers:
+    """Walkers QR(D0 + s_w (X + iY)/sqrt(2)) with a noise level s_w drawn
+    uniformly per walker (training and held-out sets of the control
+    variate)."""
+    s = rng.uniform(noise_range[0], noise_range[1], size=n_w)
+    out = []
+    for n in (n_alpha, n_beta):
+        d0 = np.zeros((M, n))
+        d0[np.arange(n), np.arange(n)] = 1.0
+        x = rng.standard_normal((n_w, M, n)) + 1j * rng.standard_normal((n_w, M, n))
+        q, _ = np.linalg.qr(d0[None] + s[:, None, None] * x / math.sqrt(2.0))
+        out.append(np.ascontiguousarray(q.astype(np.complex128)))
+    return Walkers(out[0], out[1])
