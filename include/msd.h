@@ -171,7 +171,7 @@ int msd_kernel_stat(msd_ctx* ctx, int index, const char** name, long long* launc
                     double* total_ms);
 
 /* Limit the device workspace (bytes) the context may hold; larger walker
-   batches are processed in chunks. 0 restores the default (4 GiB). */
+   batches are processed in chunks. 0 restores the default (16 GiB). */
 int msd_set_workspace_limit(msd_ctx* ctx, size_t bytes);
 
 /* With sync = 1 (the default) every call synchronises its stream before
@@ -180,6 +180,17 @@ int msd_set_workspace_limit(msd_ctx* ctx, size_t bytes);
    return as soon as the work is queued; device-side errors are then
    reported by the next synchronising call. */
 int msd_set_sync(msd_ctx* ctx, int sync);
+
+/* Mixed precision only: with fused = 1 (the default) the Cholesky
+   contraction of the local energy (Eq. 10-12, F = G L_g restricted to the
+   rows of the reference orbitals) and its per-(walker, vector) epilogue run
+   as one persistent tensor-core kernel whose FP32 products stay on chip;
+   with fused = 0 they run as a tensor-core GEMM writing F to device memory
+   followed by a separate epilogue kernel. Same arithmetic and rounding
+   points; results agree to FP32 summation order. Shapes the fused kernel
+   does not support (2N > 128 rows per walker, tiles beyond 227 KB of shared
+   memory) take the unfused path. */
+int msd_set_fused(msd_ctx* ctx, int fused);
 
 /* Number of CUDA kernels the library has launched in this process (all
    contexts), for launch accounting by benchmarks. */

@@ -75,12 +75,31 @@ int tc_gemm_3xtf32(const TcOperand& A, const TcOperand& B, int Mr, int Nc, int K
 // A, B row-major BF16 with K contiguous, K a multiple of 64).
 int tc_gemm_bf16(const void* A, long long lda, const void* B, long long ldb, int Mr, int Nc, int K, float* C,
                  long long ldc, unsigned* err, cudaStream_t st);
+// part_rows: rows per (block, part) in the output (0: R; larger pads each
+// part with zero rows).
 void launch_split_complex_rows(int nb, int R, int Kg, int Kp, const double2* src, long long src_ld,
-                               const int* cols, float* hi, float* lo, cudaStream_t st);
+                               const int* cols, float* hi, float* lo, cudaStream_t st, int part_rows = 0);
 void launch_split_real_rows(long long R, int Kg, int Kp, const double* src, long long src_ld, const int* cols,
                             float* hi, float* lo, cudaStream_t st);
 void launch_pack_complex(int nw, int n, const float* C, long long ldc, int splits, long long split_stride,
                          const double* add, double2* out, long long ldo, cudaStream_t st);
+
+// tc_fepi.cu: the Cholesky contraction of the energy fused with its
+// per-(walker, vector) epilogue (same outputs as tc_gemm_3xtf32 followed by
+// launch_fepi_f32). A: split rows of dG[occ0][virt], part c of walker w at
+// rows (2w + c) RB; B: split half-rotated Cholesky rows, vector g's at
+// g NCf + [occ0 (N), zero (RB - N), particles (np)]; both pitch ld,
+// contraction K. F0P: [n_chol][RB][NCf], F0[j][col] = L_g[occ0_j][col] in
+// the same column order, zero padded.
+struct TcFepiPlan {
+    int RB = 0, RW = 0, WPT = 0, NCf = 0, BN = 0, GPT = 0, BNe = 0, slot = 0, NCP = 0, f0s = 0;
+    size_t smem = 0;
+};
+bool tc_fepi_plan(const SpinTables& tb, TcFepiPlan& p);
+int tc_fepi_fused(const SpinTables& tb, const TcFepiPlan& p, int nw, int M, int n_chol, const float* a_hi,
+                  const float* a_lo, const float* b_hi, const float* b_lo, int ld, int K, const double2* Gr,
+                  const float* F0P, const double* c0, const double* x0, double2* v0, double2* xx,
+                  float2* Lact, float2* Xic, unsigned* err, cudaStream_t st);
 
 // k_mixed.cu
 size_t fepi_f32_smem(const SpinTables& tb);

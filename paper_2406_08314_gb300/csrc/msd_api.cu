@@ -91,12 +91,20 @@ struct msd_ctx {
     int Kp = 0;                 // M padded to a multiple of 32
     long long Kdp = 0;          // Kd padded to a multiple of 32
     float *LhF_hi[2] = {nullptr, nullptr}, *LhF_lo[2] = {nullptr, nullptr};
+    // fused path: the same rows with each vector's occ0 block padded to RB
+    // columns (zero rows), and F0 padded to [RB][RB + np]
+    float *LhP_hi[2] = {nullptr, nullptr}, *LhP_lo[2] = {nullptr, nullptr};
+    float* d_F0P[2] = {nullptr, nullptr};
     float *Lv_hi = nullptr, *Lv_lo = nullptr;
     int Kvp[2] = {0, 0};        // virtual orbitals (not in occ0) padded to 32
     int* d_virt[2] = {nullptr, nullptr};
     double *d_c0[2] = {nullptr, nullptr}, *d_x0[2] = {nullptr, nullptr}, *d_c0sum = nullptr;
     float* d_F0T[2] = {nullptr, nullptr};   // [n_chol][N][N + np] = L_g[occ0_j][col]
     int tc_bn = 0;                // tensor-core output tile width (0 = by shape)
+    int Kv[2] = {0, 0};           // virtual orbitals per spin
+    bool fuse = true;             // fused energy contraction + epilogue when the shape allows
+    bool fused_ok[2] = {false, false};
+    TcFepiPlan fplan[2];
     long long gen = 0;            // bumped whenever a device buffer may move
 };
 
@@ -408,6 +416,8 @@ void free_mixed(msd_ctx* ctx)
     for (int s = 0; s < 2; ++s) {
         cudaFree(ctx->LhF_hi[s]); cudaFree(ctx->LhF_lo[s]);
         ctx->LhF_hi[s] = ctx->LhF_lo[s] = nullptr;
+        cudaFree(ctx->LhP_hi[s]); cudaFree(ctx->LhP_lo[s]); cudaFree(ctx->d_F0P[s]);
+        ctx->LhP_hi[s] = ctx->LhP_lo[s] = ctx->d_F0P[s] = nullptr;
     }
     cudaFree(ctx->Lv_hi); cudaFree(ctx->Lv_lo);
     ctx->Lv_hi = ctx->Lv_lo = nullptr;
@@ -442,7 +452,9 @@ int prepare_mixed(msd_ctx* ctx, cudaStream_t st)
         std::vector<int> virt;
         for (int o = 0; o < M; ++o) if (!in0[o]) virt.push_back(o);
         const int Kv = (int)virt.size();
+        ctx->Kv[s] = Kv;
         ctx->Kvp[s] = std::max(32, (Kv + 31) / 32 * 32);
+        ctx->fused_ok[s] = tc_fepi_plan(tables(S, 1), ctx->fplan[s]);
         if (Kv == 0) virt.push_back(0);   // keeps the gather pointer valid; Kg = 0 pads with zeros
         int rc = upload(ctx, &ctx->d_virt[s], virt);
         if (rc) return rc;
@@ -474,6 +486,30 @@ int prepare_mixed(msd_ctx* ctx, cudaStream_t st)
         CK(cudaMalloc(&ctx->LhF_hi[s], sizeof(float) * R * ctx->Kvp[s]));
         CK(cudaMalloc(&ctx->LhF_lo[s], sizeof(float) * R * ctx->Kvp[s]));
         launch_split_real_rows(R, Kv, ctx->Kvp[s], S.d_Lh, M, ctx->d_virt[s], ctx->LhF_hi[s], ctx->LhF_lo[s], st);
+        if (ctx->fused_ok[s]) {
+            // vector g's columns: occ0 (N), zero (RB - N), particles (np)
+            const int RB = ctx->fplan[s].RB, NCf = RB + S.np;
+            std::vector<double> lp((size_t)G * NCf * M, 0.0);
+            std::vector<float> f0p((size_t)G * RB * NCf, 0.f);
+            for (int g = 0; g < G; ++g)
+                for (int cc = 0; cc < NCf; ++cc) {
+                    const int col = cc < S.N ? S.occ0[cc] : cc >= RB ? S.part_orb[cc - RB] : -1;
+                    if (col < 0) continue;
+                    const double* src = &ctx->h_L[((size_t)g * M + col) * M];
+                    std::copy(src, src + M, &lp[((size_t)g * NCf + cc) * M]);
+                    for (int j = 0; j < S.N; ++j)
+                        f0p[((size_t)g * RB + j) * NCf + cc] = (float)ctx->h_L[((size_t)g * M + S.occ0[j]) * M + col];
+                }
+            double* d_lp = nullptr;
+            if ((rc = upload(ctx, &d_lp, lp))) return rc;
+            if ((rc = upload(ctx, &ctx->d_F0P[s], f0p))) { cudaFree(d_lp); return rc; }
+            const long long RP = (long long)G * NCf;
+            CK(cudaMalloc(&ctx->LhP_hi[s], sizeof(float) * RP * ctx->Kvp[s]));
+            CK(cudaMalloc(&ctx->LhP_lo[s], sizeof(float) * RP * ctx->Kvp[s]));
+            launch_split_real_rows(RP, Kv, ctx->Kvp[s], d_lp, M, ctx->d_virt[s], ctx->LhP_hi[s], ctx->LhP_lo[s], st);
+            CK(cudaStreamSynchronize(st));
+            cudaFree(d_lp);
+        }
     }
     int rc = upload(ctx, &ctx->d_c0sum, c0sum);
     if (rc) return rc;
@@ -757,6 +793,12 @@ struct EnWork {
     void *v0[2], *xx[2], *La[2], *Xi[2], *Lh1[2], *e1[2], *Y[2], *Kaa, *Kbb, *Kab, *scal;
 };
 
+// The fused tensor-core contraction + epilogue serves spin s.
+bool fused(const msd_ctx* ctx, int s) { return ctx->fuse && ctx->fused_ok[s]; }
+
+// Rows of the split A operand per walker: 2N, or the fused kernel's padded RW.
+int a_rows(const msd_ctx* ctx, int s) { return fused(ctx, s) ? ctx->fplan[s].RW : 2 * ctx->sp[s].N; }
+
 int energy_slots(msd_ctx* ctx)
 {
     return string_energy_slots(tables(ctx->sp[0], 1)) + string_energy_slots(tables(ctx->sp[1], 1)) +
@@ -775,8 +817,9 @@ size_t en_bytes_per_walker(msd_ctx* ctx, bool fp32)
     if (fp32) {
         size_t f = 0, a = 0;
         for (int s = 0; s < 2; ++s) {
-            f = std::max(f, sizeof(float) * 2 * T1[s].N * (size_t)G * (T1[s].N + T1[s].np));
-            a = std::max(a, sizeof(float) * 2 * 2 * T1[s].N * (size_t)ctx->Kvp[s]);
+            if (!fused(ctx, s))
+                f = std::max(f, sizeof(float) * 2 * T1[s].N * (size_t)G * (T1[s].N + T1[s].np));
+            a = std::max(a, sizeof(float) * 2 * a_rows(ctx, s) * (size_t)ctx->Kvp[s]);
         }
         b += f + a;
     } else {
@@ -797,10 +840,10 @@ int en_alloc(msd_ctx* ctx, int cap, bool fp32, EnWork& E)
     if (fp32) {
         size_t f = 0, a = 0;
         for (int s = 0; s < 2; ++s) {
-            f = std::max(f, sizeof(float) * 2 * T1[s].N * (size_t)G * NC[s]);
-            a = std::max(a, sizeof(float) * 2 * T1[s].N * (size_t)ctx->Kvp[s]);
+            if (!fused(ctx, s)) f = std::max(f, sizeof(float) * 2 * T1[s].N * (size_t)G * NC[s]);
+            a = std::max(a, sizeof(float) * a_rows(ctx, s) * (size_t)ctx->Kvp[s]);
         }
-        if ((rc = arena_get(ctx, "F32", f * cap, &E.F32))) return rc;
+        if (f && (rc = arena_get(ctx, "F32", f * cap, &E.F32))) return rc;
         if ((rc = arena_get(ctx, "AF_hi", a * cap, &E.Ah))) return rc;
         if ((rc = arena_get(ctx, "AF_lo", a * cap, &E.Al))) return rc;
     }
@@ -833,7 +876,20 @@ int en_chunk(msd_ctx* ctx, Chunk& c, EnWork& E, int w0, int nw, int cap, bool fp
     const int NC[2] = {T[0].N + T[0].np, T[1].N + T[1].np};
     for (int s = 0; s < 2; ++s) {
         const int N = T[s].N;
-        if (fp32) {
+        if (fp32 && fused(ctx, s)) {
+            th.begin("k_split_F", st);
+            launch_split_complex_rows(nw, N, M - N, ctx->Kvp[s], c.Gr[s], M, ctx->d_virt[s], (float*)E.Ah,
+                                      (float*)E.Al, st, ctx->fplan[s].RB);
+            th.end(st);
+            th.begin("tc_fepi", st);
+            const int K = std::max(8, (ctx->Kv[s] + 7) / 8 * 8);
+            const int g = tc_fepi_fused(T[s], ctx->fplan[s], nw, M, G, (float*)E.Ah, (float*)E.Al, ctx->LhP_hi[s],
+                                        ctx->LhP_lo[s], ctx->Kvp[s], K, c.Gr[s], ctx->d_F0P[s], ctx->d_c0[s],
+                                        ctx->d_x0[s], (double2*)E.v0[s], (double2*)E.xx[s], (float2*)E.La[s],
+                                        (float2*)E.Xi[s], ctx->d_err, st);
+            th.end(st);
+            if (g) return fail(ctx, MSD_ERR_CUDA, "fused tensor-core contraction launch failed (energy)");
+        } else if (fp32) {
             th.begin("k_split_F", st);
             launch_split_complex_rows(nw, N, M - N, ctx->Kvp[s], c.Gr[s], M, ctx->d_virt[s], (float*)E.Ah,
                                       (float*)E.Al, st);
@@ -1339,6 +1395,17 @@ int msd_set_sync(msd_ctx* ctx, int sync)
 {
     if (!ctx) return MSD_ERR_ARG;
     ctx->sync = sync != 0;
+    return MSD_OK;
+}
+
+int msd_set_fused(msd_ctx* ctx, int fused)
+{
+    if (!ctx) return MSD_ERR_ARG;
+    if (ctx->fuse != (fused != 0)) {
+        ctx->fuse = fused != 0;
+        ctx->chunk = 0;   // workspace sizes per walker change
+        ++ctx->gen;
+    }
     return MSD_OK;
 }
 

@@ -18,113 +18,11 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "tc_ptx.cuh"
 
 namespace {
 
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(su32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ uint64_t global_ns()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Wait for the phase of the given parity to complete, for at most ~2 s.
-__device__ bool mbar_wait(uint64_t* bar, uint32_t parity)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    while (!mbar_try_wait(bar, parity))
-        if (global_ns() - t0 > 2000000000ull) return false;
-    return true;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
-        ::"r"(su32(dst)), "l"((uint64_t)map), "r"(su32(bar)), "r"(x), "r"(y)
-        : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle,
-// 8-row x 128-byte atoms stacked every 1024 bytes.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
-    d |= (uint64_t)1 << 16;                     // leading byte offset (unused for SW128 K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset
-    d |= (uint64_t)1 << 46;                     // descriptor version
-    d |= (uint64_t)2 << 61;                     // 128-byte swizzle
-    return d;
-}
-
-// Instruction descriptor of kind::tf32: FP32 accumulator, TF32 A and B,
-// both K-major, shape M x N.
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N)
-{
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
-        ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
-{
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
+using namespace tcx;
 // SPLIT: 3xTF32 (hi/lo operands, three products per K step) or a single
 // BF16 product. One k-block is 128 bytes of K per row in both cases
 // (32 FP32 or 64 BF16 elements); one MMA covers 32 bytes of K.
@@ -140,22 +38,6 @@ struct TcCfg {
     static constexpr uint32_t TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
     static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
 };
-
-// Instruction descriptor of kind::f16 with BF16 A and B, FP32 accumulator.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
-{
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
-        ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
 
 template <int BN, bool SPLIT>
 __global__ void __launch_bounds__(128, 1)
@@ -294,20 +176,31 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 
 // 2-D tensor [outer][inner] (FP32 or BF16) with row pitch `ld` elements;
 // boxes of 128 bytes x box_outer rows with 128-byte swizzle.
-int make_map(CUtensorMap* map, const void* base, int inner, int outer, long long ld, int box_outer, bool bf16)
+}  // namespace
+
+int tc_make_map(CUtensorMap* map, const void* base, int inner, int outer, long long ld, int box_outer, bool bf16,
+                int swizzle_bytes)
 {
     auto fn = encode_fn();
     if (!fn) return -1;
+    if (swizzle_bytes != 128 && swizzle_bytes != 64) return -1;
     const int esz = bf16 ? 2 : 4;
     cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
     cuuint64_t strides[1] = {(cuuint64_t)ld * esz};
-    cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_outer};
+    cuuint32_t box[2] = {(cuuint32_t)(swizzle_bytes / esz), (cuuint32_t)box_outer};
     cuuint32_t es[2] = {1, 1};
     CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base,
-                    dims, strides, box, es,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    swizzle_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? 0 : -1;
+}
+
+namespace {
+
+int make_map(CUtensorMap* map, const void* base, int inner, int outer, long long ld, int box_outer, bool bf16)
+{
+    return tc_make_map(map, base, inner, outer, ld, box_outer, bf16);
 }
 
 template <int BN, bool SPLIT>
@@ -354,20 +247,21 @@ __device__ __forceinline__ void split3(double x, float& hi, float& lo)
 // Rows of a complex FP64 matrix src[b][r][.] (b < nb, r < R) gathered at
 // columns cols[0..Kg) (all of [0, Kg) when cols is NULL) -> real rows
 // [(b, c, r)][Kp] (c = 0 real, 1 imaginary part), TF32 hi/lo, zero padded.
-__global__ void k_split_complex_rows(int nb, int R, int Kg, int Kp, const double2* __restrict__ src,
+// Part c of block b starts at row (2b + c) PR (PR >= R; rows r >= R zero).
+__global__ void k_split_complex_rows(int nb, int R, int PR, int Kg, int Kp, const double2* __restrict__ src,
                                      long long src_ld, const int* __restrict__ cols, float* __restrict__ hi,
                                      float* __restrict__ lo)
 {
-    const long long total = (long long)nb * 2 * R * Kp;
+    const long long total = (long long)nb * 2 * PR * Kp;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
         const int k = (int)(e % Kp);
         const long long row = e / Kp;
-        const int r = (int)(row % R);
-        const int c = (int)((row / R) % 2);
-        const long long b = row / (2 * R);
+        const int r = (int)(row % PR);
+        const int c = (int)((row / PR) % 2);
+        const long long b = row / (2 * PR);
         double x = 0;
-        if (k < Kg) {
+        if (k < Kg && r < R) {
             const double2 v = src[(b * R + r) * src_ld + (cols ? cols[k] : k)];
             x = c ? v.y : v.x;
         }
@@ -442,11 +336,12 @@ int tc_gemm_bf16(const void* A, long long lda, const void* B, long long ldb, int
 }
 
 void launch_split_complex_rows(int nb, int R, int Kg, int Kp, const double2* src, long long src_ld,
-                               const int* cols, float* hi, float* lo, cudaStream_t st)
+                               const int* cols, float* hi, float* lo, cudaStream_t st, int part_rows)
 {
+    const int PR = part_rows > R ? part_rows : R;
     if ((long long)nb * R * Kp <= 0) return;
-    k_split_complex_rows<<<grid_for((long long)nb * 2 * R * Kp), 256, 0, st>>>(nb, R, Kg, Kp, src, src_ld, cols,
-                                                                                hi, lo);
+    k_split_complex_rows<<<grid_for((long long)nb * 2 * PR * Kp), 256, 0, st>>>(nb, R, PR, Kg, Kp, src, src_ld,
+                                                                                 cols, hi, lo);
     msd_note_launch();
 }
 

@@ -247,8 +247,9 @@ def test_walker_chunking_matches(msd):
 MIX_E_REL, MIX_E_ABS, MIX_V = 2e-6, 1e-6, 1e-4
 
 
-def _check_mixed(m, sys_, pa, pb, ref):
+def _check_mixed(m, sys_, pa, pb, ref, fused=True):
     ctx = m.Context(sys_, "mixed")
+    ctx.set_fused(fused)
     da, db = _cuda(pa), _cuda(pb)
     e, o = ctx.local_energy(da, db, ovlp=True)
     e, o = _np(e), _np(o)
@@ -265,34 +266,43 @@ def _check_mixed(m, sys_, pa, pb, ref):
     ctx.close()
 
 
-def test_small_workload_mixed(msd):
+# fused: the energy's Cholesky contraction and its epilogue in one
+# persistent tensor-core kernel (default); unfused: GEMM + epilogue kernel.
+FUSED = pytest.mark.parametrize("fused", [True, False], ids=["fused", "unfused"])
+
+
+@FUSED
+def test_small_workload_mixed(msd, fused):
     s, w = synth.config_system("small", seed=0)
-    _check_mixed(msd, s, w.phi_a, w.phi_b, _ref(s, w.phi_a, w.phi_b))
+    _check_mixed(msd, s, w.phi_a, w.phi_b, _ref(s, w.phi_a, w.phi_b), fused)
 
 
+@FUSED
 @pytest.mark.parametrize("M,na,nb,n_det,max_level,seed", [(12, 5, 4, 150, 4, 0), (13, 7, 6, 300, 12, 1)])
-def test_tiny_systems_mixed(msd, M, na, nb, n_det, max_level, seed):
+def test_tiny_systems_mixed(msd, M, na, nb, n_det, max_level, seed, fused):
     s = tiny_system(seed, M, na, nb, n_chol=7, n_det=n_det, max_level=max_level)
     pa, pb = tiny_walkers(seed, M, na, nb, n_w=3, noise=0.3)
     # scale to the synthetic workloads' energy range (the bound is absolute in Ha)
     s.L = s.L * 0.05
     s.h1 = s.h1 * 0.05
     s, pa, pb = _relabel(s, pa, pb, seed)
-    _check_mixed(msd, s, pa, pb, _ref(s, pa, pb))
+    _check_mixed(msd, s, pa, pb, _ref(s, pa, pb), fused)
 
 
-def test_cu2o2_shaped_mixed(msd):
+@FUSED
+def test_cu2o2_shaped_mixed(msd, fused):
     s, w = synth.config_system("cu2o2", seed=0, n_w=2)
-    _check_mixed(msd, s, w.phi_a, w.phi_b, _ref(s, w.phi_a, w.phi_b))
+    _check_mixed(msd, s, w.phi_a, w.phi_b, _ref(s, w.phi_a, w.phi_b), fused)
 
 
-def test_fe2s2_shaped_subset_mixed(msd, fe2s2):
+@FUSED
+def test_fe2s2_shaped_subset_mixed(msd, fe2s2, fused):
     s, w = fe2s2
     idx = np.concatenate([[0], np.sort(np.random.default_rng(6).choice(
         np.arange(1, s.n_det), 299, replace=False))])
     t = _subtrial(s, idx)
     pa, pb = w.phi_a[:2], w.phi_b[:2]
-    _check_mixed(msd, t, pa, pb, _ref(t, pa, pb))
+    _check_mixed(msd, t, pa, pb, _ref(t, pa, pb), fused)
 
 
 def test_fe2s2_full_size_mixed_vs_fp64(msd, fe2s2):
@@ -313,3 +323,21 @@ def test_fe2s2_full_size_mixed_vs_fp64(msd, fe2s2):
     assert np.allclose(om, o64, rtol=1e-12, atol=0)
     dv = np.abs(vm - v64).max(axis=1) / np.abs(v64).max(axis=1)
     assert np.all(dv <= MIX_V), dv.max()
+
+
+def test_fe2s2_full_size_fused_matches_unfused(msd, fe2s2):
+    """Full size (640 walkers, 800 Cholesky vectors, 1.2e5 determinants):
+    the fused contraction + epilogue against the separate GEMM and epilogue
+    kernels. Same TF32 splits and FP32 rounding points; only the order of
+    the FP32 sums differs, so the local energies agree far inside the mixed
+    bound."""
+    s, w = fe2s2
+    da, db = _cuda(w.phi_a), _cuda(w.phi_b)
+    ctx = msd.Context(s, "mixed")
+    ctx.set_fused(False)
+    e0 = _np(ctx.local_energy(da, db))
+    ctx.set_fused(True)
+    e1 = _np(ctx.local_energy(da, db))
+    ctx.close()
+    assert np.all(np.isfinite(e1))
+    assert np.all(np.abs(e1 - e0) <= 0.1 * MIX_E_ABS), np.abs(e1 - e0).max()
