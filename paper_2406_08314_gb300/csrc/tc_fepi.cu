@@ -283,7 +283,7 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
         const int bq = lane / RB, j = lane % RB;
         const int bt = q * (32 / RB) + bq, wi = bt >> 1, c = bt & 1;
         const int pbar = 2 + set * 2 + wi;            // pair barrier id (RB = 32 only)
-        constexpr int SP = RB + 1;                    // odd pitch: conflict-free row writes
+        constexpr int SP = RB + 2;                    // pitch = 2 mod 4: conflict-free 64-bit row access
         float* slot = slots + (size_t)(set * WPT + wi) * a.slot;
         float* S0 = slot;                             // [RB][SP] dT real part
         float* S1 = slot + RB * SP;                   // [RB][SP] dT imaginary part
@@ -291,7 +291,9 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
         float* LamRe = FP + 2 * np * RB;              // [np][RB] Lambda, transposed
         float* LamIm = LamRe + np * RB;
         float* scal = slot + a.slot - 16;             // [2][8] trace partials of the two parts
-        const int ph = (np + 1) >> 1, p0 = c ? ph : 0, p1 = c ? np : ph;   // this part's particles
+        // this part's particles (the imaginary part, which has less trace
+        // work, takes the larger half)
+        const int ph = np >> 1, p0 = c ? ph : 0, p1 = c ? np : ph;
         // this set's sequence of vectors: (tile, gl) for gl = set, set + 2, ...
         // with g = (tile / n_rt) GPT + gl < n_chol, tiles in this CTA's order
         auto next_vec = [&](int& tile, int& gl) {
@@ -368,8 +370,7 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
                     float z0 = 0.f, z1 = 0.f;
 #pragma unroll
                     for (int l = 0; l < RB; l += 2) {
-                        Sc[j * SP + l] = t[l];
-                        Sc[j * SP + l + 1] = t[l + 1];
+                        *reinterpret_cast<float2*>(Sc + j * SP + l) = make_float2(t[l], t[l + 1]);
                         z0 = fmaf(t[l], f0[l * NCP + j], z0);
                         z1 = fmaf(t[l + 1], f0[(l + 1) * NCP + j], z1);
                     }
@@ -387,7 +388,8 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
                     float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
 #pragma unroll 4
                     for (int l = 0; l < RB; l += 2) {
-                        const float r0 = row[l], r1 = row[l + 1];
+                        const float2 rr = *reinterpret_cast<const float2*>(row + l);
+                        const float r0 = rr.x, r1 = rr.y;
                         b0 = fmaf(r0, S1[l * SP + j], b0);
                         b1 = fmaf(r1, S1[(l + 1) * SP + j], b1);
                         if (c == 0) {
@@ -418,19 +420,14 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
                 __syncwarp();
                 unsigned long long trp[RB / 2], tip[RB / 2];
                 {
-                    const float* So = (c ? S0 : S1) + j * SP;
-                    const float* fr = f0 + j * NCP;
+                    const unsigned long long* So =
+                        reinterpret_cast<const unsigned long long*>((c ? S0 : S1) + j * SP);
+                    const unsigned long long* fr = reinterpret_cast<const unsigned long long*>(f0 + j * NCP);
 #pragma unroll
                     for (int k = 0; k < RB / 2; ++k) {
-                        const float f_0 = fr[2 * k], f_1 = fr[2 * k + 1];
-                        const float o_0 = So[2 * k], o_1 = So[2 * k + 1];
-                        if (c == 0) {
-                            trp[k] = pack2(t[2 * k] + f_0, t[2 * k + 1] + f_1);
-                            tip[k] = pack2(o_0, o_1);
-                        } else {
-                            trp[k] = pack2(o_0 + f_0, o_1 + f_1);
-                            tip[k] = pack2(t[2 * k], t[2 * k + 1]);
-                        }
+                        const unsigned long long m = pack2(t[2 * k], t[2 * k + 1]), o = So[k], f = fr[k];
+                        trp[k] = add2(c ? o : m, f);   // T0 + dT_re
+                        tip[k] = c ? m : o;
                     }
                 }
                 // -- Lambda[j][p] = F_P[j][p] - sum_l T[j][l] G[occ0_l][P_p], this
@@ -506,10 +503,10 @@ bool tc_fepi_plan(const SpinTables& tb, TcFepiPlan& p)
     p.RW = 2 * p.RB;
     p.WPT = 64 / p.RB;
     p.NCf = p.RB + np;                               // B rows per vector: occ0 padded to RB, particles
-    // per-walker slot: the two [RB][RB + 1] dT parts, the F_P (later Xi)
+    // per-walker slot: the two [RB][RB + 2] dT parts, the F_P (later Xi)
     // parts [2][np][RB], Lambda^T as [np][RB] real and imaginary rows, 16 scalars
-    p.slot = 2 * p.RB * (p.RB + 1) + 4 * np * p.RB + 16;
-    p.NCP = p.NCf | 1;                               // odd pitch: conflict-free row and column reads
+    p.slot = 2 * p.RB * (p.RB + 2) + 4 * np * p.RB + 16;
+    p.NCP = (p.NCf + 1) / 4 * 4 + 2;                 // = 2 mod 4: conflict-free 64-bit row reads
     p.f0s = (p.RB * p.NCP + 3) / 4 * 4;
     // columns read per vector: RB from its start (occ0 part) and 16 from
     // its particle part, inside the buffer's 256 TMEM columns
