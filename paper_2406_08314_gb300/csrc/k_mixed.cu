@@ -2,6 +2,8 @@
 // vector) epilogue of F = G L_g computed on the tensor cores, the sums over
 // Cholesky vectors and the Gram matrices of Lambda_g = G L_g (I - G). Same
 // algebra as the FP64 kernels in k_energy.cu.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -196,46 +198,89 @@ void launch_gamma_reduce_f32(int nw, int X, int n_chol, int spin, const double2*
     msd_note_launch();
 }
 
-// K[w][x][y] = sum_g P[w][g][x] Q[w][g][y], FP32, 32 x 32 tile per block.
+// K[x][y] = sum_g P_g[x] Q_g[y] (complex, no conjugation) per walker: one
+// block per walker computes the whole Xp x Xq Gram matrix. 16 x 16 threads,
+// thread (ty, tx) owns rows ty + 16 i and columns tx + 16 j (i, j < R, R =
+// ceil(max(Xp, Xq) / 16)), so each P value read from shared memory (a
+// broadcast to the 16 threads of a row) and each Q value (consecutive,
+// conflict-free) serves R complex FMAs. Cholesky vectors stream through
+// shared memory GRAM_G at a time; the sum over g runs in a fixed order.
+#define GRAM_G 32
+template <int R>
 __global__ void __launch_bounds__(256)
-k_gram_f32(int Xp, int Xq, int n_chol, const float2* __restrict__ P, const float2* __restrict__ Q,
-           float2* __restrict__ Kout)
+k_gram_f32(GramJobs jobs, int n_chol)
 {
-    __shared__ float2 ps[32][32 + 1], qs[32][32 + 1];
-    const int w = blockIdx.z;
-    const int x0 = blockIdx.y * 32, y0 = blockIdx.x * 32;
-    const int t = threadIdx.x, ty = t / 16, tx = t % 16;
-    float2 acc[2][2] = {{make_float2(0, 0), make_float2(0, 0)}, {make_float2(0, 0), make_float2(0, 0)}};
+    const GramJob& jb = jobs.j[blockIdx.y];
+    const int Xp = jb.Xp, Xq = jb.Xq;
+    const float2* __restrict__ P = jb.P;
+    const float2* __restrict__ Q = jb.Q;
+    float2* __restrict__ Kout = jb.K;
+    if (Xp <= 0 || Xq <= 0) return;
+    extern __shared__ float2 gsm[];
+    float2* ps = gsm;                       // [GRAM_G][16 R]
+    float2* qs = gsm + GRAM_G * 16 * R;     // [GRAM_G][16 R]
+    constexpr int W = 16 * R;
+    const int w = blockIdx.x;
+    const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
+    float2 acc[R][R];
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int j = 0; j < R; ++j) acc[i][j] = make_float2(0.f, 0.f);
     const float2* Pw = P + (size_t)w * n_chol * Xp;
     const float2* Qw = Q + (size_t)w * n_chol * Xq;
-    for (int g0 = 0; g0 < n_chol; g0 += 32) {
-        for (int e = t; e < 32 * 32; e += 256) {
-            const int gg = e / 32, xx = e % 32, g = g0 + gg;
-            ps[gg][xx] = (g < n_chol && x0 + xx < Xp) ? Pw[(size_t)g * Xp + x0 + xx] : make_float2(0, 0);
-            qs[gg][xx] = (g < n_chol && y0 + xx < Xq) ? Qw[(size_t)g * Xq + y0 + xx] : make_float2(0, 0);
+    for (int g0 = 0; g0 < n_chol; g0 += GRAM_G) {
+        __syncthreads();   // previous chunk consumed
+        for (int e = t; e < GRAM_G * W; e += 256) {
+            const int gg = e / W, xx = e - gg * W, g = g0 + gg;
+            ps[e] = (g < n_chol && xx < Xp) ? Pw[(size_t)g * Xp + xx] : make_float2(0.f, 0.f);
+            qs[e] = (g < n_chol && xx < Xq) ? Qw[(size_t)g * Xq + xx] : make_float2(0.f, 0.f);
         }
         __syncthreads();
-#pragma unroll 8
-        for (int gg = 0; gg < 32; ++gg) {
-            const float2 p0 = ps[gg][ty * 2], p1 = ps[gg][ty * 2 + 1];
-            const float2 q0 = qs[gg][tx * 2], q1 = qs[gg][tx * 2 + 1];
-            acc[0][0] = fcfma(p0, q0, acc[0][0]); acc[0][1] = fcfma(p0, q1, acc[0][1]);
-            acc[1][0] = fcfma(p1, q0, acc[1][0]); acc[1][1] = fcfma(p1, q1, acc[1][1]);
+#pragma unroll 2
+        for (int gg = 0; gg < GRAM_G; ++gg) {
+            float2 pv[R], qv[R];
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                pv[i] = ps[gg * W + ty + 16 * i];
+                qv[i] = qs[gg * W + tx + 16 * i];
+            }
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+#pragma unroll
+                for (int j = 0; j < R; ++j) acc[i][j] = fcfma(pv[i], qv[j], acc[i][j]);
         }
-        __syncthreads();
     }
-    for (int i = 0; i < 2; ++i)
-        for (int j = 0; j < 2; ++j) {
-            const int x = x0 + ty * 2 + i, y = y0 + tx * 2 + j;
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const int x = ty + 16 * i, y = tx + 16 * j;
             if (x < Xp && y < Xq) Kout[((size_t)w * Xp + x) * Xq + y] = acc[i][j];
         }
 }
 
-void launch_gram_f32(int nw, int Xp, int Xq, int n_chol, const float2* P, const float2* Q, float2* K,
-                     cudaStream_t st)
+template <int R>
+static void launch_gram_r(int nw, int n_chol, const GramJobs& jobs, int nj, cudaStream_t st)
 {
-    if (Xp <= 0 || Xq <= 0 || nw <= 0) return;
-    dim3 grid((Xq + 31) / 32, (Xp + 31) / 32, nw);
-    k_gram_f32<<<grid, 256, 0, st>>>(Xp, Xq, n_chol, P, Q, K);
+    const size_t smem = sizeof(float2) * 2 * GRAM_G * 16 * R;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_gram_f32<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_gram_f32<R><<<dim3(nw, nj), 256, smem, st>>>(jobs, n_chol);
     msd_note_launch();
+}
+
+void launch_gram_f32(int nw, int n_chol, const GramJobs& jobs, int nj, cudaStream_t st)
+{
+    int xm = 0;
+    for (int i = 0; i < nj; ++i) xm = std::max(xm, std::max(jobs.j[i].Xp, jobs.j[i].Xq));
+    if (xm <= 0 || nw <= 0 || nj <= 0) return;
+    switch ((xm + 15) / 16) {   // MSD_XMAX = 112: R <= 7
+        case 1: launch_gram_r<1>(nw, n_chol, jobs, nj, st); break;
+        case 2: launch_gram_r<2>(nw, n_chol, jobs, nj, st); break;
+        case 3: launch_gram_r<3>(nw, n_chol, jobs, nj, st); break;
+        case 4: launch_gram_r<4>(nw, n_chol, jobs, nj, st); break;
+        case 5: launch_gram_r<5>(nw, n_chol, jobs, nj, st); break;
+        case 6: launch_gram_r<6>(nw, n_chol, jobs, nj, st); break;
+        default: launch_gram_r<7>(nw, n_chol, jobs, nj, st); break;
+    }
 }

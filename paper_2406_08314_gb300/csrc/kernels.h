@@ -109,8 +109,18 @@ void launch_fepi_f32(const SpinTables& tb, int nw, int M, int n_chol, const floa
 void launch_gamma_reduce_f32(int nw, int X, int n_chol, int spin, const double2* v0a, const double2* v0b,
                              const double2* xx, const float2* Lact, const float2* Xic, const double2* Lh,
                              float2* Y, double2* scal, cudaStream_t st);
-void launch_gram_f32(int nw, int Xp, int Xq, int n_chol, const float2* P, const float2* Q, float2* K,
-                     cudaStream_t st);
+// K[w][x][y] = sum_g P[w][g][x] Q[w][g][y] (FP32) for up to three
+// (P, Q, K) products of shapes Xp x Xq in one launch.
+struct GramJob {
+    int Xp, Xq;
+    const float2* P;
+    const float2* Q;
+    float2* K;
+};
+struct GramJobs {
+    GramJob j[3];
+};
+void launch_gram_f32(int nw, int n_chol, const GramJobs& jobs, int nj, cudaStream_t st);
 
 // k_batch.cu: per-determinant energy terms of many systems in one
 // persistent launch.

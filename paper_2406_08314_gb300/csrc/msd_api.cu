@@ -936,9 +936,10 @@ int en_chunk(msd_ctx* ctx, Chunk& c, EnWork& E, int w0, int nw, int cap, bool fp
     th.end(st);
     th.begin("k_gram", st);
     if (fp32) {
-        launch_gram_f32(nw, X[0], X[0], G, (float2*)E.La[0], (float2*)E.La[0], (float2*)E.Kaa, st);
-        launch_gram_f32(nw, X[1], X[1], G, (float2*)E.La[1], (float2*)E.La[1], (float2*)E.Kbb, st);
-        launch_gram_f32(nw, X[0], X[1], G, (float2*)E.La[0], (float2*)E.La[1], (float2*)E.Kab, st);
+        GramJobs jobs = {{{X[0], X[0], (float2*)E.La[0], (float2*)E.La[0], (float2*)E.Kaa},
+                          {X[1], X[1], (float2*)E.La[1], (float2*)E.La[1], (float2*)E.Kbb},
+                          {X[0], X[1], (float2*)E.La[0], (float2*)E.La[1], (float2*)E.Kab}}};
+        launch_gram_f32(nw, G, jobs, 3, st);
     } else {
         launch_gram(nw, X[0], X[0], G, (double2*)E.La[0], (double2*)E.La[0], E.Kaa, false, st);
         launch_gram(nw, X[1], X[1], G, (double2*)E.La[1], (double2*)E.La[1], E.Kbb, false, st);
