@@ -89,8 +89,8 @@ void launch_pack_complex(int nw, int n, const float* C, long long ldc, int split
 // launch_fepi_f32). A: split rows of dG[occ0][virt], part c of walker w at
 // rows (2w + c) RB; B: split half-rotated Cholesky rows, vector g's at
 // g NCf + [occ0 (N), zero (RB - N), particles (np)]; both pitch ld,
-// contraction K. F0P: [n_chol][RB][NCf], F0[j][col] = L_g[occ0_j][col] in
-// the same column order, zero padded.
+// contraction K. F0P: [n_chol][f0s], F0[j][col] = L_g[occ0_j][col] at
+// g f0s + j NCP + col in the same column order, zero padded.
 struct TcFepiPlan {
     int RB = 0, RW = 0, WPT = 0, NCf = 0, BN = 0, GPT = 0, BNe = 0, slot = 0, NCP = 0, f0s = 0;
     size_t smem = 0;

@@ -488,9 +488,9 @@ int prepare_mixed(msd_ctx* ctx, cudaStream_t st)
         launch_split_real_rows(R, Kv, ctx->Kvp[s], S.d_Lh, M, ctx->d_virt[s], ctx->LhF_hi[s], ctx->LhF_lo[s], st);
         if (ctx->fused_ok[s]) {
             // vector g's columns: occ0 (N), zero (RB - N), particles (np)
-            const int RB = ctx->fplan[s].RB, NCf = RB + S.np;
+            const int RB = ctx->fplan[s].RB, NCf = RB + S.np, NCP = ctx->fplan[s].NCP, f0s = ctx->fplan[s].f0s;
             std::vector<double> lp((size_t)G * NCf * M, 0.0);
-            std::vector<float> f0p((size_t)G * RB * NCf, 0.f);
+            std::vector<float> f0p((size_t)G * f0s, 0.f);   // [g][j NCP + col], the kernel's shared layout
             for (int g = 0; g < G; ++g)
                 for (int cc = 0; cc < NCf; ++cc) {
                     const int col = cc < S.N ? S.occ0[cc] : cc >= RB ? S.part_orb[cc - RB] : -1;
@@ -498,7 +498,7 @@ int prepare_mixed(msd_ctx* ctx, cudaStream_t st)
                     const double* src = &ctx->h_L[((size_t)g * M + col) * M];
                     std::copy(src, src + M, &lp[((size_t)g * NCf + cc) * M]);
                     for (int j = 0; j < S.N; ++j)
-                        f0p[((size_t)g * RB + j) * NCf + cc] = (float)ctx->h_L[((size_t)g * M + S.occ0[j]) * M + col];
+                        f0p[(size_t)g * f0s + (size_t)j * NCP + cc] = (float)ctx->h_L[((size_t)g * M + S.occ0[j]) * M + col];
                 }
             double* d_lp = nullptr;
             if ((rc = upload(ctx, &d_lp, lp))) return rc;

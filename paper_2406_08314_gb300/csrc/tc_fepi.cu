@@ -19,14 +19,14 @@
 // rows then the np particles, so that T is RB x RB with zero padding and
 // every epilogue loop runs over the compile-time RB without tests.
 //
-// Structure (persistent, one CTA per SM, 10 warps):
+// Structure (persistent, one CTA per SM, 14 warps):
 //   warp 0      TMA producer: A and B k-blocks of 16 FP32 (64-byte swizzle),
-//               TF32 hi and lo parts, into a three-stage shared-memory ring;
+//               TF32 hi and lo parts, into a two-stage shared-memory ring;
 //   warp 1      TMEM owner; lane 0 issues tcgen05.mma into one of two TMEM
 //               accumulators (the next tile's products overlap this tile's
 //               epilogue);
-//   warps 2-9   epilogue, two sets of four warps (one per lane quarter)
-//               taking alternate Cholesky vectors of a tile. The real and
+//   warps 2-13  epilogue, three sets of four warps (one per lane quarter)
+//               taking every third Cholesky vector of a tile. The real and
 //               imaginary row blocks of a walker (lanes of one warp, or two
 //               warps when RB = 32) swap their rows through a per-walker
 //               shared-memory slot, so that each lane holds the complex row
@@ -55,16 +55,17 @@ using namespace tcx;
 
 namespace {
 
-constexpr int FE_THREADS = 320;   // producer warp, MMA warp, 8 epilogue warps
-constexpr int FE_EPI = 256;
-constexpr int FE_STAGES = 3;
+constexpr int FE_SETS = 3;                      // epilogue sets of four warps (one per TMEM lane quarter)
+constexpr int FE_EPI = 128 * FE_SETS;
+constexpr int FE_THREADS = 64 + FE_EPI;         // producer warp, MMA warp, epilogue warps
+constexpr int FE_STAGES = 2;
 constexpr int FE_TCOLS = 256;                 // TMEM columns per accumulator buffer
 constexpr uint32_t FE_A_BYTES = 128 * 64;     // 128 rows x 16 FP32
 constexpr int FE_XMAX = 128;                  // output entries (holes x particles) mapped in shared memory
 
-__device__ __forceinline__ void cp_async4(void* dst, const void* src)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
 {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(su32(dst)), "l"(src) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
@@ -76,7 +77,7 @@ struct FeArgs {
     int NCf, NCP, f0s;         // B rows per vector, shared-memory pitch of an F0 row, floats per F0 block
     int n_rt, n_tiles;
     const double2* Gr;
-    const float* F0P;          // [n_chol][RB][NCf]: F0[j][col] at [g][j][col], zero padded
+    const float* F0P;          // [n_chol][f0s]: F0[j][col] at [g][j NCP + col], zero padded
     const double* c0;
     const double* x0;
     double2* v0;
@@ -164,7 +165,9 @@ __device__ __forceinline__ float2 cdot_row(const unsigned long long* tr, const u
 }
 
 template <int RB>
-__global__ void __launch_bounds__(FE_THREADS, 1)
+// Bounds of 512 threads cap registers at 128: with 14 warps, four share a
+// sub-partition's 16K-register file.
+__global__ void __launch_bounds__(512, 1)
 k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
           const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
           const __grid_constant__ FeArgs a)
@@ -175,11 +178,11 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int N = a.tb.N, np = a.tb.np, NCf = a.NCf, X = a.tb.nh * np, NCP = a.NCP;
     const uint32_t B_BYTES = (uint32_t)a.BN * 64, STAGE_BYTES = 2 * (FE_A_BYTES + B_BYTES);
-    float* slots = reinterpret_cast<float*>(smem + FE_STAGES * STAGE_BYTES);      // [2][WPT][slot]
-    float* gpRe = slots + 2 * WPT * a.slot;                                       // [2][WPT][np][RB]
+    float* slots = reinterpret_cast<float*>(smem + FE_STAGES * STAGE_BYTES);      // [FE_SETS][WPT][slot]
+    float* gpRe = slots + FE_SETS * WPT * a.slot;                                 // [2][WPT][np][RB]
     float* gpIm = gpRe + 2 * WPT * np * RB;                                       // [2][WPT][np][RB]
-    float* f0buf = gpIm + 2 * WPT * np * RB;                                      // [2 sets][2][f0s]
-    int* oe = reinterpret_cast<int*>(f0buf + 4 * a.f0s);                         // [X] p RB + pos(h)
+    float* f0buf = gpIm + 2 * WPT * np * RB;                                      // [FE_SETS][2][f0s]
+    int* oe = reinterpret_cast<int*>(f0buf + FE_SETS * 2 * a.f0s);               // [X] p RB + pos(h)
 
     __shared__ __align__(8) uint64_t full_bar[FE_STAGES], empty_bar[FE_STAGES];
     __shared__ __align__(8) uint64_t tfull[2], tempty[2], drain_bar;
@@ -282,7 +285,7 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
         const int q = warp & 3, set = ew >> 2;
         const int bq = lane / RB, j = lane % RB;
         const int bt = q * (32 / RB) + bq, wi = bt >> 1, c = bt & 1;
-        const int pbar = 2 + set * 2 + wi;            // pair barrier id (RB = 32 only)
+        const int pbar = 2 + set * 2 + wi;            // pair barrier id (RB = 32 only): 2 .. 7
         constexpr int SP = RB + 2;                    // pitch = 2 mod 4: conflict-free 64-bit row access
         float* slot = slots + (size_t)(set * WPT + wi) * a.slot;
         float* S0 = slot;                             // [RB][SP] dT real part
@@ -294,34 +297,36 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
         // this part's particles (the imaginary part, which has less trace
         // work, takes the larger half)
         const int ph = np >> 1, p0 = c ? ph : 0, p1 = c ? np : ph;
-        // this set's sequence of vectors: (tile, gl) for gl = set, set + 2, ...
+        // this set's sequence of vectors: (tile, gl) for gl = set, set + FE_SETS, ...
         // with g = (tile / n_rt) GPT + gl < n_chol, tiles in this CTA's order
         auto next_vec = [&](int& tile, int& gl) {
-            gl += 2;
+            gl += FE_SETS;
             if (gl >= a.GPT || (tile / a.n_rt) * a.GPT + gl >= a.n_chol) {
                 tile += gridDim.x;
                 gl = set;
-                if (tile < a.n_tiles && (tile / a.n_rt) * a.GPT + gl >= a.n_chol) tile = a.n_tiles;
+                if (tile < a.n_tiles && (gl >= a.GPT || (tile / a.n_rt) * a.GPT + gl >= a.n_chol)) tile = a.n_tiles;
             }
         };
-        // F0[j][col] (padded) of vector g into buffer k of this set, row pitch NCP
+        // F0 block of vector g (the same layout in global and shared memory)
+        // into buffer k of this set, in 16-byte pieces
+        const int st_t = (ew & 3) * 32 + lane;        // thread index within the set
         auto prefetch = [&](int tile, int gl, int k) {
             if (tile >= a.n_tiles) return;
-            const float* src = a.F0P + (size_t)((tile / a.n_rt) * a.GPT + gl) * RB * NCf;
+            const float* src = a.F0P + (size_t)((tile / a.n_rt) * a.GPT + gl) * a.f0s;
             float* dst = f0buf + (set * 2 + k) * a.f0s;
-            for (int r = (ew & 3); r < RB; r += 4)         // rows over the set's four warps
-                for (int cc = lane; cc < NCf; cc += 32) cp_async4(dst + r * NCP + cc, src + r * NCf + cc);
+            for (int e = st_t * 4; e < a.f0s; e += 128 * 4) cp_async16(dst + e, src + e);
             cp_async_commit();
         };
         int pf_tile = blockIdx.x, pf_gl = set;       // the next vector to prefetch
-        if (pf_tile < a.n_tiles && (pf_tile / a.n_rt) * a.GPT + pf_gl >= a.n_chol) pf_tile = a.n_tiles;
+        if (pf_tile < a.n_tiles && (pf_gl >= a.GPT || (pf_tile / a.n_rt) * a.GPT + pf_gl >= a.n_chol))
+            pf_tile = a.n_tiles;
         prefetch(pf_tile, pf_gl, 0);
         next_vec(pf_tile, pf_gl);
         int it = 0, vc = 0;
         for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
             const int b = it & 1, rt = tile % a.n_rt, ct = tile / a.n_rt;
             // G[occ0_l][P_p] of the tile's walkers, transposed and zero padded
-            // to RB rows; double buffered by tile parity (the two sets may be
+            // to RB rows; double buffered by tile parity (the sets may be
             // one tile apart)
             float* gbr = gpRe + b * WPT * np * RB;
             float* gbi = gpIm + b * WPT * np * RB;
@@ -348,12 +353,12 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
             const bool wv = w < a.nw;
             const float* gwr = gbr + wi * np * RB;
             const float* gwi = gbi + wi * np * RB;
-            for (int gl = set; gl < a.GPT; gl += 2, ++vc) {
+            for (int gl = set; gl < a.GPT; gl += FE_SETS, ++vc) {
                 const int g = ct * a.GPT + gl;
                 if (g >= a.n_chol) break;
                 // this vector's F0 block has landed (own copies, then the set's)
                 cp_async_wait_all();
-                bar_sync(6 + set, 128);
+                bar_sync(8 + set, 128);
                 const float* f0 = f0buf + (set * 2 + (vc & 1)) * a.f0s;   // T0[j][l] = f0[j NCP + l]
                 prefetch(pf_tile, pf_gl, (vc + 1) & 1);
                 next_vec(pf_tile, pf_gl);
@@ -513,11 +518,11 @@ bool tc_fepi_plan(const SpinTables& tb, TcFepiPlan& p)
     const int span = p.RB + 16;
     for (int BN = FE_TCOLS; BN >= 16 && BN >= span; BN -= 16) {
         int gpt = (BN - span) / p.NCf + 1;
-        if (gpt > 1 && (gpt & 1)) --gpt;             // even: the two epilogue sets stay balanced
+        if (gpt >= FE_SETS) gpt -= gpt % FE_SETS;    // a multiple of the sets: balanced epilogue
         const int bn = std::max(16, std::min(BN, ((gpt - 1) * p.NCf + span + 15) / 16 * 16));
         const size_t smem = 1024 + (size_t)FE_STAGES * 2 * (FE_A_BYTES + (size_t)bn * 64) +
-                            4 * (size_t)2 * p.WPT * p.slot + 4 * (size_t)4 * p.WPT * np * p.RB +
-                            4 * (size_t)4 * p.f0s + 4 * FE_XMAX;
+                            4 * (size_t)FE_SETS * p.WPT * p.slot + 4 * (size_t)4 * p.WPT * np * p.RB +
+                            4 * (size_t)FE_SETS * 2 * p.f0s + 4 * FE_XMAX;
         if (smem + 128 > 227 * 1024) continue;   // 128: static shared memory of the kernel
         p.BN = bn;
         p.GPT = gpt;
