@@ -196,6 +196,28 @@ int msd_set_fused(msd_ctx* ctx, int fused);
    contexts), for launch accounting by benchmarks. */
 long long msd_launch_count(void);
 
+/* ---- Propagation (Sec. II A, Eq. 7-12) ---------------------------------
+   One phaseless AFQMC step of n_w walkers, in place, in FP64 (the overlaps
+   and the force bias in the context's precision):
+     vbias_g = <Psi_T|L_g|phi>/<Psi_T|phi>, xbar_g = -i sqrt(dt) vbias_g,
+     phi'    = E T_n(V) E phi, E = exp(-dt h'/2), h' = h - 1/2 sum_g L_g L_g,
+               V = i sqrt(dt) sum_g (x_g - xbar_g) L_g, T_n the Taylor series
+               of exp to order taylor_order (1..16),
+     S       = O_T(phi')/O_T(phi), I = S exp(x.xbar - xbar.xbar/2),
+     w'      = w |I| max(0, cos arg S),
+   then, if orthonormalize != 0, phi'^s <- Q with phi'^s = Q R (the diagonal
+   of R real positive; weights are unaffected since S is computed first).
+   phi_a, phi_b: device [n_w][M][N_s] complex (in/out); weights: device
+   [n_w] double (in/out); x: device [n_w][n_chol] double, the Gaussian
+   fields drawn by the caller; ratio: optional device [n_w] complex, S.
+   Host pointers are rejected (MSD_ERR_ARG); dt <= 0 or an order outside
+   1..16 is MSD_ERR_ARG; walker blocks beyond 200 KB (M N_s complex) are
+   MSD_ERR_SHAPE. exp(-dt h'/2) is formed on the host once per dt (scaling
+   and squaring of its Taylor series) and cached with the context. */
+int msd_propagate(msd_ctx* ctx, int n_w, double* phi_a, double* phi_b, double* weights,
+                  const double* x, double dt, int taylor_order, int orthonormalize,
+                  double* ratio, void* stream);
+
 /* ---- Batched independent systems ---------------------------------------
    Many systems (each its own context: uneven orbital, electron and
    determinant counts; one device and one precision for all) evaluated

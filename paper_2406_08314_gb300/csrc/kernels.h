@@ -151,3 +151,13 @@ void launch_features(int nw, int M, int N, int n_core, int n_act, const int* pos
                      int spin, cudaStream_t st);
 void launch_features_rows(int nw, int M, int N, const double2* Gr, float* feat, long long ld, long long off,
                           cudaStream_t st);
+
+// k_prop.cu: one phaseless propagation step (FP64).
+void launch_sum_LL(int M, int G, const double* Lt, double* corr, cudaStream_t st);
+void launch_prop_coef(int nw, int G, double dt, const double* x, const double2* vbias, double2* c, double2* expo,
+                      cudaStream_t st);
+int launch_apply_rows(int nw, int M, int N, const double2* A, long long a_stride, const double* Ar,
+                      const double2* in, double2* out, double2* acc, double scale, cudaStream_t st);
+void launch_prop_weight(int nw, const double2* o_old, const double2* o_new, const double2* expo, double* w,
+                        double2* ratio, cudaStream_t st);
+int launch_qr_mgs(int nw, int M, int N, double2* phi, unsigned* err, cudaStream_t st);

@@ -3,6 +3,7 @@
 // kernels for overlap, per-determinant ratios, force bias and local energy.
 #include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -106,11 +107,18 @@ struct msd_ctx {
     bool fused_ok[2] = {false, false};
     TcFepiPlan fplan[2];
     long long gen = 0;            // bumped whenever a device buffer may move
+    // propagation (msd_propagate): transposed Cholesky vectors, sum_g L_g L_g
+    // and exp(-dt h'/2) per spin for the last dt
+    double* d_Lt = nullptr;       // [M * M][n_chol]
+    std::vector<double> h_corr;   // [M][M]
+    double* d_E[2] = {nullptr, nullptr};
+    double prop_dt = -1.0;
 };
 
 namespace {
 
 void free_mixed(msd_ctx* ctx);
+void free_prop(msd_ctx* ctx);
 
 int fail(msd_ctx* c, int code, const char* fmt, ...)
 {
@@ -1034,6 +1042,163 @@ int evaluate(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b, do
     return evaluate_impl(ctx, n_w, phi_a, phi_b, ovlp, vbias, e_loc, stream, nullptr);
 }
 
+// ------------------------------------------------------------ propagation
+void free_prop(msd_ctx* ctx)
+{
+    cudaFree(ctx->d_Lt);
+    ctx->d_Lt = nullptr;
+    for (int s = 0; s < 2; ++s) { cudaFree(ctx->d_E[s]); ctx->d_E[s] = nullptr; }
+    ctx->h_corr.clear();
+    ctx->prop_dt = -1.0;
+}
+
+// exp(A) of a real M x M matrix: scaling to norm <= 1/4, Taylor series to
+// order 18 (remainder below 1e-17 relative), then squaring.
+std::vector<double> expm_host(const std::vector<double>& A, int M)
+{
+    double nrm = 0;
+    for (int i = 0; i < M; ++i) {
+        double r = 0;
+        for (int j = 0; j < M; ++j) r += std::fabs(A[(size_t)i * M + j]);
+        nrm = std::max(nrm, r);
+    }
+    int sq = 0;
+    while (nrm > 0.25) { nrm *= 0.5; ++sq; }
+    const double scale = std::ldexp(1.0, -sq);
+    std::vector<double> B(A.size()), X((size_t)M * M, 0.0), T((size_t)M * M, 0.0), tmp((size_t)M * M);
+    for (size_t e = 0; e < A.size(); ++e) B[e] = A[e] * scale;
+    for (int i = 0; i < M; ++i) X[(size_t)i * M + i] = T[(size_t)i * M + i] = 1.0;
+    auto mul = [M](const std::vector<double>& a, const std::vector<double>& b, std::vector<double>& c) {
+        std::fill(c.begin(), c.end(), 0.0);
+        for (int i = 0; i < M; ++i)
+            for (int k = 0; k < M; ++k) {
+                const double aik = a[(size_t)i * M + k];
+                for (int j = 0; j < M; ++j) c[(size_t)i * M + j] += aik * b[(size_t)k * M + j];
+            }
+    };
+    for (int k = 1; k <= 18; ++k) {
+        mul(T, B, tmp);
+        for (size_t e = 0; e < tmp.size(); ++e) T[e] = tmp[e] / k;
+        for (size_t e = 0; e < X.size(); ++e) X[e] += T[e];
+    }
+    for (int i = 0; i < sq; ++i) {
+        mul(X, X, tmp);
+        X.swap(tmp);
+    }
+    return X;
+}
+
+// Transposed Cholesky vectors and sum_g L_g L_g once per Hamiltonian;
+// E_s = exp(-dt h'_s / 2), h'_s = h_s - 1/2 sum_g L_g L_g, once per dt.
+int prepare_prop(msd_ctx* ctx, double dt, cudaStream_t st)
+{
+    const int M = ctx->M, G = ctx->n_chol;
+    if (!ctx->d_Lt) {
+        std::vector<double> lt((size_t)M * M * G);
+        for (int g = 0; g < G; ++g)
+            for (size_t pq = 0; pq < (size_t)M * M; ++pq) lt[pq * G + g] = ctx->h_L[(size_t)g * M * M + pq];
+        int rc = upload(ctx, &ctx->d_Lt, lt);
+        if (rc) return rc;
+        double* d_corr = nullptr;
+        CK(cudaMalloc(&d_corr, sizeof(double) * M * M));
+        launch_sum_LL(M, G, ctx->d_Lt, d_corr, st);
+        ctx->h_corr.resize((size_t)M * M);
+        cudaError_t e = cudaMemcpyAsync(ctx->h_corr.data(), d_corr, sizeof(double) * M * M, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaFree(d_corr);
+        if (e != cudaSuccess) return fail(ctx, MSD_ERR_CUDA, "sum of L_g L_g failed: %s", cudaGetErrorString(e));
+        ctx->prop_dt = -1.0;
+    }
+    if (ctx->prop_dt != dt) {
+        for (int s = 0; s < 2; ++s) {
+            std::vector<double> a((size_t)M * M);
+            for (size_t e = 0; e < a.size(); ++e)
+                a[e] = -0.5 * dt * (ctx->h_h1[(size_t)s * M * M + e] - 0.5 * ctx->h_corr[e]);
+            int rc = upload(ctx, &ctx->d_E[s], expm_host(a, M));
+            if (rc) return rc;
+        }
+        ctx->prop_dt = dt;
+    }
+    return MSD_OK;
+}
+
+int propagate(msd_ctx* ctx, int n_w, double* phi_a, double* phi_b, double* weights, const double* x, double dt,
+              int order, int orthonormalize, double* ratio, void* stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = begin_call(ctx, n_w, phi_a, phi_b, st);
+    if (rc) return rc;
+    if (n_w == 0) return MSD_OK;
+    if (!(dt > 0) || order < 1 || order > 16)
+        return fail(ctx, MSD_ERR_ARG, "need dt > 0 and 1 <= taylor_order <= 16 (got %g, %d)", dt, order);
+    if (!weights || !x) return fail(ctx, MSD_ERR_ARG, "weights and x are required");
+    if (!is_device_ptr(phi_a) || !is_device_ptr(phi_b) || !is_device_ptr(weights) || !is_device_ptr(x) ||
+        (ratio && !is_device_ptr(ratio)))
+        return fail(ctx, MSD_ERR_ARG, "msd_propagate takes device pointers only");
+    const int M = ctx->M, G = ctx->n_chol, Nm = std::max(ctx->n[0], ctx->n[1]);
+    if (sizeof(double2) * (size_t)M * Nm > 200 * 1024)
+        return fail(ctx, MSD_ERR_SHAPE, "M x N = %d x %d walker blocks exceed the kernels' shared memory", M, Nm);
+    if ((rc = prepare_prop(ctx, dt, st))) return rc;
+    void *o0, *o1, *ex, *vb, *cf;
+    if ((rc = arena_get(ctx, "pr_o0", sizeof(double2) * n_w, &o0))) return rc;
+    if ((rc = arena_get(ctx, "pr_o1", sizeof(double2) * n_w, &o1))) return rc;
+    if ((rc = arena_get(ctx, "pr_expo", sizeof(double2) * n_w, &ex))) return rc;
+    if ((rc = arena_get(ctx, "pr_vb", sizeof(double2) * (size_t)n_w * G, &vb))) return rc;
+    if ((rc = arena_get(ctx, "pr_c", sizeof(double2) * (size_t)n_w * G, &cf))) return rc;
+    // Eq. 7: overlap and mixed <L_g> of the current walkers
+    if ((rc = evaluate_impl(ctx, n_w, phi_a, phi_b, (double*)o0, (double*)vb, nullptr, stream, nullptr))) return rc;
+    const TimerHook& th = ctx->hook;
+    th.begin("k_prop_coef", st);
+    launch_prop_coef(n_w, G, dt, x, (const double2*)vb, (double2*)cf, (double2*)ex, st);
+    th.end(st);
+    // B(x - xbar) on walker chunks: V, half steps, Taylor series
+    const size_t per = sizeof(double2) * ((size_t)M * M + 3 * (size_t)M * Nm);
+    const int cap = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_w, ctx->ws_limit / 2 / per));
+    void *V, *t0, *t1, *ac;
+    if ((rc = arena_get(ctx, "pr_V", sizeof(double2) * (size_t)cap * M * M, &V))) return rc;
+    if ((rc = arena_get(ctx, "pr_t0", sizeof(double2) * (size_t)cap * M * Nm, &t0))) return rc;
+    if ((rc = arena_get(ctx, "pr_t1", sizeof(double2) * (size_t)cap * M * Nm, &t1))) return rc;
+    if ((rc = arena_get(ctx, "pr_acc", sizeof(double2) * (size_t)cap * M * Nm, &ac))) return rc;
+    for (int w0 = 0; w0 < n_w; w0 += cap) {
+        const int nw = std::min(cap, n_w - w0);
+        th.begin("k_gemm_V", st);
+        launch_gemm_zd(nw, M * M, G, (const double2*)cf + (size_t)w0 * G, G, ctx->d_Lt, G, (double2*)V,
+                       (long long)M * M, st);
+        th.end(st);
+        for (int s = 0; s < 2; ++s) {
+            const int N = ctx->n[s];
+            double2* phi = (double2*)(s ? phi_b : phi_a) + (size_t)w0 * M * N;
+            double2 *cur = (double2*)t0, *nxt = (double2*)t1, *acc = (double2*)ac;
+            th.begin("k_apply_rows", st);
+            int g = launch_apply_rows(nw, M, N, nullptr, 0, ctx->d_E[s], phi, cur, nullptr, 1.0, st);
+            CK(cudaMemcpyAsync(acc, cur, sizeof(double2) * (size_t)nw * M * N, cudaMemcpyDeviceToDevice, st));
+            for (int k = 1; k <= order && !g; ++k) {
+                g = launch_apply_rows(nw, M, N, (const double2*)V, (long long)M * M, nullptr, cur, nxt, acc,
+                                      1.0 / k, st);
+                std::swap(cur, nxt);
+            }
+            if (!g) g = launch_apply_rows(nw, M, N, nullptr, 0, ctx->d_E[s], acc, phi, nullptr, 1.0, st);
+            th.end(st);
+            if (g) return fail(ctx, MSD_ERR_SHAPE, "walker block too large for the propagation kernels");
+            CKLAUNCH();
+        }
+    }
+    // Eq. 8: overlap of the propagated walkers; Eq. 10-11: weights
+    if ((rc = msd_overlap(ctx, n_w, phi_a, phi_b, (double*)o1, nullptr, stream))) return rc;
+    th.begin("k_prop_weight", st);
+    launch_prop_weight(n_w, (const double2*)o0, (const double2*)o1, (const double2*)ex, weights, (double2*)ratio,
+                       st);
+    th.end(st);
+    if (orthonormalize) {
+        th.begin("k_qr_mgs", st);
+        for (int s = 0; s < 2; ++s)
+            if (launch_qr_mgs(n_w, M, ctx->n[s], (double2*)(s ? phi_b : phi_a), ctx->d_err, st))
+                return fail(ctx, MSD_ERR_SHAPE, "walker block too large for the QR kernel");
+        th.end(st);
+    }
+    return finish(ctx, st, {}, false);
+}
+
 }  // namespace
 
 // ========================================================================
@@ -1080,6 +1245,7 @@ void msd_destroy(msd_ctx* ctx)
     cudaFree(ctx->pairs.d_a); cudaFree(ctx->pairs.d_b); cudaFree(ctx->pairs.d_c);
     cudaFree(ctx->pairs.d_det_index);
     free_mixed(ctx);
+    free_prop(ctx);
     cudaFree(ctx->d_h1); cudaFree(ctx->d_Lcat); cudaFree(ctx->d_err);
     cudaFreeHost(ctx->h_err);
     for (auto& p : ctx->pending) { ctx->ev_pool.push_back(p.a); ctx->ev_pool.push_back(p.b); }
@@ -1101,6 +1267,7 @@ int msd_set_hamiltonian(msd_ctx* ctx, const double* h1, double e0, int n_chol, c
     ctx->e0 = e0;
     int rc = upload(ctx, &ctx->d_h1, ctx->h_h1);
     if (rc) return rc;
+    free_prop(ctx);
     ctx->have_ham = true;
     return build_half_rotated(ctx);
 }
@@ -1261,6 +1428,12 @@ int msd_evaluate(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b
 {
     if (ctx && n_w > 0 && !ovlp && !vbias && !e_loc) return fail(ctx, MSD_ERR_ARG, "no output requested");
     return evaluate(ctx, n_w, phi_a, phi_b, ovlp, vbias, e_loc, stream);
+}
+
+int msd_propagate(msd_ctx* ctx, int n_w, double* phi_a, double* phi_b, double* weights, const double* x,
+                  double dt, int taylor_order, int orthonormalize, double* ratio, void* stream)
+{
+    return propagate(ctx, n_w, phi_a, phi_b, weights, x, dt, taylor_order, orthonormalize, ratio, stream);
 }
 
 int msd_features(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b, int n_core, int n_act,

@@ -22,7 +22,7 @@ _ERRORS = {-1: "MSD_ERR_ARG", -2: "MSD_ERR_SHAPE", -3: "MSD_ERR_CUDA", -4: "MSD_
 EXPORTS = ["msd_create", "msd_destroy", "msd_last_error", "msd_set_hamiltonian", "msd_set_trial",
            "msd_set_precision", "msd_overlap", "msd_det_ratios", "msd_force_bias",
            "msd_local_energy", "msd_evaluate", "msd_info", "msd_set_timing", "msd_reset_stats",
-           "msd_kernel_count", "msd_kernel_stat", "msd_set_workspace_limit", "msd_set_sync", "msd_set_fused",
+           "msd_kernel_count", "msd_kernel_stat", "msd_set_workspace_limit", "msd_set_sync", "msd_set_fused", "msd_propagate",
            "msd_launch_count", "msd_overlap_noalloc", "msd_batch_create", "msd_batch_destroy",
            "msd_batch_last_error", "msd_batch_evaluate", "msd_batch_autotune", "msd_batch_config",
            "msd_batch_set_config", "msd_batch_graph_ready", "msd_batch_graph_kernels", "msd_features", "msd_features_rows",
@@ -67,6 +67,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.msd_set_workspace_limit.argtypes = [vp, ctypes.c_size_t]
     lib.msd_set_sync.argtypes = [vp, ci]
     lib.msd_set_fused.argtypes = [vp, ci]
+    lib.msd_propagate.argtypes = [vp, ci, vp, vp, vp, vp, ctypes.c_double, ci, ci, vp, vp]
     lib.msd_launch_count.argtypes = []
     for f in EXPORTS:
         if f not in ("msd_destroy", "msd_last_error"):
@@ -303,6 +304,25 @@ class Context:
 
     def set_sync(self, sync: bool):
         self._check(_lib.msd_set_sync(self._h, int(bool(sync))))
+
+    def propagate(self, phi_a, phi_b, weights, x, dt: float, order: int = 6, orthonormalize: bool = False):
+        """One phaseless AFQMC step (Sec. II A) of device walkers, in place:
+        phi_a, phi_b (n_w, M, N) complex128, weights (n_w,) float64, x
+        (n_w, n_chol) float64 Gaussian fields. Returns the overlap ratios S
+        (n_w,) complex128."""
+        import torch
+        n_w = phi_a.shape[0]
+        for t, dt_ in ((phi_a, torch.complex128), (phi_b, torch.complex128), (weights, torch.float64),
+                       (x, torch.float64)):
+            if not t.is_cuda or t.dtype != dt_ or not t.is_contiguous():
+                raise ValueError("propagate takes contiguous CUDA tensors (complex128 walkers, float64 "
+                                 "weights and fields)")
+        ratio = torch.empty(n_w, dtype=torch.complex128, device=phi_a.device)
+        raw = lambda t: ctypes.c_void_p(t.data_ptr())
+        self._check(_lib.msd_propagate(self._h, n_w, raw(phi_a), raw(phi_b), raw(weights), raw(x),
+                                       float(dt), int(order), int(bool(orthonormalize)), raw(ratio),
+                                       self._stream(phi_a, None)))
+        return ratio
 
     def set_fused(self, fused: bool):
         """Mixed precision: fused tensor-core contraction + epilogue (default)
