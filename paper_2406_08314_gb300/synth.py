@@ -262,6 +262,10 @@ CONFIGS = {
                   max_level=6, power=1.5, n_chol=400, n_w=640, walk_steps=20),
     "fe2s2": dict(M=160, n_alpha=30, n_beta=30, n_core=15, n_act_orb=20, n_det=120000,
                   max_level=6, power=1.2, n_chol=800, n_w=640, walk_steps=0),
+    # the copper-oxo shape at the paper's largest expansion (N_det = 1e6,
+    # Sec. III), run with 640 walkers and in the 10-walker regime
+    "cu2o2_1e6": dict(M=108, n_alpha=16, n_beta=16, n_core=8, n_act_orb=16, n_det=1000000,
+                      max_level=6, power=1.5, n_chol=400, n_w=640, walk_steps=20),
 }
 
 
