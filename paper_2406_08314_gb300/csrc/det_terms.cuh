@@ -45,34 +45,68 @@ __device__ __forceinline__ double2 string_energy_term(const SpinTables& tb, int 
         for (int j = 0; j < KL; ++j) b[i][j] = B[i * KL + j];
     T lr = 0, li = 0;      // linear part
     T qr = 0, qi = 0;      // Qc - Qx
-#pragma unroll 1
-    for (int i = 0; i < KL; ++i) {
-        const int pi = sp[i];
-#pragma unroll 1
-        for (int j = 0; j < KL; ++j) {
-            const int hj = sh[j] * np;
-            const int xij = hj + pi;
-            const T2 bij = B[i * KL + j];
-            const T2 y = ys[xij];
-            lr += bij.x * y.x - bij.y * y.y;
-            li += bij.x * y.y + bij.y * y.x;
-            const T2* kc_row = ks + (size_t)xij * X;
-            T zr = 0, zi = 0;
+    if constexpr (KL <= 4) {
+        // fully unrolled: every index and B value is in registers, the loop
+        // body reads shared memory only
 #pragma unroll
-            for (int k = 0; k < KL; ++k) {
-                const T2* kx_row = ks + (size_t)(hj + px[k]) * X + pi;
+        for (int i = 0; i < KL; ++i) {
 #pragma unroll
-                for (int l = 0; l < KL; ++l) {
-                    // K[(h_j,p_i)][(h_l,p_k)] - K[(h_j,p_k)][(h_l,p_i)]
-                    const T2 kc = kc_row[hx[l] + px[k]];
-                    const T2 kx = kx_row[hx[l]];
-                    const T dr = kc.x - kx.x, di = kc.y - kx.y;
-                    zr += b[k][l].x * dr - b[k][l].y * di;
-                    zi += b[k][l].x * di + b[k][l].y * dr;
+            for (int j = 0; j < KL; ++j) {
+                const int xij = hx[j] + px[i];
+                const T2 bij = b[i][j];
+                const T2 y = ys[xij];
+                lr += bij.x * y.x - bij.y * y.y;
+                li += bij.x * y.y + bij.y * y.x;
+                const T2* kc_row = ks + (size_t)xij * X;
+                T zr = 0, zi = 0;
+#pragma unroll
+                for (int k = 0; k < KL; ++k) {
+                    const T2* kx_row = ks + (size_t)(hx[j] + px[k]) * X + px[i];
+#pragma unroll
+                    for (int l = 0; l < KL; ++l) {
+                        // K[(h_j,p_i)][(h_l,p_k)] - K[(h_j,p_k)][(h_l,p_i)]
+                        const T2 kc = kc_row[hx[l] + px[k]];
+                        const T2 kx = kx_row[hx[l]];
+                        const T dr = kc.x - kx.x, di = kc.y - kx.y;
+                        zr += b[k][l].x * dr - b[k][l].y * di;
+                        zi += b[k][l].x * di + b[k][l].y * dr;
+                    }
                 }
+                qr += bij.x * zr - bij.y * zi;
+                qi += bij.x * zi + bij.y * zr;
             }
-            qr += bij.x * zr - bij.y * zi;
-            qi += bij.x * zi + bij.y * zr;
+        }
+    } else {
+        // levels 5 and 6 (rare strings): (i, j) at run time, so their
+        // indices and B values come from memory
+#pragma unroll 1
+        for (int i = 0; i < KL; ++i) {
+            const int pi = sp[i];
+#pragma unroll 1
+            for (int j = 0; j < KL; ++j) {
+                const int hj = sh[j] * np;
+                const int xij = hj + pi;
+                const T2 bij = B[i * KL + j];
+                const T2 y = ys[xij];
+                lr += bij.x * y.x - bij.y * y.y;
+                li += bij.x * y.y + bij.y * y.x;
+                const T2* kc_row = ks + (size_t)xij * X;
+                T zr = 0, zi = 0;
+#pragma unroll
+                for (int k = 0; k < KL; ++k) {
+                    const T2* kx_row = ks + (size_t)(hj + px[k]) * X + pi;
+#pragma unroll
+                    for (int l = 0; l < KL; ++l) {
+                        const T2 kc = kc_row[hx[l] + px[k]];
+                        const T2 kx = kx_row[hx[l]];
+                        const T dr = kc.x - kx.x, di = kc.y - kx.y;
+                        zr += b[k][l].x * dr - b[k][l].y * di;
+                        zi += b[k][l].x * di + b[k][l].y * dr;
+                    }
+                }
+                qr += bij.x * zr - bij.y * zi;
+                qi += bij.x * zi + bij.y * zr;
+            }
         }
     }
     const double2 e_s = cz((double)lr + 0.5 * (double)qr, (double)li + 0.5 * (double)qi);
@@ -126,5 +160,70 @@ __device__ __forceinline__ double2 pair_cross_term(const SpinTables& ta, const S
             xim += ba.x * zi + ba.y * zr;
         }
     const double2 rr = cscale(cmul(ra[(size_t)w * ta.n_str + a], rb[(size_t)w * tbb.n_str + b]), pt.c[I]);
+    return cmul(rr, cz((double)xr, (double)xim));
+}
+
+// The opposite-spin term with both levels known at compile time: indices and
+// both inverse minors in registers, the ka^2 kb^2 gathers from shared memory
+// fully unrolled (same value as pair_cross_term).
+template <int KA, int KB, typename T>
+__device__ __forceinline__ double2 pair_cross_term2(const SpinTables& ta, const SpinTables& tbb, const PairTables& pt,
+                                                    int I, int w, const void* __restrict__ Ba_in,
+                                                    const void* __restrict__ Bb_in, const cplx_t<T>* ks,
+                                                    const double2* __restrict__ ra, const double2* __restrict__ rb)
+{
+    using T2 = cplx_t<T>;
+    const int Xb = tbb.nh * tbb.np;
+    const int a = pt.a[I], b = pt.b[I];
+    const int nsa = ta.bucket[KA + 1] - ta.bucket[KA], sa = a - ta.bucket[KA];
+    const int nsb = tbb.bucket[KB + 1] - tbb.bucket[KB], sb = b - tbb.bucket[KB];
+    int ha[KA], pa[KA], xb[KB][KB];
+#pragma unroll
+    for (int i = 0; i < KA; ++i) {
+        ha[i] = ta.str_h[(size_t)a * MSD_KMAX + i] * ta.np;
+        pa[i] = ta.str_p[(size_t)a * MSD_KMAX + i];
+    }
+    {
+        int hb[KB], pb[KB];
+#pragma unroll
+        for (int k = 0; k < KB; ++k) {
+            hb[k] = tbb.str_h[(size_t)b * MSD_KMAX + k] * tbb.np;
+            pb[k] = tbb.str_p[(size_t)b * MSD_KMAX + k];
+        }
+#pragma unroll
+        for (int k = 0; k < KB; ++k)
+#pragma unroll
+            for (int l = 0; l < KB; ++l) xb[k][l] = hb[l] + pb[k];
+    }
+    const T2* Ba = reinterpret_cast<const T2*>(Ba_in) + (size_t)ta.b_off[KA] + ((size_t)w * nsa + sa) * (KA * KA);
+    const T2* Bb = reinterpret_cast<const T2*>(Bb_in) + (size_t)tbb.b_off[KB] + ((size_t)w * nsb + sb) * (KB * KB);
+    T2 ba[KA][KA], bb[KB][KB];
+#pragma unroll
+    for (int i = 0; i < KA; ++i)
+#pragma unroll
+        for (int j = 0; j < KA; ++j) ba[i][j] = Ba[i * KA + j];
+#pragma unroll
+    for (int k = 0; k < KB; ++k)
+#pragma unroll
+        for (int l = 0; l < KB; ++l) bb[k][l] = Bb[k * KB + l];
+    const double2 rr = cscale(cmul(ra[(size_t)w * ta.n_str + a], rb[(size_t)w * tbb.n_str + b]), pt.c[I]);
+    T xr = 0, xim = 0;
+#pragma unroll
+    for (int i = 0; i < KA; ++i)
+#pragma unroll
+        for (int j = 0; j < KA; ++j) {
+            const T2* krow = ks + (size_t)(ha[j] + pa[i]) * Xb;
+            T zr = 0, zi = 0;
+#pragma unroll
+            for (int k = 0; k < KB; ++k)
+#pragma unroll
+                for (int l = 0; l < KB; ++l) {
+                    const T2 kv = krow[xb[k][l]];
+                    zr += bb[k][l].x * kv.x - bb[k][l].y * kv.y;
+                    zi += bb[k][l].x * kv.y + bb[k][l].y * kv.x;
+                }
+            xr += ba[i][j].x * zr - ba[i][j].y * zi;
+            xim += ba[i][j].x * zi + ba[i][j].y * zr;
+        }
     return cmul(rr, cz((double)xr, (double)xim));
 }

@@ -446,6 +446,10 @@ static void launch_pc_k(const SpinTables& ta, const SpinTables& tb, const PairTa
     const int nb = (n + PC_THREADS * PC_PER_THREAD - 1) / (PC_THREADS * PC_PER_THREAD);
     dim3 grid(nb, nw);
     const size_t smem = (fp32 ? sizeof(float2) : sizeof(double2)) * (size_t)(ta.nh * ta.np) * (tb.nh * tb.np);
+    if (launch_pair_cross2(ka, KB, fp32, grid, smem, ta, tb, pt, lo, n, ra, rb, Ba, Bb, K, part, nslot, slot, st)) {
+        slot += nb;
+        return;
+    }
     if (fp32) {
         cudaFuncSetAttribute(k_pair_cross<KB, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_pair_cross<KB, float><<<grid, PC_THREADS, smem, st>>>(ta, tb, pt, ka, lo, n, ra, rb, Ba, Bb, K, part, nslot, slot); msd_note_launch();

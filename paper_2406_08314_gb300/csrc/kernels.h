@@ -161,3 +161,9 @@ int launch_apply_rows(int nw, int M, int N, const double2* A, long long a_stride
 void launch_prop_weight(int nw, const double2* o_old, const double2* o_new, const double2* expo, double* w,
                         double2* ratio, cudaStream_t st);
 int launch_qr_mgs(int nw, int M, int N, double2* phi, unsigned* err, cudaStream_t st);
+
+// k_pair.cu: the opposite-spin term with both levels compiled in (ka + kb <=
+// 8); false for other level pairs.
+bool launch_pair_cross2(int ka, int kb, bool fp32, dim3 grid, size_t smem, const SpinTables& ta, const SpinTables& tb,
+                        const PairTables& pt, int lo, int n, const double2* ra, const double2* rb, const void* Ba,
+                        const void* Bb, const void* K, double2* part, int nslot, int slot, cudaStream_t st);
