@@ -78,8 +78,11 @@ struct SpinTables {
     const int* csr_off;    // [n_str+1] determinants containing each string
     const int* csr_other;  // [nnz] string of the opposite spin in that determinant
     const double* csr_c;   // [nnz] CI coefficient of that determinant
+    const uint8_t* cmx;    // [sum_k k^2 n_k] x = p_i nh + h_j of entry (i, j) of each string's
+                           // minor, bucket-major, a string's k^2 entries row-major (B's order)
     long long b_off[MSD_KMAX + 2];  // per-walker offset (complex units) of each bucket's B block
     long long b_per_walker;         // sum_k k^2 * (strings of level k)
+    long long cmx_off[MSD_KMAX + 2];  // offset of each bucket's entries in cmx
 };
 
 // Pair (determinant) tables for the opposite-spin cross term.
@@ -102,7 +105,7 @@ struct Work {
     double2* r[2];      // [nw][n_str]    ratio per string
     double2* B[2];      // [nw * b_per_walker] inverse minors (bucket-major, SoA within bucket)
     float2* Bf[2];      // FP32 copy for the mixed path (same layout)
-    double2* wts[2];    // [nw][n_str]    sum over dets containing the string of c * r_other
+    double2* wts[2];    // [nw][n_str]    r_s times the sum over dets containing the string of c * r_other
     double2* part;      // [nw][nslot]    per-block partial sums
     int nslot;
     unsigned* err;      // device error word

@@ -26,8 +26,7 @@ using cplx_t = typename std::conditional<std::is_same<T, float>::value, float2, 
 template <int KL, typename T>
 __device__ __forceinline__ double2 string_energy_term(const SpinTables& tb, int w, int sl, int ns,
                                                       const void* __restrict__ Bin, const cplx_t<T>* ks,
-                                                      const cplx_t<T>* ys, const double2* __restrict__ r,
-                                                      const double2* __restrict__ wts)
+                                                      const cplx_t<T>* ys, const double2* __restrict__ wts)
 {
     using T2 = cplx_t<T>;
     const int X = tb.nh * tb.np, np = tb.np;
@@ -110,8 +109,7 @@ __device__ __forceinline__ double2 string_energy_term(const SpinTables& tb, int 
         }
     }
     const double2 e_s = cz((double)lr + 0.5 * (double)qr, (double)li + 0.5 * (double)qi);
-    const double2 rw = cmul(r[(size_t)w * tb.n_str + s], wts[(size_t)w * tb.n_str + s]);
-    return cmul(rw, e_s);
+    return cmul(wts[(size_t)w * tb.n_str + s], e_s);   // wts holds r_s w_s
 }
 
 template <int KB, typename T>

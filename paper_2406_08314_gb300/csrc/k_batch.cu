@@ -23,12 +23,12 @@ __device__ double2 batch_se(const BatchSys& S, const BatchItem& it, int t, const
         if (sl >= ns) break;
         double2 v;
         switch (k) {
-        case 1: v = string_energy_term<1, T>(tb, it.w, sl, ns, S.B[it.spin], ks, ys, S.r[it.spin], S.wts[it.spin]); break;
-        case 2: v = string_energy_term<2, T>(tb, it.w, sl, ns, S.B[it.spin], ks, ys, S.r[it.spin], S.wts[it.spin]); break;
-        case 3: v = string_energy_term<3, T>(tb, it.w, sl, ns, S.B[it.spin], ks, ys, S.r[it.spin], S.wts[it.spin]); break;
-        case 4: v = string_energy_term<4, T>(tb, it.w, sl, ns, S.B[it.spin], ks, ys, S.r[it.spin], S.wts[it.spin]); break;
-        case 5: v = string_energy_term<5, T>(tb, it.w, sl, ns, S.B[it.spin], ks, ys, S.r[it.spin], S.wts[it.spin]); break;
-        default: v = string_energy_term<6, T>(tb, it.w, sl, ns, S.B[it.spin], ks, ys, S.r[it.spin], S.wts[it.spin]); break;
+        case 1: v = string_energy_term<1, T>(tb, it.w, sl, ns, S.B[it.spin], ks, ys, S.wts[it.spin]); break;
+        case 2: v = string_energy_term<2, T>(tb, it.w, sl, ns, S.B[it.spin], ks, ys, S.wts[it.spin]); break;
+        case 3: v = string_energy_term<3, T>(tb, it.w, sl, ns, S.B[it.spin], ks, ys, S.wts[it.spin]); break;
+        case 4: v = string_energy_term<4, T>(tb, it.w, sl, ns, S.B[it.spin], ks, ys, S.wts[it.spin]); break;
+        case 5: v = string_energy_term<5, T>(tb, it.w, sl, ns, S.B[it.spin], ks, ys, S.wts[it.spin]); break;
+        default: v = string_energy_term<6, T>(tb, it.w, sl, ns, S.B[it.spin], ks, ys, S.wts[it.spin]); break;
         }
         acc = cadd(acc, v);
     }

@@ -312,7 +312,7 @@ void launch_gram(int nw, int Xp, int Xq, int n_chol, const double2* P, const dou
 // the string's inverse minor held in registers.
 template <int KL, typename T>
 __global__ void __launch_bounds__(SE_THREADS)
-k_string_energy(SpinTables tb, const double2* __restrict__ r, const double2* __restrict__ wts,
+k_string_energy(SpinTables tb, const double2* __restrict__ wts,
                 const void* __restrict__ Bin, const void* __restrict__ Kin, const void* __restrict__ Yin,
                 double2* __restrict__ part, int nslot, int slot0)
 {
@@ -333,7 +333,7 @@ k_string_energy(SpinTables tb, const double2* __restrict__ r, const double2* __r
     for (int it = 0; it < SE_PER_THREAD; ++it) {
         const int sl = blockIdx.x * (SE_THREADS * SE_PER_THREAD) + it * SE_THREADS + t;
         if (sl >= ns) break;
-        contrib = cadd(contrib, string_energy_term<KL, T>(tb, w, sl, ns, Bin, ks, ys, r, wts));
+        contrib = cadd(contrib, string_energy_term<KL, T>(tb, w, sl, ns, Bin, ks, ys, wts));
     }
     red[t] = contrib;
     __syncthreads();
@@ -357,7 +357,7 @@ size_t string_energy_smem(const SpinTables& tb, bool fp32)
 }
 
 template <int KL>
-static void launch_se_k(const SpinTables& tb, int nw, const double2* r, const double2* wts,
+static void launch_se_k(const SpinTables& tb, int nw, const double2* wts,
                         const void* B, const void* K, const void* Y, bool fp32, double2* part,
                         int nslot, int& slot, cudaStream_t st)
 {
@@ -367,25 +367,25 @@ static void launch_se_k(const SpinTables& tb, int nw, const double2* r, const do
     const size_t smem = string_energy_smem(tb, fp32);
     if (fp32) {
         cudaFuncSetAttribute(k_string_energy<KL, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_string_energy<KL, float><<<grid, SE_THREADS, smem, st>>>(tb, r, wts, B, K, Y, part, nslot, slot); msd_note_launch();
+        k_string_energy<KL, float><<<grid, SE_THREADS, smem, st>>>(tb, wts, B, K, Y, part, nslot, slot); msd_note_launch();
     } else {
         cudaFuncSetAttribute(k_string_energy<KL, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_string_energy<KL, double><<<grid, SE_THREADS, smem, st>>>(tb, r, wts, B, K, Y, part, nslot, slot); msd_note_launch();
+        k_string_energy<KL, double><<<grid, SE_THREADS, smem, st>>>(tb, wts, B, K, Y, part, nslot, slot); msd_note_launch();
     }
     slot += nb;
 }
 
-void launch_string_energy(const SpinTables& tb, int nw, const double2* r, const double2* wts,
+void launch_string_energy(const SpinTables& tb, int nw, const double2* wts,
                           const void* B, const void* K, const void* Y, bool fp32, double2* part,
                           int nslot, int slot0, cudaStream_t st)
 {
     int slot = slot0;
-    launch_se_k<1>(tb, nw, r, wts, B, K, Y, fp32, part, nslot, slot, st);
-    launch_se_k<2>(tb, nw, r, wts, B, K, Y, fp32, part, nslot, slot, st);
-    launch_se_k<3>(tb, nw, r, wts, B, K, Y, fp32, part, nslot, slot, st);
-    launch_se_k<4>(tb, nw, r, wts, B, K, Y, fp32, part, nslot, slot, st);
-    launch_se_k<5>(tb, nw, r, wts, B, K, Y, fp32, part, nslot, slot, st);
-    launch_se_k<6>(tb, nw, r, wts, B, K, Y, fp32, part, nslot, slot, st);
+    launch_se_k<1>(tb, nw, wts, B, K, Y, fp32, part, nslot, slot, st);
+    launch_se_k<2>(tb, nw, wts, B, K, Y, fp32, part, nslot, slot, st);
+    launch_se_k<3>(tb, nw, wts, B, K, Y, fp32, part, nslot, slot, st);
+    launch_se_k<4>(tb, nw, wts, B, K, Y, fp32, part, nslot, slot, st);
+    launch_se_k<5>(tb, nw, wts, B, K, Y, fp32, part, nslot, slot, st);
+    launch_se_k<6>(tb, nw, wts, B, K, Y, fp32, part, nslot, slot, st);
 }
 
 int string_energy_slots(const SpinTables& tb)

@@ -274,8 +274,9 @@ void launch_strings(const SpinTables& tb, int nw, const double2* Gact, double2* 
 
 // ------------------------------------------------------------------------
 // CI weights per string: w_s = sum over determinants I containing string s
-// of c_I * r_other(I), so that sum_I c_I r_a r_b = sum_a r_a w_a. For spin
-// alpha the block also reduces r_s * w_s into per-walker partial sums.
+// of c_I * r_other(I), so that sum_I c_I r_a r_b = sum_a r_a w_a. Stored is
+// the product r_s w_s (what every consumer needs); for spin alpha the block
+// also reduces it into per-walker partial sums.
 __global__ void __launch_bounds__(256)
 k_weights(SpinTables tb, const double2* __restrict__ r_self, const double2* __restrict__ r_other,
           int n_other, double2* __restrict__ wts, double2* __restrict__ part, int nslot,
@@ -289,8 +290,8 @@ k_weights(SpinTables tb, const double2* __restrict__ r_self, const double2* __re
         const double2* ro = r_other + (size_t)w * n_other;
         for (int e = tb.csr_off[s]; e < tb.csr_off[s + 1]; ++e)
             acc = cadd(acc, cscale(ro[tb.csr_other[e]], tb.csr_c[e]));
-        wts[(size_t)w * tb.n_str + s] = acc;
         rw = cmul(r_self[(size_t)w * tb.n_str + s], acc);
+        wts[(size_t)w * tb.n_str + s] = rw;
     }
     if (part) {
         __shared__ double2 red[256];
@@ -354,77 +355,98 @@ void launch_sum_slots(int nw, const double2* part, int nslot, int slot0, int n, 
 
 // ------------------------------------------------------------------------
 // Cofactor accumulation (reduce_CI): per (walker, spin)
-//   Cm[p][h] = sum_s w_s r_s B_s[i][j]  at (p_i, h_j),
-// so that G_T - G = (E_P - G[:, P]) Cm G[H, :] / R. Each block takes a chunk
-// of strings of one walker and accumulates into warp-private shared copies
-// (few collisions, no global atomics); a second pass sums the chunks in a
-// fixed order. Accumulation precision T (double in FP64 mode, float in
-// mixed mode).
-#define CMAT_CHUNK 1024
-template <typename T>
-__global__ void __launch_bounds__(256)
-k_cmat(SpinTables tb, const double2* __restrict__ r, const double2* __restrict__ wts,
-       const void* __restrict__ Bin, double2* __restrict__ Cpart, int nchunk)
+//   Cm[p][h] = sum_s w_s r_s B_s[i][j]  at (p_i, h_j) = (p, h)
+// (wts holds the products r_s w_s).
+// One block per walker. The k^2 entries of one string's minor land on
+// distinct (p, h), so a group of lanes takes a whole string at once and adds
+// its entries into the group's own shared-memory copy of Cm with plain
+// read-modify-writes: B is read in its stored order (coalesced) and nothing
+// is atomic. Strings with k^2 <= 16 go two to a warp (half-warp groups),
+// longer ones one to a warp. Each group takes its strings in ascending order
+// and the copies are summed in a fixed order, so the result does not depend
+// on scheduling. Products and the per-copy sums are in T (double in FP64
+// mode, float in mixed mode); the copies are summed in double.
+#define CMAT_COPIES 16
+template <typename T, int GS, int EPL, int U>
+__device__ __forceinline__ void cmat_level(T* __restrict__ a, int g, int ng, int l, int kk, int ns, int s0,
+                                           const T* __restrict__ B, const uint8_t* __restrict__ xt,
+                                           const double2* __restrict__ ww)
 {
-    __shared__ T acc[8][2 * MSD_XMAX];
-    const int w = blockIdx.y, chunk = blockIdx.x;
-    const int X = tb.nh * tb.np;
-    const int warp = threadIdx.x >> 5;
-    for (int e = threadIdx.x; e < 8 * 2 * MSD_XMAX; e += blockDim.x) (&acc[0][0])[e] = 0;
-    __syncthreads();
-    const T* Bb = reinterpret_cast<const T*>(Bin);
-    const int s0 = max(tb.bucket[1], chunk * CMAT_CHUNK);
-    const int s1 = min(tb.n_str, (chunk + 1) * CMAT_CHUNK);
-    for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
-        int k = 1;
-        while (s >= tb.bucket[k + 1]) ++k;
-        const int ns = tb.bucket[k + 1] - tb.bucket[k], sl = s - tb.bucket[k];
-        const double2 f = cmul(r[(size_t)w * tb.n_str + s], wts[(size_t)w * tb.n_str + s]);
-        const T fr = (T)f.x, fi = (T)f.y;
-        const T* B = Bb + 2 * ((size_t)tb.b_off[k] + ((size_t)w * ns + sl) * (k * k));
-        const uint8_t* sh = tb.str_h + (size_t)s * MSD_KMAX;
-        const uint8_t* sp = tb.str_p + (size_t)s * MSD_KMAX;
-        for (int i = 0; i < k; ++i) {
-            const int row = sp[i] * tb.nh;
-            for (int j = 0; j < k; ++j) {
-                const T br = B[2 * (i * k + j)], bi = B[2 * (i * k + j) + 1];
-                const int x = row + sh[j];
-                atomicAdd(&acc[warp][2 * x], fr * br - fi * bi);
-                atomicAdd(&acc[warp][2 * x + 1], fr * bi + fi * br);
+    for (int base = 0; base < ns; base += ng * U) {
+        T vr[U][EPL], vi[U][EPL];
+        int vx[U][EPL];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int sl = base + u * ng + g;
+            double2 f = cz(0, 0);
+            if (sl < ns) f = ww[s0 + sl];
+            const T fr = (T)f.x, fi = (T)f.y;
+#pragma unroll
+            for (int q = 0; q < EPL; ++q) {
+                const int e = l + q * GS;
+                vx[u][q] = -1;
+                vr[u][q] = 0;
+                vi[u][q] = 0;
+                if (sl < ns && e < kk) {
+                    const size_t o = (size_t)sl * kk + e;
+                    const T br = B[2 * o], bi = B[2 * o + 1];
+                    vx[u][q] = xt[o];
+                    vr[u][q] = fr * br - fi * bi;
+                    vi[u][q] = fr * bi + fi * br;
+                }
             }
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+#pragma unroll
+            for (int q = 0; q < EPL; ++q)
+                if (vx[u][q] >= 0) {
+                    a[2 * vx[u][q]] += vr[u][q];
+                    a[2 * vx[u][q] + 1] += vi[u][q];
+                }
+            __syncwarp();   // the group's next string may share entries with this one
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_cmat(SpinTables tb, const double2* __restrict__ wts, const void* __restrict__ Bin, double2* __restrict__ Cm)
+{
+    __shared__ T acc[CMAT_COPIES][2 * MSD_XMAX];
+    const int w = blockIdx.x, X = tb.nh * tb.np;
+    for (int e = threadIdx.x; e < CMAT_COPIES * 2 * MSD_XMAX; e += blockDim.x) (&acc[0][0])[e] = 0;
+    __syncthreads();
+    const T* Bb = reinterpret_cast<const T*>(Bin);
+    const double2* ww = wts + (size_t)w * tb.n_str;
+    for (int k = 1; k <= MSD_KMAX; ++k) {
+        const int s0 = tb.bucket[k], ns = tb.bucket[k + 1] - s0, kk = k * k;
+        if (ns == 0) continue;
+        const T* B = Bb + 2 * ((size_t)tb.b_off[k] + (size_t)w * ns * kk);
+        const uint8_t* xt = tb.cmx + tb.cmx_off[k];
+        if (kk <= 16)
+            cmat_level<T, 16, 1, 4>(acc[threadIdx.x >> 4], threadIdx.x >> 4, 16, threadIdx.x & 15, kk, ns, s0, B, xt, ww);
+        else if (kk <= 32)
+            cmat_level<T, 32, 1, 4>(acc[(threadIdx.x >> 5) * 2], threadIdx.x >> 5, 8, threadIdx.x & 31, kk, ns, s0, B,
+                                    xt, ww);
+        else
+            cmat_level<T, 32, 2, 4>(acc[(threadIdx.x >> 5) * 2], threadIdx.x >> 5, 8, threadIdx.x & 31, kk, ns, s0, B,
+                                    xt, ww);
     }
     __syncthreads();
     for (int x = threadIdx.x; x < X; x += blockDim.x) {
         double re = 0, im = 0;
-        for (int q = 0; q < 8; ++q) { re += (double)acc[q][2 * x]; im += (double)acc[q][2 * x + 1]; }
-        Cpart[((size_t)w * nchunk + chunk) * X + x] = cz(re, im);
+        for (int q = 0; q < CMAT_COPIES; ++q) { re += (double)acc[q][2 * x]; im += (double)acc[q][2 * x + 1]; }
+        Cm[(size_t)w * X + x] = cz(re, im);
     }
 }
 
-__global__ void k_cmat_reduce(int nw, int X, int nchunk, const double2* __restrict__ Cpart, double2* __restrict__ Cm)
+void launch_cmat(const SpinTables& tb, int nw, const double2* wts, const void* B, bool fp32, double2* Cm,
+                 cudaStream_t st)
 {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nw * X) return;
-    const int w = e / X, x = e % X;
-    double2 a = cz(0, 0);
-    for (int c = 0; c < nchunk; ++c) a = cadd(a, Cpart[((size_t)w * nchunk + c) * X + x]);
-    Cm[e] = a;
-}
-
-int cmat_chunks(const SpinTables& tb) { return (tb.n_str + CMAT_CHUNK - 1) / CMAT_CHUNK; }
-
-void launch_cmat(const SpinTables& tb, int nw, const double2* r, const double2* wts, const void* B,
-                 bool fp32, double2* Cpart, double2* Cm, cudaStream_t st)
-{
-    const int X = tb.nh * tb.np;
-    if (X <= 0) return;
-    const int nchunk = cmat_chunks(tb);
-    dim3 grid(nchunk, nw);
-    if (fp32) k_cmat<float><<<grid, 256, 0, st>>>(tb, r, wts, B, Cpart, nchunk);
-    else k_cmat<double><<<grid, 256, 0, st>>>(tb, r, wts, B, Cpart, nchunk);
-    msd_note_launch();
-    k_cmat_reduce<<<(nw * X + 255) / 256, 256, 0, st>>>(nw, X, nchunk, Cpart, Cm);
+    if (tb.nh * tb.np <= 0) return;
+    if (fp32) k_cmat<float><<<nw, 256, 0, st>>>(tb, wts, B, Cm);
+    else k_cmat<double><<<nw, 256, 0, st>>>(tb, wts, B, Cm);
     msd_note_launch();
 }
 

@@ -25,9 +25,8 @@ void launch_det_ratios(const PairTables& pt, int nw, int n_str_a, int n_str_b, c
 void launch_sum_slots(int nw, const double2* part, int nslot, int slot0, int n, double2* out,
                       const double2* O0a, const double2* O0b, double2* ovlp, cudaStream_t st);
 void launch_ref_ovlp(int nw, const double2* O0a, const double2* O0b, double2* out, cudaStream_t st);
-int cmat_chunks(const SpinTables& tb);
-void launch_cmat(const SpinTables& tb, int nw, const double2* r, const double2* wts, const void* B,
-                 bool fp32, double2* Cpart, double2* Cm, cudaStream_t st);
+void launch_cmat(const SpinTables& tb, int nw, const double2* wts, const void* B, bool fp32, double2* Cm,
+                 cudaStream_t st);
 void launch_gt(const SpinTables& tb, int nw, int M, const double2* Gr, const double2* Cm,
                const double2* R, double2* GT, long long ld, long long off, bool minus_ref, cudaStream_t st);
 
@@ -48,7 +47,7 @@ void launch_gram(int nw, int Xp, int Xq, int n_chol, const double2* P, const dou
 int string_energy_blocks(const SpinTables& tb, int k);
 size_t string_energy_smem(const SpinTables& tb, bool fp32);
 int string_energy_slots(const SpinTables& tb);
-void launch_string_energy(const SpinTables& tb, int nw, const double2* r, const double2* wts,
+void launch_string_energy(const SpinTables& tb, int nw, const double2* wts,
                           const void* B, const void* K, const void* Y, bool fp32, double2* part,
                           int nslot, int slot0, cudaStream_t st);
 int pair_cross_slots(const PairTables& pt);

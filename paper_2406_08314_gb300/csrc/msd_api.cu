@@ -39,6 +39,7 @@ struct SpinHost {
     int *d_csr_off = nullptr, *d_csr_other = nullptr;
     double* d_csr_c = nullptr;
     double* d_Lh = nullptr;   // [n_chol][N + np][M]
+    uint8_t* d_cmx = nullptr;
     int* d_pos0 = nullptr;    // [M] position of an orbital in occ0, or -1
 };
 
@@ -235,12 +236,16 @@ SpinTables tables(const SpinHost& s, int cap)
     t.occ0 = s.d_occ0; t.hole_pos = s.d_hole_pos; t.part_orb = s.d_part_orb;
     t.str_h = s.d_str_h; t.str_p = s.d_str_p; t.str_sign = s.d_str_sign;
     t.csr_off = s.d_csr_off; t.csr_other = s.d_csr_other; t.csr_c = s.d_csr_c;
-    long long off = 0;
+    t.cmx = s.d_cmx;
+    long long off = 0, xo = 0;
     for (int k = 0; k <= MSD_KMAX; ++k) {
         t.b_off[k] = off;
+        t.cmx_off[k] = xo;
         off += (long long)cap * k * k * (s.bucket[k + 1] - s.bucket[k]);
+        xo += (long long)k * k * (s.bucket[k + 1] - s.bucket[k]);
     }
     t.b_off[MSD_KMAX + 1] = off;
+    t.cmx_off[MSD_KMAX + 1] = xo;
     t.b_per_walker = s.b_per_walker;
     return t;
 }
@@ -371,6 +376,18 @@ int upload_spin(msd_ctx* ctx, SpinHost& S)
     std::vector<int> pos0(ctx->M, -1);
     for (int j = 0; j < S.N; ++j) pos0[S.occ0[j]] = j;
     if ((rc = upload(ctx, &S.d_pos0, pos0))) return rc;
+    // active entry x = p_i nh + h_j of every (i, j) of every string's minor,
+    // in the order of the inverse minors B
+    std::vector<uint8_t> cmx;
+    cmx.reserve((size_t)std::max<long long>(1, S.b_per_walker));
+    for (int k = 1; k <= MSD_KMAX; ++k)
+        for (int sidx = S.bucket[k]; sidx < S.bucket[k + 1]; ++sidx)
+            for (int i = 0; i < k; ++i)
+                for (int j = 0; j < k; ++j)
+                    cmx.push_back((uint8_t)(S.str_p[(size_t)sidx * MSD_KMAX + i] * S.nh +
+                                            S.str_h[(size_t)sidx * MSD_KMAX + j]));
+    if (cmx.empty()) cmx.push_back(0);
+    if ((rc = upload(ctx, &S.d_cmx, cmx))) return rc;
     return MSD_OK;
 }
 
@@ -379,6 +396,8 @@ void free_spin(SpinHost& S)
     cudaFree(S.d_occ0); cudaFree(S.d_hole_pos); cudaFree(S.d_part_orb); cudaFree(S.d_str_h);
     cudaFree(S.d_str_p); cudaFree(S.d_str_sign); cudaFree(S.d_csr_off); cudaFree(S.d_csr_other);
     cudaFree(S.d_csr_c); cudaFree(S.d_Lh); cudaFree(S.d_pos0);
+    cudaFree(S.d_cmx);
+    S.d_cmx = nullptr;
     S.d_pos0 = nullptr;
     S.d_occ0 = S.d_hole_pos = S.d_part_orb = nullptr;
     S.d_str_h = S.d_str_p = nullptr;
@@ -706,7 +725,7 @@ int begin_call(msd_ctx* ctx, int n_w, const double* pa, const double* pb, cudaSt
 // Force-bias part for one chunk: cofactor matrix, G_T rows, contraction
 // with the half-rotated Cholesky vectors.
 struct FbWork {
-    void *GT = nullptr, *Rs = nullptr, *Cm[2] = {nullptr, nullptr}, *Cpart = nullptr;
+    void *GT = nullptr, *Rs = nullptr, *Cm[2] = {nullptr, nullptr};
     void *Ah = nullptr, *Al = nullptr, *C32 = nullptr;
     int ks = 1;
 };
@@ -716,7 +735,7 @@ size_t fb_bytes_per_walker(msd_ctx* ctx, bool fp32)
     size_t b = sizeof(double2) * (ctx->Kd + 1);
     for (int s = 0; s < 2; ++s) {
         const SpinTables t = tables(ctx->sp[s], 1);
-        b += sizeof(double2) * (size_t)t.nh * t.np * (1 + cmat_chunks(t));
+        b += sizeof(double2) * (size_t)t.nh * t.np;
     }
     if (fp32) b += sizeof(float) * 2 * 2 * ctx->Kdp + sizeof(float) * 16 * 2 * ctx->n_chol;
     return b;
@@ -727,14 +746,11 @@ int fb_alloc(msd_ctx* ctx, int cap, bool fp32, FbWork& f)
     int rc;
     if ((rc = arena_get(ctx, "GT", sizeof(double2) * cap * ctx->Kd, &f.GT))) return rc;
     if ((rc = arena_get(ctx, "Rsum", sizeof(double2) * cap, &f.Rs))) return rc;
-    size_t cp = 1;
     for (int s = 0; s < 2; ++s) {
         const SpinTables t = tables(ctx->sp[s], 1);
         static const char* nm[2] = {"Cm_a", "Cm_b"};
         if ((rc = arena_get(ctx, nm[s], sizeof(double2) * cap * std::max(1, t.nh * t.np), &f.Cm[s]))) return rc;
-        cp = std::max(cp, (size_t)cap * std::max(1, t.nh * t.np) * cmat_chunks(t));
     }
-    if ((rc = arena_get(ctx, "Cpart", sizeof(double2) * cp, &f.Cpart))) return rc;
     if (fp32) {
         f.ks = std::max(1, std::min(16, (int)(ctx->Kdp / 32 / 64)));
         if ((rc = arena_get(ctx, "Av_hi", sizeof(float) * 2 * cap * ctx->Kdp, &f.Ah))) return rc;
@@ -757,7 +773,7 @@ int fb_chunk(msd_ctx* ctx, Chunk& c, FbWork& f, int w0, int nw, int cap, bool fp
     for (int s = 0; s < 2; ++s) {
         const SpinTables T = tables(ctx->sp[s], cap);
         th.begin("k_cmat", st);
-        launch_cmat(T, nw, c.r[s], c.wts[s], c.B[s], fp32, (double2*)f.Cpart, (double2*)f.Cm[s], st);
+        launch_cmat(T, nw, c.wts[s], c.B[s], fp32, (double2*)f.Cm[s], st);
         th.end(st);
         th.begin("k_gt", st);
         launch_gt(T, nw, ctx->M, c.Gr[s], (double2*)f.Cm[s], (double2*)f.Rs, (double2*)f.GT, ctx->Kd, off, fp32,
@@ -960,7 +976,7 @@ int en_chunk(msd_ctx* ctx, Chunk& c, EnWork& E, int w0, int nw, int cap, bool fp
     void* Kss[2] = {E.Kaa, E.Kbb};
     th.begin("k_string_energy", st);
     for (int s = 0; s < 2; ++s) {
-        launch_string_energy(T[s], nw, c.r[s], c.wts[s], c.B[s], Kss[s], E.Y[s], fp32, c.part, c.nslot, slot, st);
+        launch_string_energy(T[s], nw, c.wts[s], c.B[s], Kss[s], E.Y[s], fp32, c.part, c.nslot, slot, st);
         slot += string_energy_slots(T[s]);
     }
     th.end(st);
