@@ -131,21 +131,58 @@ void launch_ref(const double2* phi, int nw, int M, int N, const SpinTables& T, d
 // Excitation strings of level K for one spin (get_dets / build_det_matrix):
 // A[i][j] = G[h_i][p_j] (a K x K minor of G). LU with partial pivoting in
 // FP64 gives r = sign * det A, the overlap ratio <D_s|phi>/<D_0|phi> of the
-// string's spin sector. B = A^-1 (precision T: double in FP64 mode, float
-// in mixed mode, solved from the LU factors with the pivot reciprocals) is
-// stored per string, K*K entries contiguous (B[i][j] at i*K + j), for the
-// Green's-function and energy terms. One thread per (walker, string); the
-// walker's active block lives in shared memory.
+// string's spin sector. B = A^-1 is stored per string, K*K entries
+// contiguous (B[i][j] at i*K + j), for the Green's-function and energy
+// terms: in FP64 mode solved from the FP64 LU factors; in mixed mode from an
+// FP32 elimination of the same row order (the FP64 pivots) on an FP32 copy of
+// the active block. One thread per (walker, string); the walker's active
+// block lives in shared memory.
+//
+// FP64 issue rate is the bound here (a few FP64 operations per clock per
+// SM), so the LU spends FP64 operations on the elimination and the
+// determinant only: the pivot search compares integer magnitude keys (the
+// larger high word of |Re|, |Im|: partial pivoting by the max-norm), the row
+// swaps count parity in an integer, and the pivot reciprocals are
+// Newton-Raphson iterations from an FP32 seed.
+
+// 1 / m for m > 0: y <- y + y (1 - m y) (Newton-Raphson for f(y) = 1/y - m),
+// two steps from the FP32 reciprocal (~2^-22 relative) reach FP64 rounding
+// (2^-44, then below 2^-53 before rounding). Outside the FP32 normal range
+// the quotient is taken directly.
+__device__ __forceinline__ double recip_nr(double m)
+{
+    if (!(m > 1e-36 && m < 1e36)) return 1.0 / m;
+    float yf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"((float)m));
+    double y = (double)yf;
+    double e = fma(-m, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-m, y, 1.0);
+    return fma(y, e, y);
+}
+
+// monotone in max(|Re v|, |Im v|) up to the low 32 bits of each mantissa
+__device__ __forceinline__ int mag_key(double2 v)
+{
+    return max(__double2hiint(v.x) & 0x7fffffff, __double2hiint(v.y) & 0x7fffffff);
+}
+
 template <int K, typename T>
 __global__ void __launch_bounds__(128)
 k_strings(SpinTables tb, int nw, const double2* __restrict__ Gact, double2* __restrict__ r,
           void* __restrict__ Bout, int want_b)
 {
     using T2 = typename std::conditional<std::is_same<T, float>::value, float2, double2>::type;
+    constexpr bool F32B = std::is_same<T, float>::value;
     __shared__ double2 g[MSD_XMAX];
+    __shared__ float2 gf[F32B ? MSD_XMAX : 1];
     const int w = blockIdx.y;
     const int X = tb.nh * tb.np;
-    for (int e = threadIdx.x; e < X; e += blockDim.x) g[e] = Gact[(size_t)w * X + e];
+    for (int e = threadIdx.x; e < X; e += blockDim.x) {
+        const double2 v = Gact[(size_t)w * X + e];
+        g[e] = v;
+        if constexpr (F32B) gf[e] = make_float2((float)v.x, (float)v.y);
+    }
     __syncthreads();
     const int ns = tb.bucket[K + 1] - tb.bucket[K];
     const int sl = blockIdx.x * blockDim.x + threadIdx.x;
@@ -164,48 +201,77 @@ k_strings(SpinTables tb, int nw, const double2* __restrict__ Gact, double2* __re
     double2 det = cz(tb.str_sign[s], 0);
     double2 dinv[K];
     bool sing = false;
+    int odd = 0;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        // pivot: largest |re| + |im| in column k
-        int p = k;
-        double best = fabs(a[k][k].x) + fabs(a[k][k].y);
+        int p = k, best = mag_key(a[k][k]);
+        double2 pv = a[k][k];
 #pragma unroll
         for (int i = k + 1; i < K; ++i) {
-            const double v = fabs(a[i][k].x) + fabs(a[i][k].y);
-            if (v > best) { best = v; p = i; }
+            const int v = mag_key(a[i][k]);
+            if (v > best) { best = v; p = i; pv = a[i][k]; }
         }
-        if (best == 0.0) sing = true;
+        if (pv.x == 0.0 && pv.y == 0.0) sing = true;
 #pragma unroll
         for (int i = k + 1; i < K; ++i) {
             if (i == p) {
 #pragma unroll
                 for (int j = 0; j < K; ++j) { double2 tt = a[k][j]; a[k][j] = a[i][j]; a[i][j] = tt; }
                 int tp = perm[k]; perm[k] = perm[i]; perm[i] = tp;
-                det = cz(-det.x, -det.y);
+                odd ^= 1;
             }
         }
         det = cmul(det, a[k][k]);
-        const double m2 = a[k][k].x * a[k][k].x + a[k][k].y * a[k][k].y;
-        const double im2 = sing ? 0.0 : 1.0 / m2;
+        const double m2 = fma(a[k][k].x, a[k][k].x, a[k][k].y * a[k][k].y);
+        const double im2 = sing ? 0.0 : recip_nr(m2);
         dinv[k] = cz(a[k][k].x * im2, -a[k][k].y * im2);
+        if (k + 1 < K) {
 #pragma unroll
-        for (int i = k + 1; i < K; ++i) {
-            const double2 f = cmul(a[i][k], dinv[k]);
-            a[i][k] = f;
+            for (int i = k + 1; i < K; ++i) {
+                const double2 f = cmul(a[i][k], dinv[k]);
+                a[i][k] = f;
 #pragma unroll
-            for (int j = k + 1; j < K; ++j) a[i][j] = cfms(f, a[k][j], a[i][j]);
+                for (int j = k + 1; j < K; ++j) a[i][j] = cfms(f, a[k][j], a[i][j]);
+            }
         }
     }
+    if (odd) det = cz(-det.x, -det.y);
     if (sing) det = cz(0, 0);
     r[(size_t)w * tb.n_str + s] = det;
     if (!want_b) return;
     // B = A^-1 from P A = L U: column c solves L U x = P e_c, in precision T.
     T2 lu[K][K], di[K];
+    if constexpr (F32B) {
+        // FP32 elimination of the rows in the FP64 pivot order
 #pragma unroll
-    for (int i = 0; i < K; ++i) {
-        di[i] = T2{(T)dinv[i].x, (T)dinv[i].y};
+        for (int i = 0; i < K; ++i) {
+            const int ro = sh[perm[i]] * tb.np;
 #pragma unroll
-        for (int j = 0; j < K; ++j) lu[i][j] = T2{(T)a[i][j].x, (T)a[i][j].y};
+            for (int j = 0; j < K; ++j) lu[i][j] = gf[ro + sp[j]];
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float m2 = fmaf(lu[k][k].x, lu[k][k].x, lu[k][k].y * lu[k][k].y);
+            const float im2 = (sing || !(m2 > 0.f)) ? 0.f : 1.f / m2;
+            di[k] = make_float2(lu[k][k].x * im2, -lu[k][k].y * im2);
+#pragma unroll
+            for (int i = k + 1; i < K; ++i) {
+                const float2 f = fmul(lu[i][k], di[k]);
+                lu[i][k] = f;
+#pragma unroll
+                for (int j = k + 1; j < K; ++j) {
+                    lu[i][j].x -= f.x * lu[k][j].x - f.y * lu[k][j].y;
+                    lu[i][j].y -= f.x * lu[k][j].y + f.y * lu[k][j].x;
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            di[i] = T2{(T)dinv[i].x, (T)dinv[i].y};
+#pragma unroll
+            for (int j = 0; j < K; ++j) lu[i][j] = T2{(T)a[i][j].x, (T)a[i][j].y};
+        }
     }
     T2* B = reinterpret_cast<T2*>(Bout) + (size_t)tb.b_off[K] + ((size_t)w * ns + sl) * (K * K);
 #pragma unroll
