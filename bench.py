@@ -209,6 +209,10 @@ def algorithmic_work(s, n_w):
     w["k_string_energy"] = sum(float(np.sum(sp["lv"] * (10 * k ** 4 + 16 * k ** 2))) for sp in spins) * n_w
     w["k_pair_cross"] = sum(8.0 * n * (ka * ka * kb * kb + ka * ka) for (ka, kb), n in pair_lv.items()
                             if ka and kb) * n_w
+    # the per-beta-string form (mixed precision): Y_b over the alpha block
+    # for every excited beta string, then k_a^2 per determinant
+    w["k_pair_y"] = (8.0 * spins[0]["X"] * float(np.sum(spins[1]["lv"][1:] * k[1:] ** 2))
+                     + sum(8.0 * n * ka * ka for (ka, kb), n in pair_lv.items() if ka and kb)) * n_w
     Kd = sum(sp["NC"] * M for sp in spins)
     w["k_gemm_vbias"] = 4.0 * Kd * G * n_w
     # tensor-core GEMMs: real GEMM flops of the contraction actually needed

@@ -192,6 +192,21 @@ int msd_set_sync(msd_ctx* ctx, int sync);
    memory) take the unfused path. */
 int msd_set_fused(msd_ctx* ctx, int fused);
 
+/* Mixed precision only: the form of the opposite-spin exchange term of the
+   local energy (Sec. III, the alpha-beta part of the two-body Wick
+   contraction),
+     sum_I c_I r_a r_b sum_ij sum_kl Ba[i][j] Bb[k][l] K^ab[(h_j,p_i)][(h_l,p_k)].
+   form = 1: the inner sum is formed once per beta string b,
+   Y_b[x] = sum_kl Bb[k][l] K^ab[x][(h_l,p_k)], so a determinant costs k_a^2
+   instead of k_a^2 k_b^2 operations (pays when many determinants share a
+   beta string); form = 0: every determinant takes the double sum;
+   form = -1 (the default): chosen per trial by a cost model over the
+   trial's excitation levels. The two forms differ by FP32 summation order
+   only. A batch (msd_batch_create) sets its systems to 0, the form its
+   persistent kernel implements. FP64 contexts always take the
+   per-determinant form. MSD_ERR_ARG for other values. */
+int msd_set_pair_form(msd_ctx* ctx, int form);
+
 /* Number of CUDA kernels the library has launched in this process (all
    contexts), for launch accounting by benchmarks. */
 long long msd_launch_count(void);
@@ -232,7 +247,8 @@ int msd_propagate(msd_ctx* ctx, int n_w, double* phi_a, double* phi_b, double* w
    Arrays are indexed by system: n_w[i] walkers, device pointers phi_a[i],
    phi_b[i], e_loc[i] (required), ovlp[i], vbias[i] (arrays or entries may be
    NULL). Every system's walkers must fit one workspace chunk (MSD_ERR_SHAPE
-   otherwise). The contexts must outlive the batch. */
+   otherwise). The contexts must outlive the batch; creating the batch sets
+   each to the per-determinant opposite-spin form (msd_set_pair_form 0). */
 typedef struct msd_batch msd_batch;
 int msd_batch_create(msd_batch** out, msd_ctx* const* ctxs, int n_sys);
 void msd_batch_destroy(msd_batch* b);

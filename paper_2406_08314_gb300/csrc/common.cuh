@@ -80,6 +80,8 @@ struct SpinTables {
     const double* csr_c;   // [nnz] CI coefficient of that determinant
     const uint8_t* cmx;    // [sum_k k^2 n_k] x = p_i nh + h_j of entry (i, j) of each string's
                            // minor, bucket-major, a string's k^2 entries row-major (B's order)
+    const uint8_t* kx;     // same layout: h_j np + p_i, the row/column of the Gram matrices
+    const float* csr_cf;   // [nnz] csr_c in FP32
     long long b_off[MSD_KMAX + 2];  // per-walker offset (complex units) of each bucket's B block
     long long b_per_walker;         // sum_k k^2 * (strings of level k)
     long long cmx_off[MSD_KMAX + 2];  // offset of each bucket's entries in cmx

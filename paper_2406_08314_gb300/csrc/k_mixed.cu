@@ -205,36 +205,29 @@ void launch_gamma_reduce_f32(int nw, int X, int n_chol, int spin, const double2*
 // broadcast to the 16 threads of a row) and each Q value (consecutive,
 // conflict-free) serves R complex FMAs. Cholesky vectors stream through
 // shared memory GRAM_G at a time; the sum over g runs in a fixed order.
+// When P and Q are the same vectors (the same-spin Gram matrices, symmetric)
+// only the sub-tiles i <= j are accumulated, one operand is staged, and the
+// upper sub-tiles are mirrored on the way out.
 #define GRAM_G 32
-template <int R>
-__global__ void __launch_bounds__(256)
-k_gram_f32(GramJobs jobs, int n_chol)
+template <int R, bool SYM>
+__device__ __forceinline__ void gram_body(int Xp, int Xq, int n_chol, const float2* __restrict__ Pw,
+                                          const float2* __restrict__ Qw, float2* __restrict__ Kw, float2* gsm)
 {
-    const GramJob& jb = jobs.j[blockIdx.y];
-    const int Xp = jb.Xp, Xq = jb.Xq;
-    const float2* __restrict__ P = jb.P;
-    const float2* __restrict__ Q = jb.Q;
-    float2* __restrict__ Kout = jb.K;
-    if (Xp <= 0 || Xq <= 0) return;
-    extern __shared__ float2 gsm[];
-    float2* ps = gsm;                       // [GRAM_G][16 R]
-    float2* qs = gsm + GRAM_G * 16 * R;     // [GRAM_G][16 R]
     constexpr int W = 16 * R;
-    const int w = blockIdx.x;
+    float2* ps = gsm;                                 // [GRAM_G][16 R]
+    float2* qs = SYM ? gsm : gsm + GRAM_G * W;        // [GRAM_G][16 R]
     const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
     float2 acc[R][R];
 #pragma unroll
     for (int i = 0; i < R; ++i)
 #pragma unroll
         for (int j = 0; j < R; ++j) acc[i][j] = make_float2(0.f, 0.f);
-    const float2* Pw = P + (size_t)w * n_chol * Xp;
-    const float2* Qw = Q + (size_t)w * n_chol * Xq;
     for (int g0 = 0; g0 < n_chol; g0 += GRAM_G) {
         __syncthreads();   // previous chunk consumed
         for (int e = t; e < GRAM_G * W; e += 256) {
             const int gg = e / W, xx = e - gg * W, g = g0 + gg;
             ps[e] = (g < n_chol && xx < Xp) ? Pw[(size_t)g * Xp + xx] : make_float2(0.f, 0.f);
-            qs[e] = (g < n_chol && xx < Xq) ? Qw[(size_t)g * Xq + xx] : make_float2(0.f, 0.f);
+            if (!SYM) qs[e] = (g < n_chol && xx < Xq) ? Qw[(size_t)g * Xq + xx] : make_float2(0.f, 0.f);
         }
         __syncthreads();
 #pragma unroll 2
@@ -248,16 +241,36 @@ k_gram_f32(GramJobs jobs, int n_chol)
 #pragma unroll
             for (int i = 0; i < R; ++i)
 #pragma unroll
-                for (int j = 0; j < R; ++j) acc[i][j] = fcfma(pv[i], qv[j], acc[i][j]);
+                for (int j = SYM ? i : 0; j < R; ++j) acc[i][j] = fcfma(pv[i], qv[j], acc[i][j]);
         }
     }
 #pragma unroll
     for (int i = 0; i < R; ++i)
 #pragma unroll
-        for (int j = 0; j < R; ++j) {
+        for (int j = SYM ? i : 0; j < R; ++j) {
             const int x = ty + 16 * i, y = tx + 16 * j;
-            if (x < Xp && y < Xq) Kout[((size_t)w * Xp + x) * Xq + y] = acc[i][j];
+            if (x < Xp && y < Xq) {
+                Kw[(size_t)x * Xq + y] = acc[i][j];
+                if (SYM && j > i) Kw[(size_t)y * Xq + x] = acc[i][j];
+            }
         }
+}
+
+template <int R>
+__global__ void __launch_bounds__(256, R <= 5 ? 3 : 1)
+k_gram_f32(GramJobs jobs, int n_chol)
+{
+    // static indices keep the job table in the parameter space
+    const GramJob jb = blockIdx.y == 0 ? jobs.j[0] : blockIdx.y == 1 ? jobs.j[1] : jobs.j[2];
+    const int Xp = jb.Xp, Xq = jb.Xq;
+    if (Xp <= 0 || Xq <= 0) return;
+    extern __shared__ float2 gsm[];
+    const int w = blockIdx.x;
+    const float2* Pw = jb.P + (size_t)w * n_chol * Xp;
+    const float2* Qw = jb.Q + (size_t)w * n_chol * Xq;
+    float2* Kw = jb.K + (size_t)w * Xp * Xq;
+    if (jb.P == jb.Q && Xp == Xq) gram_body<R, true>(Xp, Xq, n_chol, Pw, Qw, Kw, gsm);
+    else gram_body<R, false>(Xp, Xq, n_chol, Pw, Qw, Kw, gsm);
 }
 
 template <int R>

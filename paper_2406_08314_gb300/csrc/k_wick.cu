@@ -170,7 +170,7 @@ __device__ __forceinline__ int mag_key(double2 v)
 template <int K, typename T>
 __global__ void __launch_bounds__(128)
 k_strings(SpinTables tb, int nw, const double2* __restrict__ Gact, double2* __restrict__ r,
-          void* __restrict__ Bout, int want_b)
+          float2* __restrict__ rf, void* __restrict__ Bout, int want_b)
 {
     using T2 = typename std::conditional<std::is_same<T, float>::value, float2, double2>::type;
     constexpr bool F32B = std::is_same<T, float>::value;
@@ -238,6 +238,7 @@ k_strings(SpinTables tb, int nw, const double2* __restrict__ Gact, double2* __re
     if (odd) det = cz(-det.x, -det.y);
     if (sing) det = cz(0, 0);
     r[(size_t)w * tb.n_str + s] = det;
+    if (rf) rf[(size_t)w * tb.n_str + s] = make_float2((float)det.x, (float)det.y);
     if (!want_b) return;
     // B = A^-1 from P A = L U: column c solves L U x = P e_c, in precision T.
     T2 lu[K][K], di[K];
@@ -302,39 +303,42 @@ k_strings(SpinTables tb, int nw, const double2* __restrict__ Gact, double2* __re
 }
 
 template <int K>
-static void launch_strings_k(const SpinTables& tb, int nw, const double2* Gact, double2* r, void* B,
+static void launch_strings_k(const SpinTables& tb, int nw, const double2* Gact, double2* r, float2* rf, void* B,
                              bool fp32, int want_b, cudaStream_t st)
 {
     const int ns = tb.bucket[K + 1] - tb.bucket[K];
     if (ns <= 0) return;
     dim3 grid((ns + 127) / 128, nw);
-    if (fp32) k_strings<K, float><<<grid, 128, 0, st>>>(tb, nw, Gact, r, B, want_b);
-    else k_strings<K, double><<<grid, 128, 0, st>>>(tb, nw, Gact, r, B, want_b);
+    if (fp32) k_strings<K, float><<<grid, 128, 0, st>>>(tb, nw, Gact, r, rf, B, want_b);
+    else k_strings<K, double><<<grid, 128, 0, st>>>(tb, nw, Gact, r, rf, B, want_b);
     msd_note_launch();
 }
 
 // Reference string (level 0): ratio 1.
-__global__ void k_ref_string(int nw, int n_str, double2* r)
+__global__ void k_ref_string(int nw, int n_str, double2* r, float2* rf)
 {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w < nw) r[(size_t)w * n_str] = cz(1, 0);
+    if (w < nw) {
+        r[(size_t)w * n_str] = cz(1, 0);
+        if (rf) rf[(size_t)w * n_str] = make_float2(1.f, 0.f);
+    }
 }
 
-void launch_strings(const SpinTables& tb, int nw, const double2* Gact, double2* r, void* B,
+void launch_strings(const SpinTables& tb, int nw, const double2* Gact, double2* r, float2* rf, void* B,
                     bool fp32, bool want_b, cudaStream_t st, const TimerHook& th)
 {
     if (tb.bucket[1] > tb.bucket[0]) {
         th.begin("k_ref_string", st);
-        k_ref_string<<<(nw + 127) / 128, 128, 0, st>>>(nw, tb.n_str, r); msd_note_launch();
+        k_ref_string<<<(nw + 127) / 128, 128, 0, st>>>(nw, tb.n_str, r, rf); msd_note_launch();
         th.end(st);
     }
     th.begin("k_strings", st);
-    launch_strings_k<1>(tb, nw, Gact, r, B, fp32, want_b, st);
-    launch_strings_k<2>(tb, nw, Gact, r, B, fp32, want_b, st);
-    launch_strings_k<3>(tb, nw, Gact, r, B, fp32, want_b, st);
-    launch_strings_k<4>(tb, nw, Gact, r, B, fp32, want_b, st);
-    launch_strings_k<5>(tb, nw, Gact, r, B, fp32, want_b, st);
-    launch_strings_k<6>(tb, nw, Gact, r, B, fp32, want_b, st);
+    launch_strings_k<1>(tb, nw, Gact, r, rf, B, fp32, want_b, st);
+    launch_strings_k<2>(tb, nw, Gact, r, rf, B, fp32, want_b, st);
+    launch_strings_k<3>(tb, nw, Gact, r, rf, B, fp32, want_b, st);
+    launch_strings_k<4>(tb, nw, Gact, r, rf, B, fp32, want_b, st);
+    launch_strings_k<5>(tb, nw, Gact, r, rf, B, fp32, want_b, st);
+    launch_strings_k<6>(tb, nw, Gact, r, rf, B, fp32, want_b, st);
     th.end(st);
 }
 

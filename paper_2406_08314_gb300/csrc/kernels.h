@@ -15,7 +15,7 @@ struct TimerHook {
 // k_wick.cu
 void launch_ref(const double2* phi, int nw, int M, int N, const SpinTables& T, double2* Gr,
                 double2* O0, double2* Gact, unsigned* err, cudaStream_t st);
-void launch_strings(const SpinTables& tb, int nw, const double2* Gact, double2* r, void* B,
+void launch_strings(const SpinTables& tb, int nw, const double2* Gact, double2* r, float2* rf, void* B,
                     bool fp32, bool want_b, cudaStream_t st, const TimerHook& th);
 int weights_blocks(const SpinTables& tb);
 void launch_weights(const SpinTables& tb, int nw, const double2* r_self, const double2* r_other,
@@ -51,6 +51,12 @@ void launch_string_energy(const SpinTables& tb, int nw, const double2* wts,
                           const void* B, const void* K, const void* Y, bool fp32, double2* part,
                           int nslot, int slot0, cudaStream_t st);
 int pair_cross_slots(const PairTables& pt);
+// k_pair_y.cu: the opposite-spin term per beta string (mixed precision)
+bool pair_y_ok(const SpinTables& ta, const SpinTables& tb);
+int pair_y_slots(const SpinTables& tb);
+void launch_pair_y(const SpinTables& ta, const SpinTables& tb, int nw, const float2* rfa, const float2* rfb,
+                   const void* Ba, const void* Bb, const void* Kab, double2* part, int nslot, int slot0,
+                   cudaStream_t st);
 void launch_pair_cross(const SpinTables& ta, const SpinTables& tb, const PairTables& pt, int nw,
                        const double2* ra, const double2* rb, const void* Ba, const void* Bb,
                        const void* K, bool fp32, double2* part, int nslot, int slot0,

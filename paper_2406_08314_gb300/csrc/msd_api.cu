@@ -40,6 +40,8 @@ struct SpinHost {
     double* d_csr_c = nullptr;
     double* d_Lh = nullptr;   // [n_chol][N + np][M]
     uint8_t* d_cmx = nullptr;
+    uint8_t* d_kx = nullptr;
+    float* d_csr_cf = nullptr;
     int* d_pos0 = nullptr;    // [M] position of an orbital in occ0, or -1
 };
 
@@ -105,6 +107,8 @@ struct msd_ctx {
     int tc_bn = 0;                // tensor-core output tile width (0 = by shape)
     int Kv[2] = {0, 0};           // virtual orbitals per spin
     bool fuse = true;             // fused energy contraction + epilogue when the shape allows
+    int pair_form = -1;           // mixed mode, opposite-spin term: -1 auto, 0 per determinant, 1 per beta string
+    bool pair_y_auto = false;     // the auto choice for the current trial (set_trial)
     bool fused_ok[2] = {false, false};
     TcFepiPlan fplan[2];
     long long gen = 0;            // bumped whenever a device buffer may move
@@ -237,6 +241,8 @@ SpinTables tables(const SpinHost& s, int cap)
     t.str_h = s.d_str_h; t.str_p = s.d_str_p; t.str_sign = s.d_str_sign;
     t.csr_off = s.d_csr_off; t.csr_other = s.d_csr_other; t.csr_c = s.d_csr_c;
     t.cmx = s.d_cmx;
+    t.kx = s.d_kx;
+    t.csr_cf = s.d_csr_cf;
     long long off = 0, xo = 0;
     for (int k = 0; k <= MSD_KMAX; ++k) {
         t.b_off[k] = off;
@@ -378,16 +384,24 @@ int upload_spin(msd_ctx* ctx, SpinHost& S)
     if ((rc = upload(ctx, &S.d_pos0, pos0))) return rc;
     // active entry x = p_i nh + h_j of every (i, j) of every string's minor,
     // in the order of the inverse minors B
-    std::vector<uint8_t> cmx;
+    // and the same entry's row of the Gram matrices, h_j np + p_i
+    std::vector<uint8_t> cmx, kx;
     cmx.reserve((size_t)std::max<long long>(1, S.b_per_walker));
+    kx.reserve((size_t)std::max<long long>(1, S.b_per_walker));
     for (int k = 1; k <= MSD_KMAX; ++k)
         for (int sidx = S.bucket[k]; sidx < S.bucket[k + 1]; ++sidx)
             for (int i = 0; i < k; ++i)
-                for (int j = 0; j < k; ++j)
-                    cmx.push_back((uint8_t)(S.str_p[(size_t)sidx * MSD_KMAX + i] * S.nh +
-                                            S.str_h[(size_t)sidx * MSD_KMAX + j]));
-    if (cmx.empty()) cmx.push_back(0);
+                for (int j = 0; j < k; ++j) {
+                    const int p = S.str_p[(size_t)sidx * MSD_KMAX + i], h = S.str_h[(size_t)sidx * MSD_KMAX + j];
+                    cmx.push_back((uint8_t)(p * S.nh + h));
+                    kx.push_back((uint8_t)(h * S.np + p));
+                }
+    if (cmx.empty()) { cmx.push_back(0); kx.push_back(0); }
     if ((rc = upload(ctx, &S.d_cmx, cmx))) return rc;
+    if ((rc = upload(ctx, &S.d_kx, kx))) return rc;
+    std::vector<float> cf(S.csr_c.begin(), S.csr_c.end());
+    if (cf.empty()) cf.push_back(0.f);
+    if ((rc = upload(ctx, &S.d_csr_cf, cf))) return rc;
     return MSD_OK;
 }
 
@@ -396,8 +410,10 @@ void free_spin(SpinHost& S)
     cudaFree(S.d_occ0); cudaFree(S.d_hole_pos); cudaFree(S.d_part_orb); cudaFree(S.d_str_h);
     cudaFree(S.d_str_p); cudaFree(S.d_str_sign); cudaFree(S.d_csr_off); cudaFree(S.d_csr_other);
     cudaFree(S.d_csr_c); cudaFree(S.d_Lh); cudaFree(S.d_pos0);
-    cudaFree(S.d_cmx);
+    cudaFree(S.d_cmx); cudaFree(S.d_kx); cudaFree(S.d_csr_cf);
     S.d_cmx = nullptr;
+    S.d_kx = nullptr;
+    S.d_csr_cf = nullptr;
     S.d_pos0 = nullptr;
     S.d_occ0 = S.d_hole_pos = S.d_part_orb = nullptr;
     S.d_str_h = S.d_str_p = nullptr;
@@ -640,6 +656,7 @@ int finish(msd_ctx* ctx, cudaStream_t st, std::initializer_list<Out*> outs, bool
 // Per-chunk workspace for the overlap part.
 struct Chunk {
     double2 *Gr[2], *O0[2], *Gact[2], *r[2], *wts[2], *part;
+    float2* rf[2];   // FP32 copies of r (mixed mode, with B)
     void* B[2];
     int nslot, nR;
 };
@@ -650,7 +667,7 @@ size_t overlap_bytes_per_walker(msd_ctx* ctx, bool want_b, int nslot)
     for (int s = 0; s < 2; ++s) {
         const SpinHost& S = ctx->sp[s];
         b += (size_t)S.N * ctx->M + 1 + (size_t)S.nh * S.np + 2 * (size_t)S.n_str;
-        if (want_b) b += S.b_per_walker;
+        if (want_b) b += S.b_per_walker + (S.n_str + 1) / 2;
     }
     b += nslot;
     return b * sizeof(double2);
@@ -661,7 +678,7 @@ int chunk_alloc(msd_ctx* ctx, int cap, bool want_b, int nslot, Chunk& c)
     int rc;
     static const char* nGr[2] = {"Gr_a", "Gr_b"}, *nO0[2] = {"O0_a", "O0_b"};
     static const char* nGa[2] = {"Gact_a", "Gact_b"}, *nr[2] = {"r_a", "r_b"};
-    static const char* nw[2] = {"wts_a", "wts_b"}, *nB[2] = {"B_a", "B_b"};
+    static const char* nw[2] = {"wts_a", "wts_b"}, *nB[2] = {"B_a", "B_b"}, *nrf[2] = {"rf_a", "rf_b"};
     for (int s = 0; s < 2; ++s) {
         const SpinHost& S = ctx->sp[s];
         void* p;
@@ -671,9 +688,12 @@ int chunk_alloc(msd_ctx* ctx, int cap, bool want_b, int nslot, Chunk& c)
         if ((rc = arena_get(ctx, nr[s], sizeof(double2) * cap * S.n_str, &p))) return rc; c.r[s] = (double2*)p;
         if ((rc = arena_get(ctx, nw[s], sizeof(double2) * cap * S.n_str, &p))) return rc; c.wts[s] = (double2*)p;
         c.B[s] = nullptr;
+        c.rf[s] = nullptr;
         if (want_b) {
             if ((rc = arena_get(ctx, nB[s], sizeof(double2) * std::max<long long>(1, cap * S.b_per_walker), &p))) return rc;
             c.B[s] = p;
+            if ((rc = arena_get(ctx, nrf[s], sizeof(float2) * cap * S.n_str, &p))) return rc;
+            c.rf[s] = (float2*)p;
         }
     }
     void* p;
@@ -699,7 +719,7 @@ int run_overlap_part(msd_ctx* ctx, const Staged& in, int w0, int nw, int cap, Ch
         CKLAUNCH();
     }
     for (int s = 0; s < 2; ++s) {
-        launch_strings(T[s], nw, c.Gact[s], c.r[s], c.B[s], fp32_b, want_b, st, th);
+        launch_strings(T[s], nw, c.Gact[s], c.r[s], fp32_b ? c.rf[s] : nullptr, c.B[s], fp32_b, want_b, st, th);
         CKLAUNCH();
     }
     th.begin("k_weights", st);
@@ -823,10 +843,18 @@ bool fused(const msd_ctx* ctx, int s) { return ctx->fuse && ctx->fused_ok[s]; }
 // Rows of the split A operand per walker: 2N, or the fused kernel's padded RW.
 int a_rows(const msd_ctx* ctx, int s) { return fused(ctx, s) ? ctx->fplan[s].RW : 2 * ctx->sp[s].N; }
 
+// The opposite-spin term takes the per-beta-string form (k_pair_y).
+bool use_pair_y(const msd_ctx* ctx)
+{
+    const bool want = ctx->pair_form < 0 ? ctx->pair_y_auto : ctx->pair_form != 0;
+    return ctx->prec == MSD_MIXED && want && pair_y_ok(tables(ctx->sp[0], 1), tables(ctx->sp[1], 1));
+}
+
 int energy_slots(msd_ctx* ctx)
 {
-    return string_energy_slots(tables(ctx->sp[0], 1)) + string_energy_slots(tables(ctx->sp[1], 1)) +
-           pair_cross_slots(pair_tables(ctx->pairs));
+    const SpinTables ta = tables(ctx->sp[0], 1), tb = tables(ctx->sp[1], 1);
+    return string_energy_slots(ta) + string_energy_slots(tb) +
+           (use_pair_y(ctx) ? pair_y_slots(tb) : pair_cross_slots(pair_tables(ctx->pairs)));
 }
 
 size_t en_bytes_per_walker(msd_ctx* ctx, bool fp32)
@@ -981,9 +1009,14 @@ int en_chunk(msd_ctx* ctx, Chunk& c, EnWork& E, int w0, int nw, int cap, bool fp
     }
     th.end(st);
     CKLAUNCH();
-    th.begin("k_pair_cross", st);
-    launch_pair_cross(T[0], T[1], pair_tables(ctx->pairs), nw, c.r[0], c.r[1], c.B[0], c.B[1], E.Kab, fp32, c.part,
-                      c.nslot, slot, st);
+    if (use_pair_y(ctx)) {
+        th.begin("k_pair_y", st);
+        launch_pair_y(T[0], T[1], nw, c.rf[0], c.rf[1], c.B[0], c.B[1], E.Kab, c.part, c.nslot, slot, st);
+    } else {
+        th.begin("k_pair_cross", st);
+        launch_pair_cross(T[0], T[1], pair_tables(ctx->pairs), nw, c.r[0], c.r[1], c.B[0], c.B[1], E.Kab, fp32,
+                          c.part, c.nslot, slot, st);
+    }
     th.end(st);
     CKLAUNCH();
     th.begin("k_final", st);
@@ -1341,6 +1374,27 @@ int msd_set_trial(msd_ctx* ctx, int n_det, const double* coeff, const int32_t* o
         int rc = upload_spin(ctx, S);
         if (rc) return rc;
     }
+    // cost model for the two forms of the opposite-spin term (per walker;
+    // unit costs measured on GB300 with the iron-sulfur-shaped 1.2e5- and
+    // the copper-oxo-shaped 1e6-determinant trials): per beta string
+    // ~1.0 per (entry x 32-lane x slot) of Y_b plus ~3.7 per alpha entry of
+    // each determinant, per determinant ~1.1 per k_a^2 k_b^2 gather
+    {
+        const SpinHost& Sa = ctx->sp[0];
+        const SpinHost& Sb = ctx->sp[1];
+        const double xpp = 32.0 * ((Sa.nh * Sa.np + 31) / 32) + 1.0;
+        double cost_y = 0.0, cost_d = 0.0;
+        for (int k = 1; k <= MSD_KMAX; ++k) cost_y += xpp * k * k * (Sb.bucket[k + 1] - Sb.bucket[k]);
+        for (int I = 0; I < n_det; ++I) {
+            const double ka = lv(0, I), kb = lv(1, I);
+            if (ka > 0 && kb > 0) {
+                cost_y += 3.7 * ka * ka;
+                cost_d += 1.1 * ka * ka * kb * kb;
+            }
+        }
+        ctx->pair_y_auto = cost_y < cost_d;
+        ctx->chunk = 0;
+    }
     int rc;
     if ((rc = upload(ctx, &P.d_a, P.a))) return rc;
     if ((rc = upload(ctx, &P.d_b, P.b))) return rc;
@@ -1588,6 +1642,18 @@ int msd_set_sync(msd_ctx* ctx, int sync)
     return MSD_OK;
 }
 
+int msd_set_pair_form(msd_ctx* ctx, int form)
+{
+    if (!ctx) return MSD_ERR_ARG;
+    if (form < -1 || form > 1) return fail(ctx, MSD_ERR_ARG, "pair form must be -1 (auto), 0 or 1");
+    if (ctx->pair_form != form) {
+        ctx->pair_form = form;
+        ctx->chunk = 0;   // the partial-sum slots per walker may change
+        ++ctx->gen;
+    }
+    return MSD_OK;
+}
+
 int msd_set_fused(msd_ctx* ctx, int fused)
 {
     if (!ctx) return MSD_ERR_ARG;
@@ -1700,8 +1766,8 @@ extern "C" int msd_overlap_noalloc(msd_ctx* ctx, int n_w, const double* phi_a, c
         SpinTables T[2] = {tables(ctx->sp[0], cap), tables(ctx->sp[1], cap)};
         launch_ref(pa + (size_t)w0 * M * ctx->n[0], nw, M, ctx->n[0], T[0], Gr[0], O0[0], Gact[0], ctx->d_err, st);
         launch_ref(pb + (size_t)w0 * M * ctx->n[1], nw, M, ctx->n[1], T[1], Gr[1], O0[1], Gact[1], ctx->d_err, st);
-        launch_strings(T[0], nw, Gact[0], r[0], nullptr, false, false, st, none);
-        launch_strings(T[1], nw, Gact[1], r[1], nullptr, false, false, st, none);
+        launch_strings(T[0], nw, Gact[0], r[0], nullptr, nullptr, false, false, st, none);
+        launch_strings(T[1], nw, Gact[1], r[1], nullptr, nullptr, false, false, st, none);
         launch_weights(T[0], nw, r[0], r[1], T[1].n_str, wts, part, nR, 0, st);
         launch_sum_slots(nw, part, nR, 0, nR, ratio_sum ? (double2*)ratio_sum + w0 : nullptr, O0[0], O0[1],
                          ovlp ? (double2*)ovlp + w0 : nullptr, st);
@@ -1972,6 +2038,10 @@ int msd_batch_create(msd_batch** out, msd_ctx* const* ctxs, int n_sys)
         }
         b->ctx.push_back(ctxs[i]);
     }
+    // the persistent per-determinant kernel implements the per-determinant
+    // opposite-spin form; the systems' own evaluations use the same form, so
+    // batched and per-system results agree
+    for (int i = 0; i < n_sys; ++i) msd_set_pair_form(ctxs[i], 0);
     b->device = ctxs[0]->device;
     b->fp32 = ctxs[0]->prec == MSD_MIXED;
     cudaSetDevice(b->device);

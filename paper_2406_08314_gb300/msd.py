@@ -22,7 +22,7 @@ _ERRORS = {-1: "MSD_ERR_ARG", -2: "MSD_ERR_SHAPE", -3: "MSD_ERR_CUDA", -4: "MSD_
 EXPORTS = ["msd_create", "msd_destroy", "msd_last_error", "msd_set_hamiltonian", "msd_set_trial",
            "msd_set_precision", "msd_overlap", "msd_det_ratios", "msd_force_bias",
            "msd_local_energy", "msd_evaluate", "msd_info", "msd_set_timing", "msd_reset_stats",
-           "msd_kernel_count", "msd_kernel_stat", "msd_set_workspace_limit", "msd_set_sync", "msd_set_fused", "msd_propagate",
+           "msd_kernel_count", "msd_kernel_stat", "msd_set_workspace_limit", "msd_set_sync", "msd_set_fused", "msd_set_pair_form", "msd_propagate",
            "msd_launch_count", "msd_overlap_noalloc", "msd_batch_create", "msd_batch_destroy",
            "msd_batch_last_error", "msd_batch_evaluate", "msd_batch_autotune", "msd_batch_config",
            "msd_batch_set_config", "msd_batch_graph_ready", "msd_batch_graph_kernels", "msd_features", "msd_features_rows",
@@ -67,6 +67,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.msd_set_workspace_limit.argtypes = [vp, ctypes.c_size_t]
     lib.msd_set_sync.argtypes = [vp, ci]
     lib.msd_set_fused.argtypes = [vp, ci]
+    lib.msd_set_pair_form.argtypes = [vp, ci]
     lib.msd_propagate.argtypes = [vp, ci, vp, vp, vp, vp, ctypes.c_double, ci, ci, vp, vp]
     lib.msd_launch_count.argtypes = []
     for f in EXPORTS:
@@ -328,6 +329,13 @@ class Context:
         """Mixed precision: fused tensor-core contraction + epilogue (default)
         or the separate GEMM and epilogue kernels."""
         self._check(_lib.msd_set_fused(self._h, int(bool(fused))))
+
+    def set_pair_form(self, form):
+        """Mixed precision: opposite-spin energy term formed per beta string
+        (True / 1), per determinant (False / 0) or chosen per trial by the
+        library's cost model ("auto" / -1, the default); msd_set_pair_form."""
+        f = -1 if form == "auto" else int(form)
+        self._check(_lib.msd_set_pair_form(self._h, f))
 
 
 class Batch:

@@ -96,8 +96,13 @@ def test_1e6_mixed_against_fp64(msd, big):
     out = {}
     for prec in ("fp64", "mixed"):
         ctx = msd.Context(s, prec)
+        ctx.set_timing(True)
         e, o = ctx.local_energy(da, db, ovlp=True)
         out[prec] = (_np(e), _np(o), _np(ctx.force_bias(da, db)))
+        if prec == "mixed":
+            # ~80 determinants per beta string: the cost model takes the
+            # opposite-spin term per beta string
+            assert "k_pair_y" in ctx.kernel_stats() and "k_pair_cross" not in ctx.kernel_stats()
         ctx.close()
     (e64, o64, v64), (em, om, vm) = out["fp64"], out["mixed"]
     assert np.all(np.abs(em - e64) <= 1e-6), np.abs(em - e64).max()

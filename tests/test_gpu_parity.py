@@ -201,6 +201,11 @@ def test_edge_cases(msd):
     with pytest.raises(msd.MSDError) as ei:
         ctx.local_energy(_cuda(pa), _cuda(w.phi_b[:2]))
     assert ei.value.name == "MSD_ERR_REF_SINGULAR"
+    # opposite-spin form: -1, 0 or 1
+    with pytest.raises(msd.MSDError) as ei:
+        ctx.set_pair_form(2)
+    assert ei.value.name == "MSD_ERR_ARG"
+    ctx.set_pair_form("auto")
     # unsorted occupations
     bad = s.occ_a.copy()
     bad[3] = bad[3][::-1]
@@ -247,9 +252,10 @@ def test_walker_chunking_matches(msd):
 MIX_E_REL, MIX_E_ABS, MIX_V = 2e-6, 1e-6, 1e-4
 
 
-def _check_mixed(m, sys_, pa, pb, ref, fused=True):
+def _check_mixed(m, sys_, pa, pb, ref, fused=True, per_beta=True):
     ctx = m.Context(sys_, "mixed")
     ctx.set_fused(fused)
+    ctx.set_pair_form(per_beta)
     da, db = _cuda(pa), _cuda(pb)
     e, o = ctx.local_energy(da, db, ovlp=True)
     e, o = _np(e), _np(o)
@@ -268,41 +274,70 @@ def _check_mixed(m, sys_, pa, pb, ref, fused=True):
 
 # fused: the energy's Cholesky contraction and its epilogue in one
 # persistent tensor-core kernel (default); unfused: GEMM + epilogue kernel.
-FUSED = pytest.mark.parametrize("fused", [True, False], ids=["fused", "unfused"])
+# pairY: the opposite-spin term formed per beta string (default); perdet:
+# the double sum per determinant.
+FUSED = pytest.mark.parametrize("fused,per_beta", [(True, True), (False, True), (True, False)],
+                                ids=["fused-pairY", "unfused-pairY", "fused-perdet"])
 
 
 @FUSED
-def test_small_workload_mixed(msd, fused):
+def test_small_workload_mixed(msd, fused, per_beta):
     s, w = synth.config_system("small", seed=0)
-    _check_mixed(msd, s, w.phi_a, w.phi_b, _ref(s, w.phi_a, w.phi_b), fused)
+    _check_mixed(msd, s, w.phi_a, w.phi_b, _ref(s, w.phi_a, w.phi_b), fused, per_beta)
 
 
 @FUSED
 @pytest.mark.parametrize("M,na,nb,n_det,max_level,seed", [(12, 5, 4, 150, 4, 0), (13, 7, 6, 300, 12, 1)])
-def test_tiny_systems_mixed(msd, M, na, nb, n_det, max_level, seed, fused):
+def test_tiny_systems_mixed(msd, M, na, nb, n_det, max_level, seed, fused, per_beta):
     s = tiny_system(seed, M, na, nb, n_chol=7, n_det=n_det, max_level=max_level)
     pa, pb = tiny_walkers(seed, M, na, nb, n_w=3, noise=0.3)
     # scale to the synthetic workloads' energy range (the bound is absolute in Ha)
     s.L = s.L * 0.05
     s.h1 = s.h1 * 0.05
     s, pa, pb = _relabel(s, pa, pb, seed)
-    _check_mixed(msd, s, pa, pb, _ref(s, pa, pb), fused)
+    _check_mixed(msd, s, pa, pb, _ref(s, pa, pb), fused, per_beta)
 
 
 @FUSED
-def test_cu2o2_shaped_mixed(msd, fused):
+def test_cu2o2_shaped_mixed(msd, fused, per_beta):
     s, w = synth.config_system("cu2o2", seed=0, n_w=2)
-    _check_mixed(msd, s, w.phi_a, w.phi_b, _ref(s, w.phi_a, w.phi_b), fused)
+    _check_mixed(msd, s, w.phi_a, w.phi_b, _ref(s, w.phi_a, w.phi_b), fused, per_beta)
 
 
 @FUSED
-def test_fe2s2_shaped_subset_mixed(msd, fe2s2, fused):
+def test_fe2s2_shaped_subset_mixed(msd, fe2s2, fused, per_beta):
     s, w = fe2s2
     idx = np.concatenate([[0], np.sort(np.random.default_rng(6).choice(
         np.arange(1, s.n_det), 299, replace=False))])
     t = _subtrial(s, idx)
     pa, pb = w.phi_a[:2], w.phi_b[:2]
-    _check_mixed(msd, t, pa, pb, _ref(t, pa, pb), fused)
+    _check_mixed(msd, t, pa, pb, _ref(t, pa, pb), fused, per_beta)
+
+
+@pytest.mark.parametrize("spin", [0, 1])
+def test_one_spin_excitations_mixed(msd, spin):
+    """Trial whose excited determinants all keep one spin's reference string:
+    the opposite-spin term has nothing to add (the per-beta-string kernel
+    still forms Y_b for the excited beta strings, then skips every
+    determinant, or has no excited beta string at all)."""
+    import copy
+    s, w = synth.config_system("small", seed=3)
+    # the trial's distinct strings of the other spin, each paired with this
+    # spin's reference string (the reference determinant first)
+    other = s.occ_b if spin == 0 else s.occ_a
+    _, first = np.unique(other, axis=0, return_index=True)
+    idx = np.sort(first)
+    assert idx[0] == 0 and len(idx) > 5
+    t = copy.copy(s)
+    t.coeff = np.ascontiguousarray(s.coeff[idx])
+    keep = (s.occ_a if spin == 0 else s.occ_b)[0]
+    fixed = np.ascontiguousarray(np.repeat(keep[None, :], len(idx), axis=0))
+    if spin == 0:
+        t.occ_a, t.occ_b = fixed, np.ascontiguousarray(s.occ_b[idx])
+    else:
+        t.occ_a, t.occ_b = np.ascontiguousarray(s.occ_a[idx]), fixed
+    pa, pb = w.phi_a[:4], w.phi_b[:4]
+    _check_mixed(msd, t, pa, pb, _ref(t, pa, pb))
 
 
 def test_fe2s2_full_size_mixed_vs_fp64(msd, fe2s2):
@@ -340,4 +375,28 @@ def test_fe2s2_full_size_fused_matches_unfused(msd, fe2s2):
     e1 = _np(ctx.local_energy(da, db))
     ctx.close()
     assert np.all(np.isfinite(e1))
+    assert np.all(np.abs(e1 - e0) <= 0.1 * MIX_E_ABS), np.abs(e1 - e0).max()
+
+
+def test_fe2s2_full_size_pair_forms_agree(msd, fe2s2):
+    """Full size, bench launch configuration: the opposite-spin term per beta
+    string against the per-determinant double sum. Both FP32 with FP64 slot
+    sums; only the order of the FP32 sums differs."""
+    s, w = fe2s2
+    da, db = _cuda(w.phi_a), _cuda(w.phi_b)
+    ctx = msd.Context(s, "mixed")
+    ctx.set_timing(True)
+    ea = _np(ctx.local_energy(da, db))
+    # ~10 determinants per beta string: the cost model keeps the
+    # per-determinant form
+    assert "k_pair_cross" in ctx.kernel_stats() and "k_pair_y" not in ctx.kernel_stats()
+    ctx.set_pair_form(False)
+    e0 = _np(ctx.local_energy(da, db))
+    assert np.array_equal(ea, e0)
+    ctx.set_pair_form(True)
+    e1 = _np(ctx.local_energy(da, db))
+    e2 = _np(ctx.local_energy(da, db))
+    ctx.close()
+    assert np.all(np.isfinite(e1))
+    assert np.array_equal(e1, e2)   # deterministic
     assert np.all(np.abs(e1 - e0) <= 0.1 * MIX_E_ABS), np.abs(e1 - e0).max()
