@@ -34,15 +34,19 @@
 #define PY_SPW (PY_CB / PY_WARPS)   // beta strings per warp in phase A
 #define PY_EMAX (MSD_KMAX * MSD_KMAX)
 #define PY_G 4            // lanes per determinant in phase B
+#define PY_NG (PY_THREADS / PY_G)   // lane groups
+#define PY_DPG (PY_THREADS / PY_NG) // staged determinants per group and tile
 
 static __host__ __device__ __forceinline__ int py_xq(int Xa) { return (Xa + 31) / 32; }
 
 // per staged determinant of phase B
-struct PyDet {
-    int sa;        // alpha string within its level
-    int ka;        // alpha level (0: skip)
-    int bl;        // beta string within the chunk
-    float wr, wi;  // c_I r_a r_b
+struct __align__(16) PyDet {
+    long long aoff;   // offset of its alpha inverse minor in Ba
+    int xoff;         // offset of its alpha entries in ta.kx
+    int kk;           // k_a^2 (0: nothing to add)
+    int yoff;         // offset of its beta string's row in Ys
+    float wr, wi;     // c_I r_a r_b
+    int pad;
 };
 
 // bytes of the staging area (phase A's entries or phase B's tile)
@@ -142,7 +146,7 @@ k_pair_y(SpinTables ta, SpinTables tbb, const float2* __restrict__ rfa, const fl
             {   // stage: thread t takes determinant tile + t
                 const int d = tile + t;
                 PyDet q;
-                q.ka = 0; q.sa = 0; q.bl = 0; q.wr = 0.f; q.wi = 0.f;
+                q.aoff = 0; q.xoff = 0; q.kk = 0; q.yoff = 0; q.wr = 0.f; q.wi = 0.f; q.pad = 0;
                 if (d < d1) {
                     const int a = tbb.csr_other[d];
                     if (a >= ta.bucket[1]) {
@@ -155,31 +159,48 @@ k_pair_y(SpinTables ta, SpinTables tbb, const float2* __restrict__ rfa, const fl
                         while (a >= ta.bucket[ka + 1]) ++ka;
                         const float2 wab = fmul(rfa[(size_t)w * ta.n_str + a], rbs[lo]);
                         const float c = tbb.csr_cf[d];
-                        q.ka = ka; q.sa = a - ta.bucket[ka]; q.bl = lo;
+                        const int nsa = ta.bucket[ka + 1] - ta.bucket[ka], sa = a - ta.bucket[ka];
+                        q.kk = ka * ka;
+                        q.aoff = ta.b_off[ka] + ((long long)w * nsa + sa) * q.kk;
+                        q.xoff = (int)ta.cmx_off[ka] + sa * q.kk;
+                        q.yoff = lo * XPP;
                         q.wr = c * wab.x; q.wi = c * wab.y;
                     }
                 }
                 dst[t] = q;
             }
             __syncthreads();
-            // process: group grp takes staged determinants grp, grp + PY_THREADS / PY_G, ...
+            // process: group grp takes the staged determinants grp + u PY_NG
+            // (u < PY_DPG) together, so their loads are in flight at once
             const int n_here = min(PY_THREADS, d1 - tile);
-            for (int j = grp; j < n_here; j += PY_THREADS / PY_G) {
-                const PyDet q = dst[j];
-                if (q.ka == 0) continue;
-                const int ka = q.ka, kk = ka * ka, nsa = ta.bucket[ka + 1] - ta.bucket[ka];
-                const float2* A = Ba + (size_t)ta.b_off[ka] + ((size_t)w * nsa + q.sa) * kk;
-                const uint8_t* xa = ta.kx + ta.cmx_off[ka] + (size_t)q.sa * kk;
-                const float2* yrow = Ys + q.bl * XPP;
-                float xr = 0.f, xi = 0.f;
-#pragma unroll 3
-                for (int e = l; e < kk; e += PY_G) {
-                    const float2 bv = A[e], yv = yrow[xa[e]];
-                    xr = fmaf(bv.x, yv.x, fmaf(-bv.y, yv.y, xr));
-                    xi = fmaf(bv.x, yv.y, fmaf(bv.y, yv.x, xi));
+            PyDet q[PY_DPG];
+            int kmax = 0;
+#pragma unroll
+            for (int u = 0; u < PY_DPG; ++u) {
+                const int j = grp + u * PY_NG;
+                if (j < n_here) {
+                    q[u] = dst[j];
+                } else {
+                    q[u].aoff = 0; q[u].xoff = 0; q[u].kk = 0; q[u].yoff = 0; q[u].wr = 0.f; q[u].wi = 0.f;
                 }
-                vr_sum = fmaf(q.wr, xr, fmaf(-q.wi, xi, vr_sum));
-                vi_sum = fmaf(q.wr, xi, fmaf(q.wi, xr, vi_sum));
+                kmax = max(kmax, q[u].kk);
+            }
+            float xr[PY_DPG], xi[PY_DPG];
+#pragma unroll
+            for (int u = 0; u < PY_DPG; ++u) { xr[u] = 0.f; xi[u] = 0.f; }
+            for (int e = l; e < kmax; e += PY_G) {
+#pragma unroll
+                for (int u = 0; u < PY_DPG; ++u)
+                    if (e < q[u].kk) {
+                        const float2 bv = Ba[q[u].aoff + e], yv = Ys[q[u].yoff + ta.kx[q[u].xoff + e]];
+                        xr[u] = fmaf(bv.x, yv.x, fmaf(-bv.y, yv.y, xr[u]));
+                        xi[u] = fmaf(bv.x, yv.y, fmaf(bv.y, yv.x, xi[u]));
+                    }
+            }
+#pragma unroll
+            for (int u = 0; u < PY_DPG; ++u) {
+                vr_sum = fmaf(q[u].wr, xr[u], fmaf(-q[u].wi, xi[u], vr_sum));
+                vi_sum = fmaf(q[u].wr, xi[u], fmaf(q[u].wi, xr[u], vi_sum));
             }
             __syncthreads();   // the tile is consumed
         }
