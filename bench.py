@@ -51,6 +51,11 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    # library options (alternative implementations of the same step)
+    p.add_argument("--no-fused", action="store_true",
+                   help="mixed: tensor-core GEMM + separate epilogue instead of the fused kernel")
+    p.add_argument("--pair-form", default="auto", choices=["auto", "0", "1"],
+                   help="mixed: opposite-spin term per determinant (0), per beta string (1) or chosen by the cost model")
     return p.parse_args()
 
 
@@ -282,6 +287,8 @@ def run_ours(args, rank, world, local):
     stream = torch.cuda.current_stream(dev)
     ctx = msd.Context(s, args.precision, device=local)
     ctx.set_sync(False)
+    ctx.set_fused(not args.no_fused)
+    ctx.set_pair_form(args.pair_form)
     vb = torch.empty((n_w, s.n_chol), dtype=torch.complex128, device=dev)
     el = torch.empty((n_w,), dtype=torch.complex128, device=dev)
     ov = torch.empty((n_w,), dtype=torch.complex128, device=dev)
@@ -409,10 +416,13 @@ def run_ours(args, rank, world, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64 minors + f32 contractions" if args.precision == "mixed" else "f64",
-            "data": "synthetic (seeded; shapes of the paper's Fe2S2 system)",
+            "data": "synthetic (seeded; shapes of the paper's "
+                    + ("Fe2S2" if args.workload.startswith("fe2s2") else "Cu2O2") + " system)",
             "config": {"workload": f"{args.workload}: M={s.M}, {s.n_alpha}+{s.n_beta} e, "
                                    f"N_det={n_det}, N_chol={s.n_chol}, {n_w} walkers/GPU",
                        "precision": args.precision, "n_walkers": n_w, "n_det": n_det,
+                       "fused": args.precision == "mixed" and not args.no_fused,
+                       "opposite_spin_form": ("per beta string" if "k_pair_y" in kernels else "per determinant"),
                        "n_chol": s.n_chol, "M": s.M,
                        "step": "msd_evaluate: overlap + force bias + local energy",
                        "l2": "flushed between timed steps (256 MiB write)",
