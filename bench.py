@@ -238,13 +238,21 @@ FP64_KERNELS = {"k_ref", "k_strings", "k_weights", "k_gt", "k_onebody", "k_final
 # kernel, from a one-pass ncu --metrics capture of this bench's default
 # workload; reported only while the kernel's source file still hashes to
 # the value recorded with the capture (a changed kernel gets null).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/k_tc_fepi_fe2s2_640w_dram.md (640 walkers, one spin per launch)
+    "tc_fepi": {"source": "paper_2406_08314_gb300/csrc/tc_fepi.cu",
+                "sha256": "e6260de6680423bd15b5e69e68cb85ded7cc48caef815774db20a0af2c5a612d",
+                "bytes_per_launch": 553659136 + 614598144, "workload": "fe2s2", "n_w": 640},
+}
 
 
-def ncu_traffic(name):
+def ncu_traffic(name, workload=None, n_w=None):
+    """DRAM bytes per launch of a kernel from its recorded capture, for the
+    captured workload and walker count only, while the kernel's source is
+    unchanged; None otherwise."""
     import hashlib
     t = NCU_TRAFFIC.get(name)
-    if not t:
+    if not t or t.get("workload") != workload or t.get("n_w") != n_w:
         return None
     try:
         with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), t["source"]), "rb") as f:
@@ -404,7 +412,7 @@ def run_ours(args, rank, world, local):
         b, pk, src = kernel_peak(dom, args.precision, peaks)
         ach = d.get("gflops")
         roofline = {"kernel": dom, "bound": b, "achieved": ach, "peak": pk, "unit": "GFLOP/s",
-                    "frac": (ach / pk) if ach else None, "traffic": ncu_traffic(dom), "peak_source": src}
+                    "frac": (ach / pk) if ach else None, "traffic": ncu_traffic(dom, args.workload, n_w), "peak_source": src}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -804,7 +812,7 @@ def run_prop(args, rank, world, local):
     if dom is not None:
         d = kernels[dom]
         roofline = {"kernel": dom, "bound": "alu", "achieved": d.get("gflops"), "peak": FP64_ALU_GFLOPS,
-                    "unit": "GFLOP/s", "frac": d.get("frac"), "traffic": ncu_traffic(dom),
+                    "unit": "GFLOP/s", "frac": d.get("frac"), "traffic": ncu_traffic(dom, "propagate"),
                     "peak_source": "derived: 152 SMs x 2070 MHz x 2 FP64 FMA/clk/SM"}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
