@@ -480,12 +480,12 @@ __device__ __forceinline__ void cmat_level(T* __restrict__ a, int g, int ng, int
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256)
-k_cmat(SpinTables tb, const double2* __restrict__ wts, const void* __restrict__ Bin, double2* __restrict__ Cm)
+__device__ __forceinline__ void cmat_walker(const SpinTables& tb, int w, const double2* __restrict__ wts,
+                                            const void* __restrict__ Bin, double2* __restrict__ Cm, T* accp)
 {
-    __shared__ T acc[CMAT_COPIES][2 * MSD_XMAX];
-    const int w = blockIdx.x, X = tb.nh * tb.np;
-    for (int e = threadIdx.x; e < CMAT_COPIES * 2 * MSD_XMAX; e += blockDim.x) (&acc[0][0])[e] = 0;
+    T (*acc)[2 * MSD_XMAX] = reinterpret_cast<T (*)[2 * MSD_XMAX]>(accp);
+    const int X = tb.nh * tb.np;
+    for (int e = threadIdx.x; e < CMAT_COPIES * 2 * MSD_XMAX; e += blockDim.x) accp[e] = 0;
     __syncthreads();
     const T* Bb = reinterpret_cast<const T*>(Bin);
     const double2* ww = wts + (size_t)w * tb.n_str;
@@ -495,12 +495,13 @@ k_cmat(SpinTables tb, const double2* __restrict__ wts, const void* __restrict__ 
         const T* B = Bb + 2 * ((size_t)tb.b_off[k] + (size_t)w * ns * kk);
         const uint8_t* xt = tb.cmx + tb.cmx_off[k];
         if (kk <= 16)
-            cmat_level<T, 16, 1, 4>(acc[threadIdx.x >> 4], threadIdx.x >> 4, 16, threadIdx.x & 15, kk, ns, s0, B, xt, ww);
+            cmat_level<T, 16, 1, 3>(acc[threadIdx.x >> 4], threadIdx.x >> 4, 16, threadIdx.x & 15, kk, ns, s0, B, xt,
+                                    ww);
         else if (kk <= 32)
-            cmat_level<T, 32, 1, 4>(acc[(threadIdx.x >> 5) * 2], threadIdx.x >> 5, 8, threadIdx.x & 31, kk, ns, s0, B,
+            cmat_level<T, 32, 1, 3>(acc[(threadIdx.x >> 5) * 2], threadIdx.x >> 5, 8, threadIdx.x & 31, kk, ns, s0, B,
                                     xt, ww);
         else
-            cmat_level<T, 32, 2, 4>(acc[(threadIdx.x >> 5) * 2], threadIdx.x >> 5, 8, threadIdx.x & 31, kk, ns, s0, B,
+            cmat_level<T, 32, 2, 3>(acc[(threadIdx.x >> 5) * 2], threadIdx.x >> 5, 8, threadIdx.x & 31, kk, ns, s0, B,
                                     xt, ww);
     }
     __syncthreads();
@@ -511,12 +512,29 @@ k_cmat(SpinTables tb, const double2* __restrict__ wts, const void* __restrict__ 
     }
 }
 
-void launch_cmat(const SpinTables& tb, int nw, const double2* wts, const void* B, bool fp32, double2* Cm,
-                 cudaStream_t st)
+// Both spins in one grid (blockIdx.y = spin), so the two spins' blocks fill
+// the machine together.
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3)
+k_cmat(SpinTables ta, SpinTables tb, const double2* __restrict__ wts_a, const double2* __restrict__ wts_b,
+       const void* __restrict__ Ba, const void* __restrict__ Bb, double2* __restrict__ Cm_a,
+       double2* __restrict__ Cm_b)
 {
-    if (tb.nh * tb.np <= 0) return;
-    if (fp32) k_cmat<float><<<nw, 256, 0, st>>>(tb, wts, B, Cm);
-    else k_cmat<double><<<nw, 256, 0, st>>>(tb, wts, B, Cm);
+    __shared__ T acc[CMAT_COPIES][2 * MSD_XMAX];
+    if (blockIdx.y == 0) {
+        if (ta.nh * ta.np > 0) cmat_walker<T>(ta, blockIdx.x, wts_a, Ba, Cm_a, &acc[0][0]);
+    } else {
+        if (tb.nh * tb.np > 0) cmat_walker<T>(tb, blockIdx.x, wts_b, Bb, Cm_b, &acc[0][0]);
+    }
+}
+
+void launch_cmat(const SpinTables& ta, const SpinTables& tb, int nw, const double2* wts_a, const double2* wts_b,
+                 const void* Ba, const void* Bb, bool fp32, double2* Cm_a, double2* Cm_b, cudaStream_t st)
+{
+    if (ta.nh * ta.np <= 0 && tb.nh * tb.np <= 0) return;
+    const dim3 grid(nw, 2);
+    if (fp32) k_cmat<float><<<grid, 256, 0, st>>>(ta, tb, wts_a, wts_b, Ba, Bb, Cm_a, Cm_b);
+    else k_cmat<double><<<grid, 256, 0, st>>>(ta, tb, wts_a, wts_b, Ba, Bb, Cm_a, Cm_b);
     msd_note_launch();
 }
 

@@ -25,8 +25,8 @@ void launch_det_ratios(const PairTables& pt, int nw, int n_str_a, int n_str_b, c
 void launch_sum_slots(int nw, const double2* part, int nslot, int slot0, int n, double2* out,
                       const double2* O0a, const double2* O0b, double2* ovlp, cudaStream_t st);
 void launch_ref_ovlp(int nw, const double2* O0a, const double2* O0b, double2* out, cudaStream_t st);
-void launch_cmat(const SpinTables& tb, int nw, const double2* wts, const void* B, bool fp32, double2* Cm,
-                 cudaStream_t st);
+void launch_cmat(const SpinTables& ta, const SpinTables& tb, int nw, const double2* wts_a, const double2* wts_b,
+                 const void* Ba, const void* Bb, bool fp32, double2* Cm_a, double2* Cm_b, cudaStream_t st);
 void launch_gt(const SpinTables& tb, int nw, int M, const double2* Gr, const double2* Cm,
                const double2* R, double2* GT, long long ld, long long off, bool minus_ref, cudaStream_t st);
 

@@ -790,11 +790,12 @@ int fb_chunk(msd_ctx* ctx, Chunk& c, FbWork& f, int w0, int nw, int cap, bool fp
                      ov_out ? ov_out + w0 : nullptr, st);
     th.end(st);
     long long off = 0;
+    th.begin("k_cmat", st);
+    launch_cmat(tables(ctx->sp[0], cap), tables(ctx->sp[1], cap), nw, c.wts[0], c.wts[1], c.B[0], c.B[1], fp32,
+                (double2*)f.Cm[0], (double2*)f.Cm[1], st);
+    th.end(st);
     for (int s = 0; s < 2; ++s) {
         const SpinTables T = tables(ctx->sp[s], cap);
-        th.begin("k_cmat", st);
-        launch_cmat(T, nw, c.wts[s], c.B[s], fp32, (double2*)f.Cm[s], st);
-        th.end(st);
         th.begin("k_gt", st);
         launch_gt(T, nw, ctx->M, c.Gr[s], (double2*)f.Cm[s], (double2*)f.Rs, (double2*)f.GT, ctx->Kd, off, fp32,
                   st);
