@@ -70,6 +70,7 @@ struct SpinTables {
     int n_str;          // distinct excitation strings, reference string first
     int bucket[MSD_KMAX + 2];   // strings of level k: [bucket[k], bucket[k+1])
     const int* occ0;    // [N]
+    const int* pos0;    // [M] position of an orbital in occ0, or -1
     const int* hole_pos;   // [nh] position in occ0 of each hole orbital
     const int* part_orb;   // [np] orbital of each particle
     const uint8_t* str_h;  // [n_str][KMAX] hole indices (0..nh-1), ascending

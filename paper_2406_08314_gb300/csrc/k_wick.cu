@@ -12,12 +12,15 @@
 // (Sec. II A overlap of two determinants). LU with partial pivoting in
 // FP64 gives O0 = det S and S^-1; then
 //   Gr[j][r]  = (phi S^-1)[r][j] = G[occ0_j][r]   (G = G0^T, G0 = Theta D0^dag)
+//               (rows r in occ0 of phi are S itself, so there Gr is exactly
+//               the identity and is written, not computed)
 //   Gact[h][p] = G[H_h][P_p]                       (active hole x particle block)
 // One block per walker. A walker whose |det S| falls below 1e-14 times the
 // product of the column norms of S is flagged singular.
 __global__ void __launch_bounds__(256)
 k_ref(const double2* __restrict__ phi, int M, int N, const int* __restrict__ occ0,
-      const int* __restrict__ hole_pos, int nh, const int* __restrict__ part_orb, int np,
+      const int* __restrict__ pos0, const int* __restrict__ hole_pos, int nh, const int* __restrict__ part_orb,
+      int np,
       double2* __restrict__ Gr, double2* __restrict__ O0, double2* __restrict__ Gact,
       unsigned* err)
 {
@@ -101,12 +104,21 @@ k_ref(const double2* __restrict__ phi, int M, int N, const int* __restrict__ occ
     }
     __syncthreads();
     double2* gr = Gr + (size_t)w * N * M;
-    for (int e = t; e < N * M; e += nt) {
-        const int j = e / M, r = e % M;
+    // lanes over the columns j (S^-1 row reads contiguous, the phi element a
+    // broadcast), warps over the rows r
+    const int JW = N <= 32 ? 32 : 64;
+    for (int e = t; e < M * JW; e += nt) {
+        const int r = e / JW, j = e - r * JW;
+        if (j >= N) continue;
+        const int q = pos0[r];
+        if (q >= 0) {
+            gr[(size_t)j * M + r] = cz(q == j ? 1.0 : 0.0, 0.0);
+            continue;
+        }
         const double2* pr = ph + (size_t)r * N;
         double2 a = cz(0, 0);
         for (int k = 0; k < N; ++k) a = cfma(pr[k], Si[k * N + j], a);
-        gr[e] = a;
+        gr[(size_t)j * M + r] = a;
     }
     for (int e = t; e < nh * np; e += nt) {
         const int h = e / np, p = e % np;
@@ -123,7 +135,7 @@ void launch_ref(const double2* phi, int nw, int M, int N, const SpinTables& T, d
 {
     size_t smem = sizeof(double2) * 2 * N * N;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_ref, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_ref<<<nw, 256, smem, st>>>(phi, M, N, T.occ0, T.hole_pos, T.nh, T.part_orb, T.np, Gr, O0,
+    k_ref<<<nw, 256, smem, st>>>(phi, M, N, T.occ0, T.pos0, T.hole_pos, T.nh, T.part_orb, T.np, Gr, O0,
                                  Gact, err); msd_note_launch();
 }
 
@@ -548,22 +560,23 @@ void launch_cmat(const SpinTables& ta, const SpinTables& tb, int nw, const doubl
 // row of length ld (both spins are concatenated per walker). With
 // minus_ref the reference part D0 D0^T (ones at (occ0_l, occ0_l)) is
 // subtracted, for the mixed path that adds its contraction in FP64.
+#define GT_COLS 16   // output columns per block
 __global__ void __launch_bounds__(256)
 k_gt(SpinTables tb, int M, const double2* __restrict__ Gr, const double2* __restrict__ Cm,
      const double2* __restrict__ Rsum, double2* __restrict__ GT, long long ld, long long off, int minus_ref)
 {
     __shared__ double2 cm[MSD_XMAX];
-    __shared__ double2 y[MSD_XMAX * 8];   // [np][8 columns]
+    __shared__ double2 y[MSD_XMAX * GT_COLS];   // [np][GT_COLS columns]
     const int w = blockIdx.y;
-    const int c0 = blockIdx.x * 8;
+    const int c0 = blockIdx.x * GT_COLS;
     const int N = tb.N, nh = tb.nh, np = tb.np;
     const double2* gr = Gr + (size_t)w * N * M;
     for (int e = threadIdx.x; e < nh * np; e += blockDim.x) cm[e] = Cm[(size_t)w * nh * np + e];
     __syncthreads();
     const double2 R = Rsum[w];
     const double2 iR = cdiv(cz(1, 0), R);
-    for (int e = threadIdx.x; e < np * 8; e += blockDim.x) {
-        const int p = e / 8, c = c0 + e % 8;
+    for (int e = threadIdx.x; e < np * GT_COLS; e += blockDim.x) {
+        const int p = e / GT_COLS, c = c0 + e % GT_COLS;
         double2 a = cz(0, 0);
         if (c < M)
             for (int h = 0; h < nh; ++h) a = cfma(cm[p * nh + h], gr[(size_t)tb.hole_pos[h] * M + c], a);
@@ -571,16 +584,16 @@ k_gt(SpinTables tb, int M, const double2* __restrict__ Gr, const double2* __rest
     }
     __syncthreads();
     double2* out = GT + (size_t)w * ld + off;
-    for (int e = threadIdx.x; e < (N + np) * 8; e += blockDim.x) {
-        const int x = e / 8, c = c0 + e % 8;
+    for (int e = threadIdx.x; e < (N + np) * GT_COLS; e += blockDim.x) {
+        const int x = e / GT_COLS, c = c0 + e % GT_COLS;
         if (c >= M) continue;
         double2 v;
         if (x < N) {
             v = gr[(size_t)x * M + c];
-            for (int p = 0; p < np; ++p) v = cfms(gr[(size_t)x * M + tb.part_orb[p]], y[p * 8 + e % 8], v);
+            for (int p = 0; p < np; ++p) v = cfms(gr[(size_t)x * M + tb.part_orb[p]], y[p * GT_COLS + e % GT_COLS], v);
             if (minus_ref && c == tb.occ0[x]) v.x -= 1.0;   // G_T - D0 D0^T
         } else {
-            v = y[(x - N) * 8 + e % 8];
+            v = y[(x - N) * GT_COLS + e % GT_COLS];
         }
         out[(size_t)x * M + c] = v;
     }
@@ -589,7 +602,7 @@ k_gt(SpinTables tb, int M, const double2* __restrict__ Gr, const double2* __rest
 void launch_gt(const SpinTables& tb, int nw, int M, const double2* Gr, const double2* Cm,
                const double2* R, double2* GT, long long ld, long long off, bool minus_ref, cudaStream_t st)
 {
-    dim3 grid((M + 7) / 8, nw);
+    dim3 grid((M + GT_COLS - 1) / GT_COLS, nw);
     k_gt<<<grid, 256, 0, st>>>(tb, M, Gr, Cm, R, GT, ld, off, minus_ref ? 1 : 0); msd_note_launch();
 }
 

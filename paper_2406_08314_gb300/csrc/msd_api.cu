@@ -237,7 +237,7 @@ SpinTables tables(const SpinHost& s, int cap)
     SpinTables t;
     t.N = s.N; t.nh = s.nh; t.np = s.np; t.n_str = s.n_str;
     for (int k = 0; k < MSD_KMAX + 2; ++k) t.bucket[k] = s.bucket[k];
-    t.occ0 = s.d_occ0; t.hole_pos = s.d_hole_pos; t.part_orb = s.d_part_orb;
+    t.occ0 = s.d_occ0; t.pos0 = s.d_pos0; t.hole_pos = s.d_hole_pos; t.part_orb = s.d_part_orb;
     t.str_h = s.d_str_h; t.str_p = s.d_str_p; t.str_sign = s.d_str_sign;
     t.csr_off = s.d_csr_off; t.csr_other = s.d_csr_other; t.csr_c = s.d_csr_c;
     t.cmx = s.d_cmx;
