@@ -95,6 +95,7 @@ struct PairTables {
     const int* a;       // [n_det] alpha string
     const int* b;       // [n_det] beta string
     const double* c;    // [n_det] coefficient
+    const float* cf;    // [n_det] coefficient in FP32
     const int* det_index;  // [n_det] original position in the trial list
 };
 

@@ -112,11 +112,25 @@ __device__ __forceinline__ double2 string_energy_term(const SpinTables& tb, int 
     return cmul(wts[(size_t)w * tb.n_str + s], e_s);   // wts holds r_s w_s
 }
 
+// The determinant's weight c_I r_a r_b and its product with X_ab are formed
+// in the working precision T (the ratios and coefficients come in T: the
+// FP64 arrays in FP64 mode, their FP32 copies in mixed mode).
+template <typename T>
+__device__ __forceinline__ cplx_t<T> pair_weight_times(const PairTables& pt, int I, cplx_t<T> ra, cplx_t<T> rb,
+                                                       T xr, T xi)
+{
+    using T2 = cplx_t<T>;
+    const T c = std::is_same<T, float>::value ? (T)pt.cf[I] : (T)pt.c[I];
+    const T2 r = T2{ra.x * rb.x - ra.y * rb.y, ra.x * rb.y + ra.y * rb.x};
+    const T2 rr = T2{r.x * c, r.y * c};
+    return T2{rr.x * xr - rr.y * xi, rr.x * xi + rr.y * xr};
+}
+
 template <int KB, typename T>
-__device__ __forceinline__ double2 pair_cross_term(const SpinTables& ta, const SpinTables& tbb, const PairTables& pt,
-                                                   int ka, int I, int w, const void* __restrict__ Ba_in,
-                                                   const void* __restrict__ Bb_in, const cplx_t<T>* ks,
-                                                   const double2* __restrict__ ra, const double2* __restrict__ rb)
+__device__ __forceinline__ cplx_t<T> pair_cross_term(const SpinTables& ta, const SpinTables& tbb, const PairTables& pt,
+                                                     int ka, int I, int w, const void* __restrict__ Ba_in,
+                                                     const void* __restrict__ Bb_in, const cplx_t<T>* ks,
+                                                     const cplx_t<T>* __restrict__ ra, const cplx_t<T>* __restrict__ rb)
 {
     using T2 = cplx_t<T>;
     const int Xb = tbb.nh * tbb.np;
@@ -157,18 +171,17 @@ __device__ __forceinline__ double2 pair_cross_term(const SpinTables& ta, const S
             xr += ba.x * zr - ba.y * zi;
             xim += ba.x * zi + ba.y * zr;
         }
-    const double2 rr = cscale(cmul(ra[(size_t)w * ta.n_str + a], rb[(size_t)w * tbb.n_str + b]), pt.c[I]);
-    return cmul(rr, cz((double)xr, (double)xim));
+    return pair_weight_times<T>(pt, I, ra[(size_t)w * ta.n_str + a], rb[(size_t)w * tbb.n_str + b], xr, xim);
 }
 
 // The opposite-spin term with both levels known at compile time: indices and
 // both inverse minors in registers, the ka^2 kb^2 gathers from shared memory
 // fully unrolled (same value as pair_cross_term).
 template <int KA, int KB, typename T>
-__device__ __forceinline__ double2 pair_cross_term2(const SpinTables& ta, const SpinTables& tbb, const PairTables& pt,
-                                                    int I, int w, const void* __restrict__ Ba_in,
-                                                    const void* __restrict__ Bb_in, const cplx_t<T>* ks,
-                                                    const double2* __restrict__ ra, const double2* __restrict__ rb)
+__device__ __forceinline__ cplx_t<T> pair_cross_term2(const SpinTables& ta, const SpinTables& tbb, const PairTables& pt,
+                                                      int I, int w, const void* __restrict__ Ba_in,
+                                                      const void* __restrict__ Bb_in, const cplx_t<T>* ks,
+                                                      const cplx_t<T>* __restrict__ ra, const cplx_t<T>* __restrict__ rb)
 {
     using T2 = cplx_t<T>;
     const int Xb = tbb.nh * tbb.np;
@@ -204,7 +217,7 @@ __device__ __forceinline__ double2 pair_cross_term2(const SpinTables& ta, const 
     for (int k = 0; k < KB; ++k)
 #pragma unroll
         for (int l = 0; l < KB; ++l) bb[k][l] = Bb[k * KB + l];
-    const double2 rr = cscale(cmul(ra[(size_t)w * ta.n_str + a], rb[(size_t)w * tbb.n_str + b]), pt.c[I]);
+    const cplx_t<T> rav = ra[(size_t)w * ta.n_str + a], rbv = rb[(size_t)w * tbb.n_str + b];
     T xr = 0, xim = 0;
 #pragma unroll
     for (int i = 0; i < KA; ++i)
@@ -223,5 +236,5 @@ __device__ __forceinline__ double2 pair_cross_term2(const SpinTables& ta, const 
             xr += ba[i][j].x * zr - ba[i][j].y * zi;
             xim += ba[i][j].x * zi + ba[i][j].y * zr;
         }
-    return cmul(rr, cz((double)xr, (double)xim));
+    return pair_weight_times<T>(pt, I, rav, rbv, xr, xim);
 }

@@ -38,25 +38,32 @@ __device__ double2 batch_se(const BatchSys& S, const BatchItem& it, int t, const
 template <typename T>
 __device__ double2 batch_pc(const BatchSys& S, const BatchItem& it, int t, const cplx_t<T>* ks)
 {
+    using T2 = cplx_t<T>;
     const int idx = it.ka * (MSD_KMAX + 1) + it.kb;
     const int lo = S.pt.bucket[idx], n = S.pt.bucket[idx + 1] - lo;
-    double2 acc = cz(0, 0);
+    // the ratios in the working precision, as in the per-system kernels
+    const T2* ra = std::is_same<T, float>::value ? reinterpret_cast<const T2*>(S.rf[0])
+                                                 : reinterpret_cast<const T2*>(S.r[0]);
+    const T2* rb = std::is_same<T, float>::value ? reinterpret_cast<const T2*>(S.rf[1])
+                                                 : reinterpret_cast<const T2*>(S.r[1]);
+    T2 acc = T2{0, 0};
     for (int q = 0; q < PC_PER_THREAD; ++q) {
         const int i0 = it.blk * (PC_THREADS * PC_PER_THREAD) + q * PC_THREADS + t;
         if (i0 >= n) break;
         const int I = lo + i0;
-        double2 v;
+        T2 v;
         switch (it.kb) {
-        case 1: v = pair_cross_term<1, T>(S.t[0], S.t[1], S.pt, it.ka, I, it.w, S.B[0], S.B[1], ks, S.r[0], S.r[1]); break;
-        case 2: v = pair_cross_term<2, T>(S.t[0], S.t[1], S.pt, it.ka, I, it.w, S.B[0], S.B[1], ks, S.r[0], S.r[1]); break;
-        case 3: v = pair_cross_term<3, T>(S.t[0], S.t[1], S.pt, it.ka, I, it.w, S.B[0], S.B[1], ks, S.r[0], S.r[1]); break;
-        case 4: v = pair_cross_term<4, T>(S.t[0], S.t[1], S.pt, it.ka, I, it.w, S.B[0], S.B[1], ks, S.r[0], S.r[1]); break;
-        case 5: v = pair_cross_term<5, T>(S.t[0], S.t[1], S.pt, it.ka, I, it.w, S.B[0], S.B[1], ks, S.r[0], S.r[1]); break;
-        default: v = pair_cross_term<6, T>(S.t[0], S.t[1], S.pt, it.ka, I, it.w, S.B[0], S.B[1], ks, S.r[0], S.r[1]); break;
+        case 1: v = pair_cross_term<1, T>(S.t[0], S.t[1], S.pt, it.ka, I, it.w, S.B[0], S.B[1], ks, ra, rb); break;
+        case 2: v = pair_cross_term<2, T>(S.t[0], S.t[1], S.pt, it.ka, I, it.w, S.B[0], S.B[1], ks, ra, rb); break;
+        case 3: v = pair_cross_term<3, T>(S.t[0], S.t[1], S.pt, it.ka, I, it.w, S.B[0], S.B[1], ks, ra, rb); break;
+        case 4: v = pair_cross_term<4, T>(S.t[0], S.t[1], S.pt, it.ka, I, it.w, S.B[0], S.B[1], ks, ra, rb); break;
+        case 5: v = pair_cross_term<5, T>(S.t[0], S.t[1], S.pt, it.ka, I, it.w, S.B[0], S.B[1], ks, ra, rb); break;
+        default: v = pair_cross_term<6, T>(S.t[0], S.t[1], S.pt, it.ka, I, it.w, S.B[0], S.B[1], ks, ra, rb); break;
         }
-        acc = cadd(acc, v);
+        acc.x += v.x;
+        acc.y += v.y;
     }
-    return acc;
+    return cz((double)acc.x, (double)acc.y);
 }
 
 template <typename T>

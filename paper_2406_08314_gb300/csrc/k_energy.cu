@@ -404,7 +404,7 @@ int string_energy_slots(const SpinTables& tb)
 template <int KB, typename T>
 __global__ void __launch_bounds__(PC_THREADS)
 k_pair_cross(SpinTables ta, SpinTables tbb, PairTables pt, int ka, int lo, int n,
-             const double2* __restrict__ ra, const double2* __restrict__ rb,
+             const void* __restrict__ ra_in, const void* __restrict__ rb_in,
              const void* __restrict__ Ba_in, const void* __restrict__ Bb_in,
              const void* __restrict__ Kin, double2* __restrict__ part, int nslot, int slot0)
 {
@@ -417,15 +417,19 @@ k_pair_cross(SpinTables ta, SpinTables tbb, PairTables pt, int ka, int lo, int n
     const T2* Kw = reinterpret_cast<const T2*>(Kin) + (size_t)w * Xa * Xb;
     for (int e = t; e < Xa * Xb; e += blockDim.x) ks[e] = Kw[e];
     __syncthreads();
-    double2 contrib = cz(0, 0);
+    const T2* ra = reinterpret_cast<const T2*>(ra_in);
+    const T2* rb = reinterpret_cast<const T2*>(rb_in);
+    T2 contrib = T2{0, 0};   // this thread's determinants, in the working precision
     // the shared Gram matrix is filled once per block and reused by
     // PC_PER_THREAD determinants per thread
     for (int it = 0; it < PC_PER_THREAD; ++it) {
         const int i0 = blockIdx.x * (PC_THREADS * PC_PER_THREAD) + it * PC_THREADS + t;
         if (i0 >= n) break;
-        contrib = cadd(contrib, pair_cross_term<KB, T>(ta, tbb, pt, ka, lo + i0, w, Ba_in, Bb_in, ks, ra, rb));
+        const T2 v = pair_cross_term<KB, T>(ta, tbb, pt, ka, lo + i0, w, Ba_in, Bb_in, ks, ra, rb);
+        contrib.x += v.x;
+        contrib.y += v.y;
     }
-    red[t] = contrib;
+    red[t] = cz((double)contrib.x, (double)contrib.y);
     __syncthreads();
     for (int o = PC_THREADS / 2; o; o >>= 1) {
         if (t < o) red[t] = cadd(red[t], red[t + o]);
@@ -436,7 +440,7 @@ k_pair_cross(SpinTables ta, SpinTables tbb, PairTables pt, int ka, int lo, int n
 
 template <int KB>
 static void launch_pc_k(const SpinTables& ta, const SpinTables& tb, const PairTables& pt, int ka,
-                        int nw, const double2* ra, const double2* rb, const void* Ba, const void* Bb,
+                        int nw, const void* ra, const void* rb, const void* Ba, const void* Bb,
                         const void* K, bool fp32, double2* part, int nslot, int& slot,
                         cudaStream_t st)
 {
@@ -461,7 +465,7 @@ static void launch_pc_k(const SpinTables& ta, const SpinTables& tb, const PairTa
 }
 
 void launch_pair_cross(const SpinTables& ta, const SpinTables& tb, const PairTables& pt, int nw,
-                       const double2* ra, const double2* rb, const void* Ba, const void* Bb,
+                       const void* ra, const void* rb, const void* Ba, const void* Bb,
                        const void* K, bool fp32, double2* part, int nslot, int slot0,
                        cudaStream_t st)
 {

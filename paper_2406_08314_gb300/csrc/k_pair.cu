@@ -13,8 +13,8 @@
 
 template <int KA, int KB, typename T>
 __global__ void __launch_bounds__(PC_THREADS)
-k_pair_cross2(SpinTables ta, SpinTables tbb, PairTables pt, int lo, int n, const double2* __restrict__ ra,
-              const double2* __restrict__ rb, const void* __restrict__ Ba_in, const void* __restrict__ Bb_in,
+k_pair_cross2(SpinTables ta, SpinTables tbb, PairTables pt, int lo, int n, const void* __restrict__ ra_in,
+              const void* __restrict__ rb_in, const void* __restrict__ Ba_in, const void* __restrict__ Bb_in,
               const void* __restrict__ Kin, double2* __restrict__ part, int nslot, int slot0)
 {
     using T2 = cplx_t<T>;
@@ -26,13 +26,17 @@ k_pair_cross2(SpinTables ta, SpinTables tbb, PairTables pt, int lo, int n, const
     const T2* Kw = reinterpret_cast<const T2*>(Kin) + (size_t)w * Xa * Xb;
     for (int e = t; e < Xa * Xb; e += blockDim.x) ks[e] = Kw[e];
     __syncthreads();
-    double2 contrib = cz(0, 0);
+    const T2* ra = reinterpret_cast<const T2*>(ra_in);
+    const T2* rb = reinterpret_cast<const T2*>(rb_in);
+    T2 contrib = T2{0, 0};   // this thread's determinants, in the working precision
     for (int it = 0; it < PC_PER_THREAD; ++it) {
         const int i0 = blockIdx.x * (PC_THREADS * PC_PER_THREAD) + it * PC_THREADS + t;
         if (i0 >= n) break;
-        contrib = cadd(contrib, pair_cross_term2<KA, KB, T>(ta, tbb, pt, lo + i0, w, Ba_in, Bb_in, ks, ra, rb));
+        const T2 v = pair_cross_term2<KA, KB, T>(ta, tbb, pt, lo + i0, w, Ba_in, Bb_in, ks, ra, rb);
+        contrib.x += v.x;
+        contrib.y += v.y;
     }
-    red[t] = contrib;
+    red[t] = cz((double)contrib.x, (double)contrib.y);
     __syncthreads();
     for (int o = PC_THREADS / 2; o; o >>= 1) {
         if (t < o) red[t] = cadd(red[t], red[t + o]);
@@ -43,7 +47,7 @@ k_pair_cross2(SpinTables ta, SpinTables tbb, PairTables pt, int lo, int n, const
 
 template <int KA, int KB>
 static bool go(bool fp32, dim3 grid, size_t smem, const SpinTables& ta, const SpinTables& tb, const PairTables& pt,
-               int lo, int n, const double2* ra, const double2* rb, const void* Ba, const void* Bb, const void* K,
+               int lo, int n, const void* ra, const void* rb, const void* Ba, const void* Bb, const void* K,
                double2* part, int nslot, int slot, cudaStream_t st)
 {
     if (fp32) {
@@ -60,7 +64,7 @@ static bool go(bool fp32, dim3 grid, size_t smem, const SpinTables& ta, const Sp
 }
 
 bool launch_pair_cross2(int ka, int kb, bool fp32, dim3 grid, size_t smem, const SpinTables& ta, const SpinTables& tb,
-                        const PairTables& pt, int lo, int n, const double2* ra, const double2* rb, const void* Ba,
+                        const PairTables& pt, int lo, int n, const void* ra, const void* rb, const void* Ba,
                         const void* Bb, const void* K, double2* part, int nslot, int slot, cudaStream_t st)
 {
     switch (ka * 8 + kb) {

@@ -57,8 +57,10 @@ int pair_y_slots(const SpinTables& tb);
 void launch_pair_y(const SpinTables& ta, const SpinTables& tb, int nw, const float2* rfa, const float2* rfb,
                    const void* Ba, const void* Bb, const void* Kab, double2* part, int nslot, int slot0,
                    cudaStream_t st);
+// ra, rb: the string ratios in the working precision (double2 in FP64 mode,
+// their FP32 copies in mixed mode)
 void launch_pair_cross(const SpinTables& ta, const SpinTables& tb, const PairTables& pt, int nw,
-                       const double2* ra, const double2* rb, const void* Ba, const void* Bb,
+                       const void* ra, const void* rb, const void* Ba, const void* Bb,
                        const void* K, bool fp32, double2* part, int nslot, int slot0,
                        cudaStream_t st);
 void launch_final(int nw, const double2* part, int nslot, int nR, double e0, const double2* e1a,
@@ -133,6 +135,7 @@ struct BatchSys {
     SpinTables t[2];
     PairTables pt;
     const double2* r[2];
+    const float2* rf[2];  // FP32 copies of r (mixed mode)
     const double2* wts[2];
     const void* B[2];
     const void* K[3];   // same-spin alpha, same-spin beta, opposite-spin Gram matrices
@@ -170,5 +173,5 @@ int launch_qr_mgs(int nw, int M, int N, double2* phi, unsigned* err, cudaStream_
 // k_pair.cu: the opposite-spin term with both levels compiled in (ka + kb <=
 // 8); false for other level pairs.
 bool launch_pair_cross2(int ka, int kb, bool fp32, dim3 grid, size_t smem, const SpinTables& ta, const SpinTables& tb,
-                        const PairTables& pt, int lo, int n, const double2* ra, const double2* rb, const void* Ba,
+                        const PairTables& pt, int lo, int n, const void* ra, const void* rb, const void* Ba,
                         const void* Bb, const void* K, double2* part, int nslot, int slot, cudaStream_t st);

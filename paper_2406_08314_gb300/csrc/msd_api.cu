@@ -52,6 +52,7 @@ struct PairHost {
     int bucket[(MSD_KMAX + 1) * (MSD_KMAX + 1) + 1] = {0};
     int *d_a = nullptr, *d_b = nullptr, *d_det_index = nullptr;
     double* d_c = nullptr;
+    float* d_cf = nullptr;   // FP32 copy of c
 };
 
 struct Buf {
@@ -261,7 +262,7 @@ PairTables pair_tables(const PairHost& p)
     PairTables t;
     t.n_det = p.n_det;
     for (int i = 0; i < (MSD_KMAX + 1) * (MSD_KMAX + 1) + 1; ++i) t.bucket[i] = p.bucket[i];
-    t.a = p.d_a; t.b = p.d_b; t.c = p.d_c; t.det_index = p.d_det_index;
+    t.a = p.d_a; t.b = p.d_b; t.c = p.d_c; t.cf = p.d_cf; t.det_index = p.d_det_index;
     return t;
 }
 
@@ -1015,8 +1016,11 @@ int en_chunk(msd_ctx* ctx, Chunk& c, EnWork& E, int w0, int nw, int cap, bool fp
         launch_pair_y(T[0], T[1], nw, c.rf[0], c.rf[1], c.B[0], c.B[1], E.Kab, c.part, c.nslot, slot, st);
     } else {
         th.begin("k_pair_cross", st);
-        launch_pair_cross(T[0], T[1], pair_tables(ctx->pairs), nw, c.r[0], c.r[1], c.B[0], c.B[1], E.Kab, fp32,
-                          c.part, c.nslot, slot, st);
+        // the ratios in the working precision: FP32 copies in mixed mode
+        const void* ra = fp32 ? (const void*)c.rf[0] : (const void*)c.r[0];
+        const void* rb = fp32 ? (const void*)c.rf[1] : (const void*)c.r[1];
+        launch_pair_cross(T[0], T[1], pair_tables(ctx->pairs), nw, ra, rb, c.B[0], c.B[1], E.Kab, fp32, c.part,
+                          c.nslot, slot, st);
     }
     th.end(st);
     CKLAUNCH();
@@ -1293,7 +1297,7 @@ void msd_destroy(msd_ctx* ctx)
     for (auto& kv : ctx->arena) cudaFree(kv.second.p);
     for (int s = 0; s < 2; ++s) free_spin(ctx->sp[s]);
     cudaFree(ctx->pairs.d_a); cudaFree(ctx->pairs.d_b); cudaFree(ctx->pairs.d_c);
-    cudaFree(ctx->pairs.d_det_index);
+    cudaFree(ctx->pairs.d_det_index); cudaFree(ctx->pairs.d_cf);
     free_mixed(ctx);
     free_prop(ctx);
     cudaFree(ctx->d_h1); cudaFree(ctx->d_Lcat); cudaFree(ctx->d_err);
@@ -1338,7 +1342,7 @@ int msd_set_trial(msd_ctx* ctx, int n_det, const double* coeff, const int32_t* o
     }
     // determinants ordered by (level_a, level_b, a, b)
     PairHost& P = ctx->pairs;
-    cudaFree(P.d_a); cudaFree(P.d_b); cudaFree(P.d_c); cudaFree(P.d_det_index);
+    cudaFree(P.d_a); cudaFree(P.d_b); cudaFree(P.d_c); cudaFree(P.d_det_index); cudaFree(P.d_cf);
     P = PairHost{};
     P.n_det = n_det;
     std::vector<int> order(n_det);
@@ -1400,6 +1404,10 @@ int msd_set_trial(msd_ctx* ctx, int n_det, const double* coeff, const int32_t* o
     if ((rc = upload(ctx, &P.d_a, P.a))) return rc;
     if ((rc = upload(ctx, &P.d_b, P.b))) return rc;
     if ((rc = upload(ctx, &P.d_c, P.c))) return rc;
+    {
+        std::vector<float> cf(P.c.begin(), P.c.end());
+        if ((rc = upload(ctx, &P.d_cf, cf))) return rc;
+    }
     if ((rc = upload(ctx, &P.d_det_index, P.det_index))) return rc;
     // shared-memory needs of the energy kernels
     for (int s = 0; s < 2; ++s) {
@@ -1915,6 +1923,7 @@ int batch_run(msd_batch* b, const int* n_w, const double* const* pa, const doubl
             S.pt = pair_tables(ctx->pairs);
             for (int s = 0; s < 2; ++s) {
                 S.r[s] = d[i].c.r[s];
+                S.rf[s] = d[i].c.rf[s];
                 S.wts[s] = d[i].c.wts[s];
                 S.B[s] = d[i].c.B[s];
                 S.Y[s] = d[i].E.Y[s];
