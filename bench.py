@@ -470,8 +470,8 @@ def run_batched(args, rank, world, local):
     units = float(sum(w.n_w * s.n_det for s, w in sysw))
     batch = msd.Batch(ctxs)
     outs = batch.outputs(walkers)
-    cache = os.path.join(ROOT, "gpurun_out", "batch_tune.txt") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) \
-        else None
+    import tempfile
+    cache = os.path.join(tempfile.gettempdir(), "msd_batch_tune.txt")   # autotuner cache across runs
     t0 = time.perf_counter()
     cfg = batch.autotune(walkers, outs, cache_path=cache)
     tune_s = time.perf_counter() - t0
