@@ -46,7 +46,12 @@ __device__ __forceinline__ double2 string_energy_term(const SpinTables& tb, int 
     T qr = 0, qi = 0;      // Qc - Qx
     if constexpr (KL <= 4) {
         // fully unrolled: every index and B value is in registers, the loop
-        // body reads shared memory only
+        // body reads shared memory only. K is symmetric (a same-spin Gram
+        // matrix), and so is each summand of Q under (i, j) <-> (k, l):
+        // b_ij b_kl K[(j,i)][(l,k)] and b_ij b_kl K[(j,k)][(l,i)] map to
+        // themselves. So only the pairs (k, l) >= (i, j) (row-major order)
+        // are summed, the others counted by doubling: k^2 (k^2 + 1) / 2
+        // instead of k^4 pairs (the skipped pairs vanish at compile time).
 #pragma unroll
         for (int i = 0; i < KL; ++i) {
 #pragma unroll
@@ -57,20 +62,31 @@ __device__ __forceinline__ double2 string_energy_term(const SpinTables& tb, int 
                 lr += bij.x * y.x - bij.y * y.y;
                 li += bij.x * y.y + bij.y * y.x;
                 const T2* kc_row = ks + (size_t)xij * X;
-                T zr = 0, zi = 0;
+                T zr = 0, zi = 0;      // pairs after (i, j)
+                T dgr = 0, dgi = 0;    // the pair (i, j) itself
 #pragma unroll
                 for (int k = 0; k < KL; ++k) {
                     const T2* kx_row = ks + (size_t)(hx[j] + px[k]) * X + px[i];
 #pragma unroll
                     for (int l = 0; l < KL; ++l) {
+                        if (k * KL + l < i * KL + j) continue;
                         // K[(h_j,p_i)][(h_l,p_k)] - K[(h_j,p_k)][(h_l,p_i)]
                         const T2 kc = kc_row[hx[l] + px[k]];
                         const T2 kx = kx_row[hx[l]];
                         const T dr = kc.x - kx.x, di = kc.y - kx.y;
-                        zr += b[k][l].x * dr - b[k][l].y * di;
-                        zi += b[k][l].x * di + b[k][l].y * dr;
+                        const T tr = b[k][l].x * dr - b[k][l].y * di;
+                        const T ti = b[k][l].x * di + b[k][l].y * dr;
+                        if (k * KL + l == i * KL + j) {
+                            dgr = tr;
+                            dgi = ti;
+                        } else {
+                            zr += tr;
+                            zi += ti;
+                        }
                     }
                 }
+                zr = dgr + 2 * zr;
+                zi = dgi + 2 * zi;
                 qr += bij.x * zr - bij.y * zi;
                 qi += bij.x * zi + bij.y * zr;
             }
