@@ -147,6 +147,22 @@ int msd_local_energy(msd_ctx* ctx, int n_w, const double* phi_a, const double* p
 int msd_evaluate(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b,
                  double* ovlp, double* vbias, double* e_loc, void* stream);
 
+/* Per-determinant local energies for sampled (walker, determinant) pairs,
+   the localisation output of the energy path (Sec. III energy estimator:
+   E_I = <D_I|H|phi> / <D_I|phi>, whose c_I r_I-weighted mean is E_L). The
+   library runs the energy path up to its per-walker intermediates (the
+   reference energy, the same-spin Gram matrices and linear terms, the
+   opposite-spin Gram matrix, the inverse minors of every excitation string)
+   and evaluates each requested E_I from them with the same per-determinant
+   arithmetic, in the context's precision.
+     n_pairs          number of pairs (0 is a no-op)
+     w_idx, det_idx   [n_pairs] HOST int32 arrays: walker index in [0, n_w)
+                      and determinant index in the trial list [0, n_det)
+     e_det            [n_pairs] complex E_I (host or device)
+   MSD_ERR_ARG for an index out of range or device index arrays. */
+int msd_det_energies(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b, int n_pairs,
+                     const int32_t* w_idx, const int32_t* det_idx, double* e_det, void* stream);
+
 /* Introspection. Keys: */
 #define MSD_INFO_N_DET          1
 #define MSD_INFO_N_CHOL         2
@@ -158,6 +174,8 @@ int msd_evaluate(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b
 #define MSD_INFO_N_PARTS_B      8
 #define MSD_INFO_WORKSPACE_BYTES 9  /* device workspace currently held          */
 #define MSD_INFO_WALKER_CHUNK  10   /* walkers per internal pass                */
+#define MSD_INFO_EXACT_REFERENCE 11 /* 1 if the next mixed energy takes the exact
+                                       reference sums (msd_set_exact_reference) */
 int msd_info(const msd_ctx* ctx, int key, long long* value);
 
 /* Per-kernel timing with CUDA events on the launching stream. When enabled,
@@ -191,6 +209,21 @@ int msd_set_sync(msd_ctx* ctx, int sync);
    does not support (2N > 128 rows per walker, tiles beyond 227 KB of shared
    memory) take the unfused path. */
 int msd_set_fused(msd_ctx* ctx, int fused);
+
+/* Mixed precision only: with on = 1 (the default) the reference-determinant
+   part of the local energy (Sec. II A, the generalized Wick theorem for the
+   reference D_0: one-body, Coulomb and exchange energy of G, the dominant
+   part of E_L) is computed to FP64 accuracy. Its terms linear in
+   dG = G - D_0 D_0^T are one-body contractions with constant matrices
+   (FP64); its quadratic terms sum_g tr(L_g dG)^2 and sum_g tr(dT_g dT_g),
+   dT_g = (dG L_g)[occ0][occ0], are one product of the walker's dG with a
+   constant exchange-integral matrix, evaluated on the tensor cores by an
+   exact-integer split of both operands into BF16 slices (about 35 bits).
+   With on = 0 these sums come from the FP32 traces of the 3xTF32
+   contraction (relative error about 1e-7 of the energy). The constant
+   operand takes about 10 (N (M - N) + n_chol) N (M - N) bytes per spin;
+   spins with N (M - N) above 16384 always take the FP32 traces. */
+int msd_set_exact_reference(msd_ctx* ctx, int on);
 
 /* Mixed precision only: the form of the opposite-spin exchange term of the
    local energy (Sec. III, the alpha-beta part of the two-body Wick

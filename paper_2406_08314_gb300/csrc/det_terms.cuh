@@ -2,7 +2,7 @@
 // (k_energy.cu) and the persistent batched kernel (k_batch.cu).
 //
 // string_energy_term: same-spin term of one excitation string s (level KL,
-// index sl in its bucket) of walker w:
+// index sl in its bucket) of walker w (string_energy_value: e_s alone):
 //   r_s w_s e_s,  e_s = sum_ij B_ij Y[h_j][p_i] + 1/2 (Qc - Qx),
 //   Qc = sum_ijkl B_ij B_kl K[(h_j,p_i)][(h_l,p_k)],
 //   Qx = sum_ijkl B_ij B_kl K[(h_j,p_k)][(h_l,p_i)]
@@ -11,7 +11,7 @@
 // loop is unrolled over the inverse minor held in registers.
 //
 // pair_cross_term: opposite-spin term of determinant I = (a, b) with levels
-// (ka, KB) of walker w:
+// (ka, KB) of walker w (pair_cross_value: X_ab alone):
 //   c_I r_a r_b X_ab,  X_ab = sum_ij Ba_ij sum_kl Bb_kl K^{ab}[(ha_j,pa_i)][(hb_l,pb_k)]
 // (K^{ab} in shared memory).
 #pragma once
@@ -23,10 +23,12 @@
 template <typename T>
 using cplx_t = typename std::conditional<std::is_same<T, float>::value, float2, double2>::type;
 
+// e_s of string s = bucket[KL] + sl (unweighted); string_energy_term below
+// multiplies it by r_s w_s.
 template <int KL, typename T>
-__device__ __forceinline__ double2 string_energy_term(const SpinTables& tb, int w, int sl, int ns,
-                                                      const void* __restrict__ Bin, const cplx_t<T>* ks,
-                                                      const cplx_t<T>* ys, const double2* __restrict__ wts)
+__device__ __forceinline__ double2 string_energy_value(const SpinTables& tb, int w, int sl, int ns,
+                                                       const void* __restrict__ Bin, const cplx_t<T>* ks,
+                                                       const cplx_t<T>* ys)
 {
     using T2 = cplx_t<T>;
     const int X = tb.nh * tb.np, np = tb.np;
@@ -124,8 +126,16 @@ __device__ __forceinline__ double2 string_energy_term(const SpinTables& tb, int 
             }
         }
     }
-    const double2 e_s = cz((double)lr + 0.5 * (double)qr, (double)li + 0.5 * (double)qi);
-    return cmul(wts[(size_t)w * tb.n_str + s], e_s);   // wts holds r_s w_s
+    return cz((double)lr + 0.5 * (double)qr, (double)li + 0.5 * (double)qi);
+}
+
+template <int KL, typename T>
+__device__ __forceinline__ double2 string_energy_term(const SpinTables& tb, int w, int sl, int ns,
+                                                      const void* __restrict__ Bin, const cplx_t<T>* ks,
+                                                      const cplx_t<T>* ys, const double2* __restrict__ wts)
+{
+    const double2 e_s = string_energy_value<KL, T>(tb, w, sl, ns, Bin, ks, ys);
+    return cmul(wts[(size_t)w * tb.n_str + tb.bucket[KL] + sl], e_s);   // wts holds r_s w_s
 }
 
 // The determinant's weight c_I r_a r_b and its product with X_ab are formed
@@ -142,15 +152,14 @@ __device__ __forceinline__ cplx_t<T> pair_weight_times(const PairTables& pt, int
     return T2{rr.x * xr - rr.y * xi, rr.x * xi + rr.y * xr};
 }
 
+// X_ab of alpha string a (level ka) and beta string b (level KB), unweighted.
 template <int KB, typename T>
-__device__ __forceinline__ cplx_t<T> pair_cross_term(const SpinTables& ta, const SpinTables& tbb, const PairTables& pt,
-                                                     int ka, int I, int w, const void* __restrict__ Ba_in,
-                                                     const void* __restrict__ Bb_in, const cplx_t<T>* ks,
-                                                     const cplx_t<T>* __restrict__ ra, const cplx_t<T>* __restrict__ rb)
+__device__ __forceinline__ cplx_t<T> pair_cross_value(const SpinTables& ta, const SpinTables& tbb, int ka, int a,
+                                                      int b, int w, const void* __restrict__ Ba_in,
+                                                      const void* __restrict__ Bb_in, const cplx_t<T>* ks)
 {
     using T2 = cplx_t<T>;
     const int Xb = tbb.nh * tbb.np;
-    const int a = pt.a[I], b = pt.b[I];
     const int nsa = ta.bucket[ka + 1] - ta.bucket[ka], sa = a - ta.bucket[ka];
     const int nsb = tbb.bucket[KB + 1] - tbb.bucket[KB], sb = b - tbb.bucket[KB];
     int xb[KB][KB];
@@ -187,7 +196,18 @@ __device__ __forceinline__ cplx_t<T> pair_cross_term(const SpinTables& ta, const
             xr += ba.x * zr - ba.y * zi;
             xim += ba.x * zi + ba.y * zr;
         }
-    return pair_weight_times<T>(pt, I, ra[(size_t)w * ta.n_str + a], rb[(size_t)w * tbb.n_str + b], xr, xim);
+    return T2{xr, xim};
+}
+
+template <int KB, typename T>
+__device__ __forceinline__ cplx_t<T> pair_cross_term(const SpinTables& ta, const SpinTables& tbb, const PairTables& pt,
+                                                     int ka, int I, int w, const void* __restrict__ Ba_in,
+                                                     const void* __restrict__ Bb_in, const cplx_t<T>* ks,
+                                                     const cplx_t<T>* __restrict__ ra, const cplx_t<T>* __restrict__ rb)
+{
+    const int a = pt.a[I], b = pt.b[I];
+    const cplx_t<T> x = pair_cross_value<KB, T>(ta, tbb, ka, a, b, w, Ba_in, Bb_in, ks);
+    return pair_weight_times<T>(pt, I, ra[(size_t)w * ta.n_str + a], rb[(size_t)w * tbb.n_str + b], x.x, x.y);
 }
 
 // The opposite-spin term with both levels known at compile time: indices and

@@ -108,6 +108,49 @@ int tc_fepi_fused(const SpinTables& tb, const TcFepiPlan& p, int nw, int M, int 
                   const float* F0P, const double* c0, const double* x0, double2* v0, double2* xx,
                   float2* Lact, float2* Xic, unsigned* err, cudaStream_t st);
 
+// tc_ozaki.cu: the reference-determinant Cholesky sums of the mixed local
+// energy in FP64 accuracy (exact-integer BF16 slices on the tensor cores).
+// Constant operand of one spin: B = [V | W]^T sliced, NB = N Kv + G rows.
+struct OzConst {
+    int N = 0, Kv = 0, G = 0, NK = 0, NB = 0, NBp = 0, Kp = 0;
+    void* Bs = nullptr;   // [OZ_S][NBp][Kp] BF16
+    int* eb = nullptr;    // [NBp] row exponents
+};
+// One spin's inputs to the per-walker reduction.
+struct RefSpin {
+    int N, M, Kv, nparts, Mpad;
+    const double2* Gr;
+    const int* virt;
+    const double* JJ;     // [N Kv] J[v_r][o_j], J = sum_g (c0a_g + c0b_g) L_g
+    const double* KK;     // [N Kv] (sum_g L_g P0 L_g)[v_r][o_j]
+    const double* t1;     // [2 nw][G]
+    const double2* part;  // [nparts][Mpad]
+    double x0sum;         // sum_g x0_g of this spin
+};
+size_t oz_const_bytes(int N, int Kv, int G);
+int oz_rows_padded(int nrow);
+int oz_k_padded(int NK);
+int oz_parts(int NB);
+int oz_slices();
+// d_XT: [N Kv][G] FP64, XT[r N + l][g] = L_g[v_r][o_l]. Allocates out's arrays.
+int oz_prepare_const(int N, int Kv, int G, const double* d_XT, OzConst& out, cudaStream_t st);
+void oz_free_const(OzConst& c);
+// As: [OZ_S][pad(2 nw)][Kp] BF16 scratch, ea: [pad(2 nw)]; writes part
+// [oz_parts(NB)][pad(2 nw)] and t1 [2 nw][G].
+int oz_spin(const OzConst& K, int nw, int M, const double2* Gr, const int* virt, void* As, int* ea, double2* part,
+            double* t1, unsigned* err, cudaStream_t st);
+void launch_ref_reduce(int nw, int G, const RefSpin& a, const RefSpin& b, double C2sum, double2* scal,
+                       cudaStream_t st);
+
+// k_debug.cu: E_I of sampled (walker, determinant) pairs.
+struct DetRec {
+    int w, a, b, ka, kb;   // walker, alpha and beta string, their levels
+};
+void launch_det_energy(int n, const DetRec* recs, int w0, int nw, const SpinTables& ta, const SpinTables& tb,
+                       const void* Ba, const void* Bb, const void* Kaa, const void* Kbb, const void* Kab,
+                       const void* Ya, const void* Yb, const double2* scal, const double2* e1a, const double2* e1b,
+                       double e0, bool fp32, double2* out, cudaStream_t st);
+
 // k_mixed.cu
 size_t fepi_f32_smem(const SpinTables& tb);
 void launch_fepi_f32(const SpinTables& tb, int nw, int M, int n_chol, const float* dF, long long ldf,

@@ -111,6 +111,14 @@ struct msd_ctx {
     int pair_form = -1;           // mixed mode, opposite-spin term: -1 auto, 0 per determinant, 1 per beta string
     bool pair_y_auto = false;     // the auto choice for the current trial (set_trial)
     bool fused_ok[2] = {false, false};
+    // exact reference-determinant sums of the mixed energy (tc_ozaki.cu)
+    bool exact_ref = true;        // requested (msd_set_exact_reference)
+    bool oz_ready = false;        // constants built for the current Hamiltonian and trial
+    bool oz_ok = false;           // the shapes allow it (set with oz_ready)
+    bool oz_shared = false;       // spin 1 uses spin 0's constants (same reference orbitals)
+    OzConst oz[2];
+    double *d_JJ[2] = {nullptr, nullptr}, *d_KK[2] = {nullptr, nullptr};
+    double oz_x0sum[2] = {0, 0}, oz_C2sum = 0;
     TcFepiPlan fplan[2];
     long long gen = 0;            // bumped whenever a device buffer may move
     // propagation (msd_propagate): transposed Cholesky vectors, sum_g L_g L_g
@@ -124,6 +132,7 @@ struct msd_ctx {
 namespace {
 
 void free_mixed(msd_ctx* ctx);
+void free_exact_ref(msd_ctx* ctx);
 void free_prop(msd_ctx* ctx);
 
 int fail(msd_ctx* c, int code, const char* fmt, ...)
@@ -472,7 +481,111 @@ void free_mixed(msd_ctx* ctx)
     cudaFree(ctx->d_c0sum);
     ctx->d_c0sum = nullptr;
     ctx->mixed_ready = false;
+    free_exact_ref(ctx);
 }
+
+void free_exact_ref(msd_ctx* ctx)
+{
+    for (int s = 0; s < 2; ++s) {
+        if (s == 1 && ctx->oz_shared) {
+            ctx->oz[1] = OzConst{};
+            ctx->d_JJ[1] = ctx->d_KK[1] = nullptr;
+            continue;
+        }
+        oz_free_const(ctx->oz[s]);
+        cudaFree(ctx->d_JJ[s]); cudaFree(ctx->d_KK[s]);
+        ctx->d_JJ[s] = ctx->d_KK[s] = nullptr;
+    }
+    ctx->oz_shared = false;
+    ctx->oz_ready = ctx->oz_ok = false;
+}
+
+// Largest N (M - N) per spin for which the exact reference sums are built
+// (their constant operand takes about 10 (N (M - N) + n_chol) N (M - N) bytes).
+constexpr long long OZ_MAX_NK = 16384;
+
+bool exact_ref_shapes_ok(const msd_ctx* ctx)
+{
+    for (int s = 0; s < 2; ++s) {
+        const long long NK = (long long)ctx->sp[s].N * (ctx->M - ctx->sp[s].N);
+        if (NK <= 0 || NK > OZ_MAX_NK) return false;
+    }
+    return ctx->n_chol > 0;
+}
+
+// Constants of the exact reference part, once per Hamiltonian and trial.
+// With C_g = c0a_g + c0b_g (c0 = tr(L_g D0 D0^T) per spin), v_r the orbitals
+// outside occ0 and u[(j, r)] = dG[occ0_j][v_r]:
+//   sum_g C_g t1_g      = u . JJ,  JJ[(j, r)] = (sum_g C_g L_g)[v_r][o_j]
+//   sum_g tr(T0_g dT_g) = u . KK,  KK[(j, r)] = (sum_g L_g D0 D0^T L_g)[v_r][o_j]
+// (both linear in dG, FP64), x0sum = sum_g x0_g, C2sum = sum_g C_g^2, and the
+// sliced constant operand [V | W] of tc_ozaki.cu.
+int prepare_exact_ref(msd_ctx* ctx, cudaStream_t st)
+{
+    if (ctx->oz_ready) return MSD_OK;
+    free_exact_ref(ctx);
+    ctx->oz_ready = true;
+    if (!exact_ref_shapes_ok(ctx)) return MSD_OK;
+    const int M = ctx->M, G = ctx->n_chol;
+    const double* L = ctx->h_L.data();
+    auto Lv = [&](int g, int p, int q) { return L[((size_t)g * M + p) * M + q]; };
+    std::vector<double> C(G, 0.0);
+    for (int s = 0; s < 2; ++s)
+        for (int g = 0; g < G; ++g)
+            for (int o : ctx->sp[s].occ0) C[g] += Lv(g, o, o);
+    ctx->oz_C2sum = 0;
+    for (int g = 0; g < G; ++g) ctx->oz_C2sum += C[g] * C[g];
+    ctx->oz_shared = ctx->sp[1].occ0 == ctx->sp[0].occ0;
+    for (int s = 0; s < 2; ++s) {
+        const SpinHost& S = ctx->sp[s];
+        const int N = S.N;
+        double x0 = 0;
+        for (int g = 0; g < G; ++g)
+            for (int j = 0; j < N; ++j)
+                for (int l = 0; l < N; ++l) x0 += Lv(g, S.occ0[j], S.occ0[l]) * Lv(g, S.occ0[j], S.occ0[l]);
+        ctx->oz_x0sum[s] = x0;
+        if (s == 1 && ctx->oz_shared) {
+            ctx->oz[1] = ctx->oz[0];
+            ctx->d_JJ[1] = ctx->d_JJ[0];
+            ctx->d_KK[1] = ctx->d_KK[0];
+            continue;
+        }
+        std::vector<char> in0(M, 0);
+        for (int o : S.occ0) in0[o] = 1;
+        std::vector<int> v;
+        for (int o = 0; o < M; ++o) if (!in0[o]) v.push_back(o);
+        const int Kv = (int)v.size(), NK = N * Kv;
+        std::vector<double> XT((size_t)NK * G), JJ(NK, 0.0), KK(NK, 0.0);
+        for (int r = 0; r < Kv; ++r)
+            for (int l = 0; l < N; ++l)
+                for (int g = 0; g < G; ++g) XT[((size_t)r * N + l) * G + g] = Lv(g, v[r], S.occ0[l]);
+        std::vector<double> row(N);
+        for (int g = 0; g < G; ++g)
+            for (int r = 0; r < Kv; ++r) {
+                for (int l = 0; l < N; ++l) row[l] = Lv(g, v[r], S.occ0[l]);
+                for (int j = 0; j < N; ++j) {
+                    double k = 0;
+                    for (int l = 0; l < N; ++l) k += row[l] * Lv(g, S.occ0[l], S.occ0[j]);
+                    JJ[(size_t)j * Kv + r] += C[g] * row[j];
+                    KK[(size_t)j * Kv + r] += k;
+                }
+            }
+        int rc;
+        if ((rc = upload(ctx, &ctx->d_JJ[s], JJ)) || (rc = upload(ctx, &ctx->d_KK[s], KK))) return rc;
+        double* d_XT = nullptr;
+        if ((rc = upload(ctx, &d_XT, XT))) return rc;
+        const int pr = oz_prepare_const(N, Kv, G, d_XT, ctx->oz[s], st);
+        CK(cudaStreamSynchronize(st));
+        cudaFree(d_XT);
+        if (pr) return fail(ctx, MSD_ERR_NOMEM, "exact reference constants (%lld bytes) could not be built",
+                            (long long)oz_const_bytes(N, Kv, G));
+    }
+    ctx->oz_ok = true;
+    return MSD_OK;
+}
+
+// The exact reference sums run for this call.
+bool exact_ref_on(const msd_ctx* ctx) { return ctx->prec == MSD_MIXED && ctx->exact_ref && exact_ref_shapes_ok(ctx); }
 
 // Mixed-path operands, once per Hamiltonian and trial. The reference part
 // of the Green's function is known exactly: Theta[occ0, :] = I, so
@@ -837,6 +950,7 @@ int fb_chunk(msd_ctx* ctx, Chunk& c, FbWork& f, int w0, int nw, int cap, bool fp
 struct EnWork {
     void *F[2] = {nullptr, nullptr}, *F32 = nullptr, *Ah = nullptr, *Al = nullptr;
     void *v0[2], *xx[2], *La[2], *Xi[2], *Lh1[2], *e1[2], *Y[2], *Kaa, *Kbb, *Kab, *scal;
+    void *ozA = nullptr, *ozE = nullptr, *ozP[2] = {nullptr, nullptr}, *ozT[2] = {nullptr, nullptr};
 };
 
 // The fused tensor-core contraction + epilogue serves spin s.
@@ -868,6 +982,13 @@ size_t en_bytes_per_walker(msd_ctx* ctx, bool fp32)
     for (int s = 0; s < 2; ++s) e += (size_t)G * (2 + 2 * X[s]) + 3 * X[s] + 1;
     e += (size_t)X[0] * X[0] + (size_t)X[1] * X[1] + (size_t)X[0] * X[1];
     size_t b = e * sizeof(double2);
+    if (fp32 && exact_ref_on(ctx)) {
+        int kp = 0;
+        for (int s = 0; s < 2; ++s) kp = std::max(kp, oz_k_padded(T1[s].N * (ctx->M - T1[s].N)));
+        b += (size_t)2 * oz_slices() * kp * 2 + 2 * sizeof(int);
+        for (int s = 0; s < 2; ++s)
+            b += (size_t)2 * oz_parts(T1[s].N * (ctx->M - T1[s].N) + G) * sizeof(double2) + 2 * sizeof(double) * G;
+    }
     if (fp32) {
         size_t f = 0, a = 0;
         for (int s = 0; s < 2; ++s) {
@@ -917,6 +1038,20 @@ int en_alloc(msd_ctx* ctx, int cap, bool fp32, EnWork& E)
     if ((rc = arena_get(ctx, "K_bb", sizeof(double2) * cap * std::max(1, X[1] * X[1]), &E.Kbb))) return rc;
     if ((rc = arena_get(ctx, "K_ab", sizeof(double2) * cap * std::max(1, X[0] * X[1]), &E.Kab))) return rc;
     if ((rc = arena_get(ctx, "scal", sizeof(double2) * cap * 8, &E.scal))) return rc;
+    if (fp32 && exact_ref_on(ctx)) {
+        const int Mpad = oz_rows_padded(2 * cap);
+        int kp = 0;
+        for (int s = 0; s < 2; ++s) kp = std::max(kp, oz_k_padded(T1[s].N * (ctx->M - T1[s].N)));
+        if ((rc = arena_get(ctx, "oz_A", (size_t)oz_slices() * Mpad * kp * 2, &E.ozA))) return rc;
+        if ((rc = arena_get(ctx, "oz_ea", sizeof(int) * Mpad, &E.ozE))) return rc;
+        static const char* np_[2] = {"oz_part_a", "oz_part_b"};
+        static const char* nt_[2] = {"oz_t1_a", "oz_t1_b"};
+        for (int s = 0; s < 2; ++s) {
+            const int NB = T1[s].N * (ctx->M - T1[s].N) + G;
+            if ((rc = arena_get(ctx, np_[s], sizeof(double2) * oz_parts(NB) * Mpad, &E.ozP[s]))) return rc;
+            if ((rc = arena_get(ctx, nt_[s], sizeof(double) * 2 * cap * (size_t)G, &E.ozT[s]))) return rc;
+        }
+    }
     return MSD_OK;
 }
 
@@ -988,6 +1123,27 @@ int en_chunk(msd_ctx* ctx, Chunk& c, EnWork& E, int w0, int nw, int cap, bool fp
                                 (double2*)E.scal, st);
     }
     th.end(st);
+    if (fp32 && exact_ref_on(ctx)) {
+        // the reference-determinant sums again, exactly split on the tensor
+        // cores: they replace the FP32 traces in scal[0..2]
+        if (!ctx->oz_ok) return fail(ctx, MSD_ERR_STATE, "exact reference constants missing");
+        RefSpin rs[2];
+        for (int s = 0; s < 2; ++s) {
+            const OzConst& K = ctx->oz[s];
+            th.begin("tc_ozaki", st);
+            if (oz_spin(K, nw, M, c.Gr[s], ctx->d_virt[s], E.ozA, (int*)E.ozE, (double2*)E.ozP[s],
+                        (double*)E.ozT[s], ctx->d_err, st))
+                return fail(ctx, MSD_ERR_CUDA, "exact reference tensor-core launch failed");
+            th.end(st);
+            rs[s] = RefSpin{K.N, M, K.Kv, oz_parts(K.NB), oz_rows_padded(2 * nw), c.Gr[s], ctx->d_virt[s],
+                            ctx->d_JJ[s], ctx->d_KK[s], (const double*)E.ozT[s], (const double2*)E.ozP[s],
+                            ctx->oz_x0sum[s]};
+        }
+        th.begin("k_ref_reduce", st);
+        launch_ref_reduce(nw, G, rs[0], rs[1], ctx->oz_C2sum, (double2*)E.scal, st);
+        th.end(st);
+        CKLAUNCH();
+    }
     th.begin("k_gram", st);
     if (fp32) {
         GramJobs jobs = {{{X[0], X[0], (float2*)E.La[0], (float2*)E.La[0], (float2*)E.Kaa},
@@ -1050,6 +1206,7 @@ int evaluate_impl(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_
     if (n_w == 0) return MSD_OK;
     const bool fp32 = ctx->prec == MSD_MIXED;
     if (fp32 && (rc = prepare_mixed(ctx, st))) return rc;
+    if (fp32 && e_loc && exact_ref_on(ctx) && (rc = prepare_exact_ref(ctx, st))) return rc;
     Staged in;
     if ((rc = stage_inputs(ctx, n_w, phi_a, phi_b, st, in))) return rc;
     Out o_v, o_e, o_ov;
@@ -1094,6 +1251,61 @@ int evaluate(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b, do
              double* e_loc, void* stream)
 {
     return evaluate_impl(ctx, n_w, phi_a, phi_b, ovlp, vbias, e_loc, stream, nullptr);
+}
+
+// E_I for sampled (walker, determinant) pairs: the energy path up to the
+// per-walker Gram matrices, then one thread per pair.
+int det_energies(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b, int n_pairs,
+                 const int32_t* w_idx, const int32_t* det_idx, double* e_det, void* stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = begin_call(ctx, n_w, phi_a, phi_b, st);
+    if (rc) return rc;
+    if (n_pairs < 0 || (n_pairs > 0 && (!w_idx || !det_idx || !e_det)))
+        return fail(ctx, MSD_ERR_ARG, "bad pair arguments");
+    if (n_pairs == 0) return MSD_OK;
+    if (is_device_ptr(w_idx) || is_device_ptr(det_idx))
+        return fail(ctx, MSD_ERR_ARG, "w_idx and det_idx must be host arrays");
+    const PairHost& P = ctx->pairs;
+    std::vector<int> pos(P.n_det);
+    for (int i = 0; i < P.n_det; ++i) pos[P.det_index[i]] = i;
+    std::vector<DetRec> recs(n_pairs);
+    for (int i = 0; i < n_pairs; ++i) {
+        if (w_idx[i] < 0 || w_idx[i] >= n_w || det_idx[i] < 0 || det_idx[i] >= P.n_det)
+            return fail(ctx, MSD_ERR_ARG, "pair %d: walker %d or determinant %d out of range", i, w_idx[i],
+                        det_idx[i]);
+        const int at = pos[det_idx[i]], a = P.a[at], b = P.b[at];
+        recs[i] = DetRec{w_idx[i], a, b, ctx->sp[0].str_k[a], ctx->sp[1].str_k[b]};
+    }
+    const bool fp32 = ctx->prec == MSD_MIXED;
+    if (fp32 && (rc = prepare_mixed(ctx, st))) return rc;
+    if (fp32 && exact_ref_on(ctx) && (rc = prepare_exact_ref(ctx, st))) return rc;
+    Staged in;
+    if ((rc = stage_inputs(ctx, n_w, phi_a, phi_b, st, in))) return rc;
+    Out o_e;
+    if ((rc = stage_output(ctx, "out_edet", e_det, n_pairs, o_e))) return rc;
+    void* d_rec;
+    if ((rc = arena_get(ctx, "det_rec", sizeof(DetRec) * n_pairs, &d_rec))) return rc;
+    CK(cudaMemcpyAsync(d_rec, recs.data(), sizeof(DetRec) * n_pairs, cudaMemcpyHostToDevice, st));
+    const int nR = weights_blocks(tables(ctx->sp[0], 1));
+    const size_t per = overlap_bytes_per_walker(ctx, true, nR) + en_bytes_per_walker(ctx, fp32);
+    const int cap = chunk_for(ctx, per, n_w);
+    Chunk c;
+    EnWork E;
+    if ((rc = chunk_alloc(ctx, cap, true, nR, c))) return rc;
+    if ((rc = en_alloc(ctx, cap, fp32, E))) return rc;
+    for (int w0 = 0; w0 < n_w; w0 += cap) {
+        const int nw = std::min(cap, n_w - w0);
+        if ((rc = run_overlap_part(ctx, in, w0, nw, cap, c, true, fp32, st))) return rc;
+        if ((rc = en_chunk(ctx, c, E, w0, nw, cap, fp32, nullptr, nullptr, st, true))) return rc;
+        launch_det_energy(n_pairs, (const DetRec*)d_rec, w0, nw, tables(ctx->sp[0], cap), tables(ctx->sp[1], cap),
+                          c.B[0], c.B[1], E.Kaa, E.Kbb, E.Kab, E.Y[0], E.Y[1], (const double2*)E.scal,
+                          (const double2*)E.e1[0], (const double2*)E.e1[1], ctx->e0, fp32, o_e.dev, st);
+        CKLAUNCH();
+    }
+    rc = finish(ctx, st, {&o_e}, in.host_any);
+    CK(cudaStreamSynchronize(st));   // recs is a host vector
+    return rc;
 }
 
 // ------------------------------------------------------------ propagation
@@ -1502,6 +1714,12 @@ int msd_local_energy(msd_ctx* ctx, int n_w, const double* phi_a, const double* p
     return evaluate(ctx, n_w, phi_a, phi_b, ovlp, nullptr, e_loc, stream);
 }
 
+int msd_det_energies(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b, int n_pairs,
+                     const int32_t* w_idx, const int32_t* det_idx, double* e_det, void* stream)
+{
+    return det_energies(ctx, n_w, phi_a, phi_b, n_pairs, w_idx, det_idx, e_det, stream);
+}
+
 int msd_evaluate(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b, double* ovlp,
                  double* vbias, double* e_loc, void* stream)
 {
@@ -1600,6 +1818,7 @@ int msd_info(const msd_ctx* ctx, int key, long long* value)
         break;
     }
     case MSD_INFO_WALKER_CHUNK: *value = ctx->chunk; break;
+    case MSD_INFO_EXACT_REFERENCE: *value = exact_ref_on(ctx) ? 1 : 0; break;
     default: return MSD_ERR_ARG;
     }
     return MSD_OK;
@@ -1658,6 +1877,17 @@ int msd_set_pair_form(msd_ctx* ctx, int form)
     if (ctx->pair_form != form) {
         ctx->pair_form = form;
         ctx->chunk = 0;   // the partial-sum slots per walker may change
+        ++ctx->gen;
+    }
+    return MSD_OK;
+}
+
+int msd_set_exact_reference(msd_ctx* ctx, int on)
+{
+    if (!ctx) return MSD_ERR_ARG;
+    if (ctx->exact_ref != (on != 0)) {
+        ctx->exact_ref = on != 0;
+        ctx->chunk = 0;   // workspace sizes per walker change
         ++ctx->gen;
     }
     return MSD_OK;

@@ -21,15 +21,15 @@ _ERRORS = {-1: "MSD_ERR_ARG", -2: "MSD_ERR_SHAPE", -3: "MSD_ERR_CUDA", -4: "MSD_
            -5: "MSD_ERR_REF_SINGULAR", -6: "MSD_ERR_STATE", -7: "MSD_ERR_NOMEM"}
 EXPORTS = ["msd_create", "msd_destroy", "msd_last_error", "msd_set_hamiltonian", "msd_set_trial",
            "msd_set_precision", "msd_overlap", "msd_det_ratios", "msd_force_bias",
-           "msd_local_energy", "msd_evaluate", "msd_info", "msd_set_timing", "msd_reset_stats",
-           "msd_kernel_count", "msd_kernel_stat", "msd_set_workspace_limit", "msd_set_sync", "msd_set_fused", "msd_set_pair_form", "msd_propagate",
+           "msd_local_energy", "msd_evaluate", "msd_det_energies", "msd_info", "msd_set_timing", "msd_reset_stats",
+           "msd_kernel_count", "msd_kernel_stat", "msd_set_workspace_limit", "msd_set_sync", "msd_set_fused", "msd_set_pair_form", "msd_set_exact_reference", "msd_propagate",
            "msd_launch_count", "msd_overlap_noalloc", "msd_batch_create", "msd_batch_destroy",
            "msd_batch_last_error", "msd_batch_evaluate", "msd_batch_autotune", "msd_batch_config",
            "msd_batch_set_config", "msd_batch_graph_ready", "msd_batch_graph_kernels", "msd_features", "msd_features_rows",
            "msd_mlp_create", "msd_mlp_destroy", "msd_mlp_last_error", "msd_mlp_param_count",
            "msd_mlp_set_params", "msd_mlp_get_params", "msd_mlp_forward", "msd_mlp_grad", "msd_mlp_adam_step"]
 INFO = {"n_det": 1, "n_chol": 2, "n_strings_a": 3, "n_strings_b": 4, "n_holes_a": 5,
-        "n_parts_a": 6, "n_holes_b": 7, "n_parts_b": 8, "workspace_bytes": 9, "walker_chunk": 10}
+        "n_parts_a": 6, "n_holes_b": 7, "n_parts_b": 8, "workspace_bytes": 9, "walker_chunk": 10, "exact_reference": 11}
 
 
 class MSDError(RuntimeError):
@@ -68,6 +68,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.msd_set_sync.argtypes = [vp, ci]
     lib.msd_set_fused.argtypes = [vp, ci]
     lib.msd_set_pair_form.argtypes = [vp, ci]
+    lib.msd_set_exact_reference.argtypes = [vp, ci]
+    lib.msd_det_energies.argtypes = [vp, ci, vp, vp, ci, vp, vp, vp, vp]
     lib.msd_propagate.argtypes = [vp, ci, vp, vp, vp, vp, ctypes.c_double, ci, ci, vp, vp]
     lib.msd_launch_count.argtypes = []
     for f in EXPORTS:
@@ -281,6 +283,24 @@ class Context:
         self._check(_lib.msd_evaluate(self._h, n_w, _ptr(phi_a), _ptr(phi_b), _ptr(o), _ptr(v), _ptr(e),
                                       self._stream(phi_a, stream)))
         return o, v, e
+
+    def det_energies(self, phi_a, phi_b, w_idx, det_idx, stream=None):
+        """E_I of the sampled (walker, determinant) pairs (w_idx[i], det_idx[i])
+        from the energy path's own intermediates (complex, like phi_a)."""
+        n_w = self._walkers(phi_a, phi_b)
+        wi = np.ascontiguousarray(w_idx, np.int32)
+        di = np.ascontiguousarray(det_idx, np.int32)
+        assert wi.shape == di.shape and wi.ndim == 1
+        out = self._alloc(phi_a, (wi.shape[0],))
+        self._check(_lib.msd_det_energies(self._h, n_w, _ptr(phi_a), _ptr(phi_b), int(wi.shape[0]),
+                                          wi.ctypes.data_as(ctypes.c_void_p), di.ctypes.data_as(ctypes.c_void_p),
+                                          _ptr(out), self._stream(phi_a, stream)))
+        return out
+
+    def set_exact_reference(self, on: bool):
+        """Mixed precision: reference-determinant energy to FP64 accuracy
+        (default on) or from the FP32 traces."""
+        self._check(_lib.msd_set_exact_reference(self._h, int(bool(on))))
 
     # --------------------------------------------------------------- timing
     def set_timing(self, enable=True):
