@@ -32,10 +32,42 @@ if ROOT not in sys.path:
 
 METRIC = ("walker·det overlap+energy evals/s at N_det=1.2e5; mixed vs FP64 at stated error")
 UNIT = "walker*det/s"
-# GB300: 152 SMs at up to 2070 MHz; 2 FP64 and 128 FP32 FMA per SM per clock.
-FP64_ALU_GFLOPS = 152 * 2 * 2 * 2.070
-FP32_ALU_GFLOPS = 152 * 128 * 2 * 2.070
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def measure_alu_peaks(dev):
+    """FP64, FP32 (SIMT) and TF32 (tensor) rates of this GPU, measured here:
+    the best of 5 square cuBLAS GEMMs (torch.matmul, 2 n^3 flops, CUDA events
+    on the current stream) at n = 4096 (FP64) and 8192 (FP32 with TF32 off,
+    TF32), after a warm-up. Library GEMMs at these sizes run close to the
+    respective pipes' peak, as the measured BF16 peak beside them does."""
+    import torch
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    try:
+        for key, dtype, n, tf32 in (("fp64_gflops", torch.float64, 4096, False),
+                                    ("fp32_gflops", torch.float32, 8192, False),
+                                    ("tf32_gflops", torch.float32, 8192, True)):
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            a = torch.randn(n, n, dtype=dtype, device=dev)
+            b = torch.randn(n, n, dtype=dtype, device=dev)
+            c = a @ b
+            torch.cuda.synchronize(dev)
+            best = float("inf")
+            for _ in range(5):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b, out=c)
+                e1.record()
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            out[key] = 2.0 * n ** 3 / (best / 1e3) / 1e9
+            del a, b, c
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    out["how"] = "best of 5 cuBLAS GEMMs (torch.matmul): FP64 n=4096, FP32 (TF32 off) and TF32 n=8192"
+    return out
 
 
 def parse():
@@ -94,12 +126,20 @@ def barrier():
         dist.barrier()
 
 
-def load_peaks():
+def load_peaks(dev=None):
+    """HBM and BF16 peaks from MEASURED_PEAKS.json (else the fallback), plus
+    the FP64, FP32 and TF32 GEMM rates measured on `dev` now."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         with open(path) as f:
-            return json.load(f), "measured"
-    return dict(FALLBACK_PEAKS), "fallback"
+            peaks, src = json.load(f), "measured"
+    else:
+        peaks, src = dict(FALLBACK_PEAKS), "fallback"
+    if dev is not None:
+        alu = measure_alu_peaks(dev)
+        peaks.update(alu)
+        peaks["alu_how"] = alu["how"]
+    return peaks, src
 
 
 # ---------------------------------------------------------------- clocks
@@ -229,6 +269,15 @@ def algorithmic_work(s, n_w):
     # k_fepi above, runs on the FP32 pipes beside the tensor cores)
     w["tc_fepi"] = w["tc_gemm_F"]
     w["tc_gemm_vbias"] = 2.0 * 2 * Kd * G * n_w
+    # CI weights: per string and determinant containing it one complex x real
+    # multiply-add (4 flops), then r_s times the sum (6 flops); both spins
+    w["k_weights"] = sum(4.0 * s.n_det + 6.0 * float(np.sum(sp["lv"])) for sp in spins) * n_w
+    # cofactor accumulation: w_s r_s B_s added into k^2 cofactor entries per
+    # string (one complex multiply-add each, 8 flops)
+    w["k_cmat"] = sum(8.0 * float(np.sum(sp["lv"] * k ** 2)) for sp in spins) * n_w
+    # exact reference sums: the real GEMM of the 2 walker rows per spin with
+    # the constant [V | W] (N (M - N) x (N (M - N) + N_chol)), counted once
+    w["tc_ozaki"] = sum(2.0 * 2 * (sp["N"] * (M - sp["N"])) * (sp["N"] * (M - sp["N"]) + G) for sp in spins) * n_w
     return w, spins
 
 
@@ -239,7 +288,7 @@ FP64_KERNELS = {"k_ref", "k_strings", "k_weights", "k_gt", "k_onebody", "k_final
 # workload; reported only while the kernel's source file still hashes to
 # the value recorded with the capture (a changed kernel gets null).
 NCU_TRAFFIC = {
-    # profiles/k_tc_fepi_fe2s2_640w_dram.md (640 walkers, one spin per launch)
+    # 640 walkers, one spin per launch
     "tc_fepi": {"source": "paper_2406_08314_gb300/csrc/tc_fepi.cu",
                 "sha256": "e6260de6680423bd15b5e69e68cb85ded7cc48caef815774db20a0af2c5a612d",
                 "bytes_per_launch": 553659136 + 614598144, "workload": "fe2s2", "n_w": 640},
@@ -264,14 +313,17 @@ def ncu_traffic(name, workload=None, n_w=None):
 
 
 def kernel_peak(name, precision, peaks):
-    """(bound, peak GFLOP/s, source) for a kernel group."""
+    """(bound, peak GFLOP/s, source) for a kernel group, against the rates
+    measured on this GPU (measure_alu_peaks, MEASURED_PEAKS.json)."""
+    if name == "tc_ozaki":
+        return ("tensor", peaks["bf16_tflops"] * 1e3 / 15,
+                "measured bf16 burst / 15 BF16 slice products of the exact split")
     if name.startswith("tc_"):
-        tf32 = peaks["bf16_tflops_sustained"] * (1.1 / 2.25) * 1e3
-        return ("tensor", tf32 / 3,
-                "measured sustained bf16 x nominal tf32/bf16 (1.1/2.25), / 3 products of the 3xTF32 split")
+        return ("tensor", peaks["tf32_gflops"] / 3,
+                "measured TF32 GEMM / 3 products of the 3xTF32 split")
     if precision == "fp64" or name in FP64_KERNELS:
-        return ("alu", FP64_ALU_GFLOPS, "derived: 152 SMs x 2070 MHz x 2 FP64 FMA/clk/SM")
-    return ("alu", FP32_ALU_GFLOPS, "derived: 152 SMs x 2070 MHz x 128 FP32 FMA/clk/SM")
+        return ("alu", peaks["fp64_gflops"], "measured FP64 GEMM")
+    return ("alu", peaks["fp32_gflops"], "measured FP32 GEMM (TF32 off)")
 
 
 # -------------------------------------------------------------- our arm
@@ -370,6 +422,24 @@ def run_ours(args, rank, world, local):
                     "vbias_rel_max": float(np.max(dv / vscale)),
                     "ovlp_rel_max": float(do.max())}}
         ctx.set_precision(args.precision)
+        # the same walkers and trial at a chemical energy scale: the Cholesky
+        # vectors scaled so that the mean on-site Coulomb integral
+        # sum_g L_g[p][p]^2 is 1 Ha (|E_L| ~ 400 Ha at the Fe2S2 shape)
+        import copy
+        sc = copy.copy(s)
+        diag = np.einsum("gpp->gp", s.L)
+        sc.L = s.L * math.sqrt(1.0 / float(np.mean(np.sum(diag * diag, axis=0))))
+        got = {}
+        for prec in ("mixed", "fp64"):
+            cx = msd.Context(sc, prec, device=local)
+            got[prec] = cx.local_energy(da, db)
+            torch.cuda.synchronize(dev)
+            cx.close()
+        dc = (got["mixed"] - got["fp64"]).abs().cpu().numpy()
+        fp64["error_of_mixed_chemical_scale"] = {
+            "e_loc_abs_max_Ha": float(dc.max()), "e_loc_abs_median_Ha": float(np.median(dc)),
+            "e_loc_scale_Ha": float(got["fp64"].abs().mean().item()),
+            "variant": "Cholesky vectors scaled to mean (pp|pp) = 1 Ha"}
 
     # end to end through the C-ABI with host buffers (pinned)
     e2e = None
@@ -391,7 +461,7 @@ def run_ours(args, rank, world, local):
                "d2h_bytes_per_step": int(v_h.nbytes + e_h.nbytes + o_h.nbytes)}
 
     work, spins = algorithmic_work(s, n_w)
-    peaks, peak_src = load_peaks()
+    peaks, peak_src = load_peaks(dev)
     kernels = {}
     for name, (n_launch, ms) in kstats.items():
         steps = args.steps
@@ -444,6 +514,8 @@ def run_ours(args, rank, world, local):
             "fp64": fp64,
             "kernels": kernels,
             "peaks_source": peak_src,
+            "peaks": {k: peaks[k] for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained", "fp64_gflops",
+                                            "fp32_gflops", "tf32_gflops", "alu_how") if k in peaks},
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -798,22 +870,23 @@ def run_prop(args, rank, world, local):
     M = s.M
     work = {"k_gemm_V": 4.0 * M * M * G * n_w,
             "k_apply_rows": sum(2 * 4.0 * M * M * n + 6 * 8.0 * M * M * n for n in (s.n_alpha, s.n_beta)) * n_w}
-    peaks, _ = load_peaks()
+    peaks, _ = load_peaks(dev)
+    fp64_peak = peaks["fp64_gflops"]
     kernels = {}
     for name, (n_launch, ms) in kstats.items():
         entry = {"launches": n_launch, "ms_per_step": ms / args.steps,
                  "share": ms / max(1e-9, sum(v[1] for v in kstats.values()))}
         if name in work and ms > 0:
             entry["gflops"] = work[name] * args.steps / (ms / 1e3) / 1e9
-            entry["frac"] = entry["gflops"] / FP64_ALU_GFLOPS
+            entry["frac"] = entry["gflops"] / fp64_peak
         kernels[name] = entry
     dom = max(kstats.items(), key=lambda kv: kv[1][1])[0] if kstats else None
     roofline = None
     if dom is not None:
         d = kernels[dom]
-        roofline = {"kernel": dom, "bound": "alu", "achieved": d.get("gflops"), "peak": FP64_ALU_GFLOPS,
+        roofline = {"kernel": dom, "bound": "alu", "achieved": d.get("gflops"), "peak": fp64_peak,
                     "unit": "GFLOP/s", "frac": d.get("frac"), "traffic": ncu_traffic(dom, "propagate"),
-                    "peak_source": "derived: 152 SMs x 2070 MHz x 2 FP64 FMA/clk/SM"}
+                    "peak_source": "measured FP64 GEMM (" + peaks["alu_how"] + ")"}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import prop_oracle

@@ -140,6 +140,18 @@ int msd_force_bias(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi
 int msd_local_energy(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b,
                      double* e_loc, double* ovlp, void* stream);
 
+/* Mixed one-body reduced density matrix (the mixed estimator of the
+   one-particle density, the first property estimator beyond the energy,
+   Sec. IV; the quantity whose contraction with L_g is the force bias, Eq. 7):
+     rdm [n_w][2][M][M]  G_T^s[p][q] = <Psi_T|a+_ps a_qs|phi> / <Psi_T|phi>,
+                         complex, spin alpha then beta (host or device)
+   computed as the rank-k update of the reference Green's function by the
+   cofactor matrix of all determinants (Sec. III, reduce_CI). Rows outside
+   the reference orbitals and the trial's particles are zero. In mixed
+   precision the cofactor sums come from FP32 inverse minors (relative error
+   about 1e-6 of max |G_T|). */
+int msd_rdm1(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b, double* rdm, void* stream);
+
 /* Overlap, force bias and local energy in one pass: the reference inverse,
    the excitation-string minors and the CI weights are computed once and
    shared. Outputs as in msd_overlap (ovlp), msd_force_bias (vbias) and
@@ -209,6 +221,16 @@ int msd_set_sync(msd_ctx* ctx, int sync);
    does not support (2N > 128 rows per walker, tiles beyond 227 KB of shared
    memory) take the unfused path. */
 int msd_set_fused(msd_ctx* ctx, int fused);
+
+/* Budget of the device-side waits of the tensor-core kernels (a consumer
+   warp waiting for the producer's copies or products), in nanoseconds of the
+   GPU's global timer; the default is 2000000000 (about 2 s). When a wait
+   exceeds it the kernel stops its pipeline, lets its own copies and products
+   in flight complete, frees its tensor memory and returns; the call reports
+   MSD_ERR_TIMEOUT and the context stays usable. 0 makes every such wait a
+   single poll (the first wait that finds its data not yet there expires),
+   which exercises this path. */
+int msd_set_wait_budget(msd_ctx* ctx, unsigned long long ns);
 
 /* Mixed precision only: with on = 1 (the default) the reference-determinant
    part of the local energy (Sec. II A, the generalized Wick theorem for the

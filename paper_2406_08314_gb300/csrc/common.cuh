@@ -56,12 +56,21 @@ __host__ __device__ __forceinline__ float2 ffma(float2 b, float2 c, float2 a) {
 
 // Count of kernel launches made by the library (for launch accounting).
 void msd_note_launch();
+// Streaming multiprocessors of the current device (queried once per device).
+int msd_sm_count();
 
 // ------------------------------------------------------------ device state
 // Error word bits set by kernels (read back by the host after a call).
 #define MSD_DEV_ERR_SINGULAR 1u
 #define MSD_DEV_ERR_TIMEOUT  2u
 #define MSD_DEV_ERR_BOUNDS   4u
+// The error word is four 32-bit words: [0] the flags above, [1] unused,
+// [2..3] the budget of the tensor-core kernels' pipeline waits in
+// nanoseconds (one 64-bit value; about 2 s unless the caller changes it).
+#define MSD_ERR_WORDS 4
+#define MSD_WAIT_DEFAULT_NS 2000000000ull
+// Allocate and initialise an error word on the current device (0 or -1).
+int msd_err_word_alloc(unsigned** out);
 
 // Per-spin trial tables on the device.
 struct SpinTables {

@@ -606,6 +606,27 @@ void launch_gt(const SpinTables& tb, int nw, int M, const double2* Gr, const dou
     k_gt<<<grid, 256, 0, st>>>(tb, M, Gr, Cm, R, GT, ld, off, minus_ref ? 1 : 0); msd_note_launch();
 }
 
+// The mixed one-body density matrix as full M x M matrices per walker and
+// spin: rdm[w][spin][orb(x)][c] = GT[w][off + x M + c] for the rows x of G_T
+// (occ0, then the particles); the caller zeroes the other rows.
+__global__ void k_rdm_scatter(SpinTables tb, int M, const double2* __restrict__ GT, long long ld, long long off,
+                              int spin, double2* __restrict__ rdm)
+{
+    const int x = blockIdx.x, w = blockIdx.y;
+    const int orb = x < tb.N ? tb.occ0[x] : tb.part_orb[x - tb.N];
+    const double2* src = GT + (size_t)w * ld + off + (size_t)x * M;
+    double2* dst = rdm + (((size_t)w * 2 + spin) * M + orb) * M;
+    for (int c = threadIdx.x; c < M; c += blockDim.x) dst[c] = src[c];
+}
+
+void launch_rdm_scatter(const SpinTables& tb, int nw, int M, const double2* GT, long long ld, long long off, int spin,
+                        double2* rdm, cudaStream_t st)
+{
+    if (nw <= 0) return;
+    k_rdm_scatter<<<dim3(tb.N + tb.np, nw), 128, 0, st>>>(tb, M, GT, ld, off, spin, rdm);
+    msd_note_launch();
+}
+
 // <D_0|phi> = det(D0^dag phi_a) det(D0^dag phi_b) per walker.
 __global__ void k_ref_ovlp(int nw, const double2* __restrict__ O0a, const double2* __restrict__ O0b,
                            double2* __restrict__ out)

@@ -29,6 +29,8 @@ void launch_cmat(const SpinTables& ta, const SpinTables& tb, int nw, const doubl
                  const void* Ba, const void* Bb, bool fp32, double2* Cm_a, double2* Cm_b, cudaStream_t st);
 void launch_gt(const SpinTables& tb, int nw, int M, const double2* Gr, const double2* Cm,
                const double2* R, double2* GT, long long ld, long long off, bool minus_ref, cudaStream_t st);
+void launch_rdm_scatter(const SpinTables& tb, int nw, int M, const double2* GT, long long ld, long long off, int spin,
+                        double2* rdm, cudaStream_t st);
 
 // k_energy.cu
 void launch_gemm_zd(int Mr, int Nc, int K, const double2* A, long long lda, const double* B,

@@ -29,7 +29,11 @@ __device__ __forceinline__ float gelu_d(float z)
     return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
 }
 
-int grid_of(long long n) { return (int)((n + 255) / 256 < 152 * 32 ? (n + 255) / 256 : 152 * 32); }
+int grid_of(long long n)
+{
+    const long long cap = 32ll * msd_sm_count();
+    return (int)((n + 255) / 256 < cap ? (n + 255) / 256 : cap);
+}
 
 // x fp32 [B][n] -> row-major bf16 [B][n] and transposed bf16 [n][ldt]
 __global__ void k_in_bf16(int B, int n, const float* __restrict__ x, bf16* __restrict__ xb, bf16* __restrict__ xt,
@@ -404,7 +408,7 @@ int msd_mlp_create(msd_mlp** out, int n_in, int width, int device)
               cudaMalloc(&m->g, sizeof(float) * off) == cudaSuccess &&
               cudaMalloc(&m->m, sizeof(float) * off) == cudaSuccess &&
               cudaMalloc(&m->v, sizeof(float) * off) == cudaSuccess &&
-              cudaMalloc(&m->d_err, sizeof(unsigned)) == cudaSuccess;
+              msd_err_word_alloc(&m->d_err) == 0;
     for (int l = 0; ok && l < 3; ++l)
         ok = cudaMalloc(&m->wb[l], sizeof(bf16) * width * ins[l]) == cudaSuccess &&
              cudaMalloc(&m->wt[l], sizeof(bf16) * width * ins[l]) == cudaSuccess;
@@ -413,7 +417,6 @@ int msd_mlp_create(msd_mlp** out, int n_in, int width, int device)
     cudaMemset(m->g, 0, sizeof(float) * off);
     cudaMemset(m->m, 0, sizeof(float) * off);
     cudaMemset(m->v, 0, sizeof(float) * off);
-    cudaMemset(m->d_err, 0, sizeof(unsigned));
     *out = m;
     return MSD_OK;
 }

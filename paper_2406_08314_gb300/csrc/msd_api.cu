@@ -18,6 +18,34 @@
 static std::atomic<long long> g_launches{0};
 void msd_note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+int msd_err_word_alloc(unsigned** out)
+{
+    *out = nullptr;
+    unsigned w[MSD_ERR_WORDS] = {0, 0, 0, 0};
+    const unsigned long long budget = MSD_WAIT_DEFAULT_NS;
+    std::memcpy(&w[2], &budget, sizeof budget);
+    if (cudaMalloc((void**)out, sizeof w) != cudaSuccess) { cudaGetLastError(); *out = nullptr; return -1; }
+    if (cudaMemcpy(*out, w, sizeof w, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(*out);
+        *out = nullptr;
+        return -1;
+    }
+    return 0;
+}
+
+int msd_sm_count()
+{
+    static std::atomic<int> cache[256];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return 1;
+    int n = cache[dev].load(std::memory_order_relaxed);
+    if (n <= 0) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+        cache[dev].store(n, std::memory_order_relaxed);
+    }
+    return n;
+}
+
 namespace {
 
 std::string g_create_error;
@@ -1253,6 +1281,56 @@ int evaluate(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b, do
     return evaluate_impl(ctx, n_w, phi_a, phi_b, ovlp, vbias, e_loc, stream, nullptr);
 }
 
+// Mixed one-body density matrix G_T per walker and spin: the force-bias
+// path up to G_T (cofactor accumulation, rank-k update), written out as full
+// matrices.
+int rdm1(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b, double* rdm, void* stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = begin_call(ctx, n_w, phi_a, phi_b, st);
+    if (rc) return rc;
+    if (n_w == 0) return MSD_OK;
+    if (!rdm) return fail(ctx, MSD_ERR_ARG, "no output");
+    const bool fp32 = ctx->prec == MSD_MIXED;
+    const int M = ctx->M;
+    Staged in;
+    if ((rc = stage_inputs(ctx, n_w, phi_a, phi_b, st, in))) return rc;
+    Out o_r;
+    if ((rc = stage_output(ctx, "out_rdm", rdm, (size_t)n_w * 2 * M * M, o_r))) return rc;
+    CK(cudaMemsetAsync(o_r.dev, 0, o_r.bytes, st));
+    const int nR = weights_blocks(tables(ctx->sp[0], 1));
+    const int cap = chunk_for(ctx, overlap_bytes_per_walker(ctx, true, nR) + fb_bytes_per_walker(ctx, false), n_w);
+    Chunk c;
+    FbWork f;
+    if ((rc = chunk_alloc(ctx, cap, true, nR, c))) return rc;
+    if ((rc = fb_alloc(ctx, cap, false, f))) return rc;
+    const TimerHook& th = ctx->hook;
+    for (int w0 = 0; w0 < n_w; w0 += cap) {
+        const int nw = std::min(cap, n_w - w0);
+        if ((rc = run_overlap_part(ctx, in, w0, nw, cap, c, true, fp32, st))) return rc;
+        th.begin("k_sum_slots", st);
+        launch_sum_slots(nw, c.part, c.nslot, 0, c.nR, (double2*)f.Rs, c.O0[0], c.O0[1], nullptr, st);
+        th.end(st);
+        th.begin("k_cmat", st);
+        launch_cmat(tables(ctx->sp[0], cap), tables(ctx->sp[1], cap), nw, c.wts[0], c.wts[1], c.B[0], c.B[1], fp32,
+                    (double2*)f.Cm[0], (double2*)f.Cm[1], st);
+        th.end(st);
+        long long off = 0;
+        for (int s = 0; s < 2; ++s) {
+            const SpinTables T = tables(ctx->sp[s], cap);
+            th.begin("k_gt", st);
+            launch_gt(T, nw, M, c.Gr[s], (double2*)f.Cm[s], (double2*)f.Rs, (double2*)f.GT, ctx->Kd, off, false, st);
+            th.end(st);
+            th.begin("k_rdm_scatter", st);
+            launch_rdm_scatter(T, nw, M, (const double2*)f.GT, ctx->Kd, off, s, o_r.dev + (size_t)w0 * 2 * M * M, st);
+            th.end(st);
+            off += (long long)(T.N + T.np) * M;
+        }
+        CKLAUNCH();
+    }
+    return finish(ctx, st, {&o_r}, in.host_any);
+}
+
 // E_I for sampled (walker, determinant) pairs: the energy path up to the
 // per-walker Gram matrices, then one thread per pair.
 int det_energies(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b, int n_pairs,
@@ -1489,13 +1567,13 @@ int msd_create(msd_ctx** out, int M, int n_alpha, int n_beta, int precision, int
     if (cudaSetDevice(device) != cudaSuccess) return fail(nullptr, MSD_ERR_CUDA, "cudaSetDevice failed");
     ctx = new msd_ctx();
     ctx->device = device; ctx->M = M; ctx->n[0] = n_alpha; ctx->n[1] = n_beta; ctx->prec = precision;
-    if (cudaMalloc(&ctx->d_err, sizeof(unsigned)) != cudaSuccess ||
+    if (msd_err_word_alloc(&ctx->d_err) != 0 ||
         cudaMallocHost(&ctx->h_err, sizeof(unsigned)) != cudaSuccess) {
         cudaGetLastError();
+        cudaFree(ctx->d_err);
         delete ctx;
         return fail(nullptr, MSD_ERR_NOMEM, "allocation failed");
     }
-    cudaMemset(ctx->d_err, 0, sizeof(unsigned));
     ctx->hook.self = ctx;
     *out = ctx;
     return MSD_OK;
@@ -1714,6 +1792,11 @@ int msd_local_energy(msd_ctx* ctx, int n_w, const double* phi_a, const double* p
     return evaluate(ctx, n_w, phi_a, phi_b, ovlp, nullptr, e_loc, stream);
 }
 
+int msd_rdm1(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b, double* rdm, void* stream)
+{
+    return rdm1(ctx, n_w, phi_a, phi_b, rdm, stream);
+}
+
 int msd_det_energies(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b, int n_pairs,
                      const int32_t* w_idx, const int32_t* det_idx, double* e_det, void* stream)
 {
@@ -1882,6 +1965,14 @@ int msd_set_pair_form(msd_ctx* ctx, int form)
     return MSD_OK;
 }
 
+int msd_set_wait_budget(msd_ctx* ctx, unsigned long long ns)
+{
+    if (!ctx) return MSD_ERR_ARG;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaMemcpy(ctx->d_err + 2, &ns, sizeof ns, cudaMemcpyHostToDevice));
+    return MSD_OK;
+}
+
 int msd_set_exact_reference(msd_ctx* ctx, int on)
 {
     if (!ctx) return MSD_ERR_ARG;
@@ -2036,7 +2127,7 @@ extern "C" int msd_overlap_noalloc(msd_ctx* ctx, int n_w, const double* phi_a, c
 struct msd_batch {
     std::vector<msd_ctx*> ctx;
     int device = 0;
-    int n_sm = 152;
+    int n_sm = 1;                 // set from the device at creation
     std::string err;
     cudaStream_t cap = nullptr;
     cudaGraphExec_t exec = nullptr;

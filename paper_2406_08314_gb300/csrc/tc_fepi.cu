@@ -190,6 +190,7 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
     __shared__ int fail;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nkb = (a.K + 15) / 16;
+    const uint64_t wb = wait_budget(a.err);
 
     for (int e = threadIdx.x; e < X; e += blockDim.x) oe[e] = (e % np) * RB + a.tb.hole_pos[e / np];
     if (threadIdx.x == 0) {
@@ -218,7 +219,7 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
                 const int m0 = (tile % a.n_rt) * 128, n0 = (tile / a.n_rt) * a.GPT * NCf;
                 for (int kb = 0; kb < nkb; ++kb, ++kbg) {
                     const int s = kbg % FE_STAGES;
-                    if (!mbar_wait(&empty_bar[s], ((kbg / FE_STAGES) & 1) ^ 1) || *vfail) {
+                    if (!mbar_wait(&empty_bar[s], ((kbg / FE_STAGES) & 1) ^ 1, wb) || *vfail) {
                         *vfail = 1;
                         atomicOr(a.err, MSD_DEV_ERR_TIMEOUT);
                         break;
@@ -234,7 +235,7 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
             }
             // the copies issued last must land before the CTA may exit
             for (int k = kbg - FE_STAGES < 0 ? 0 : kbg - FE_STAGES; k < kbg; ++k)
-                mbar_wait(&full_bar[k % FE_STAGES], (k / FE_STAGES) & 1);
+                mbar_drain(&full_bar[k % FE_STAGES], (k / FE_STAGES) & 1);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -243,7 +244,7 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
             int kbg = 0, it = 0;
             for (int tile = blockIdx.x; tile < a.n_tiles && !*vfail; tile += gridDim.x, ++it) {
                 const int b = it & 1;
-                if (!mbar_wait(&tempty[b], ((it >> 1) & 1) ^ 1)) {
+                if (!mbar_wait(&tempty[b], ((it >> 1) & 1) ^ 1, wb)) {
                     *vfail = 1;
                     atomicOr(a.err, MSD_DEV_ERR_TIMEOUT);
                     break;
@@ -253,7 +254,7 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
                 bool ok = true;
                 for (int kb = 0; kb < nkb; ++kb, ++kbg) {
                     const int s = kbg % FE_STAGES;
-                    if (!mbar_wait(&full_bar[s], (kbg / FE_STAGES) & 1) || *vfail) { ok = false; break; }
+                    if (!mbar_wait(&full_bar[s], (kbg / FE_STAGES) & 1, wb) || *vfail) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t sa = su32(smem + (size_t)s * STAGE_BYTES);
                     const int nk = min(2, (a.K - kb * 16) / 8);
@@ -277,7 +278,7 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
             }
             // every product issued by this thread completes before TMEM is freed
             mma_commit(&drain_bar);
-            mbar_wait(&drain_bar, 0);
+            mbar_drain(&drain_bar, 0);
         }
     } else {
         // ---------------------------------------------------- epilogue
@@ -342,7 +343,7 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
                 gbr[e] = re;
                 gbi[e] = im;
             }
-            bool ok = mbar_wait(&tfull[b], (it >> 1) & 1);
+            bool ok = mbar_wait(&tfull[b], (it >> 1) & 1, wb);
             ok = bar_and(1, FE_EPI, ok && !*vfail);
             if (!ok) {
                 if (et == 0) { *vfail = 1; atomicOr(a.err, MSD_DEV_ERR_TIMEOUT); }

@@ -57,6 +57,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
     __shared__ int fail;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const uint64_t wb = wait_budget(err);
     // k-blocks [kb0, kb1) of this split
     const int nkb_all = K / BK;
     const int kb0 = (int)((long long)nkb_all * blockIdx.z / gridDim.z);
@@ -86,7 +87,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
         for (int kb = 0; kb < nkb; ++kb) {
             const int s = kb % STAGES;
             const uint32_t ph = (kb / STAGES) & 1;
-            if (!mbar_wait(&empty_bar[s], ph ^ 1)) { fail = 1; atomicOr(err, MSD_DEV_ERR_TIMEOUT); break; }
+            if (!mbar_wait(&empty_bar[s], ph ^ 1, wb)) { fail = 1; atomicOr(err, MSD_DEV_ERR_TIMEOUT); break; }
             uint8_t* st = smem + (size_t)s * Cfg::STAGE_BYTES;
             mbar_expect_tx(&full_bar[s], Cfg::STAGE_BYTES);
             const int kx = (kb0 + kb) * BK;
@@ -98,18 +99,17 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
             }
             issued = kb + 1;
         }
-        if (fail) {
-            // drain: the loads already issued must land before the CTA exits
-            for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb)
-                mbar_wait(&full_bar[kb % STAGES], (kb / STAGES) & 1);
-        }
+        // the loads issued last must land before the CTA may exit (the MMA
+        // warp may have given up on them)
+        for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb)
+            mbar_drain(&full_bar[kb % STAGES], (kb / STAGES) & 1);
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
         constexpr uint32_t idesc = SPLIT ? idesc_tf32(BM, BN) : idesc_bf16(BM, BN);
         for (int kb = 0; kb < nkb; ++kb) {
             const int s = kb % STAGES;
             const uint32_t ph = (kb / STAGES) & 1;
-            if (!mbar_wait(&full_bar[s], ph)) { fail = 1; atomicOr(err, MSD_DEV_ERR_TIMEOUT); break; }
+            if (!mbar_wait(&full_bar[s], ph, wb)) { fail = 1; atomicOr(err, MSD_DEV_ERR_TIMEOUT); break; }
             tc_fence_after();
             const uint32_t sa = su32(smem + (size_t)s * Cfg::STAGE_BYTES);
 #pragma unroll
@@ -129,9 +129,11 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
             mma_commit(&empty_bar[s]);
         }
         mma_commit(&done_bar);
+        // every product issued here completes before TMEM may be freed
+        mbar_drain(&done_bar, 0);
     }
     __syncwarp();
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(&done_bar, 0) ? 1 : 0);
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(&done_bar, 0, wb) ? 1 : 0);
     tc_fence_after();
     if (ok && !fail) {
         const int row = m0 + warp * 32 + lane;
@@ -308,7 +310,11 @@ __global__ void k_pack_complex(int nw, int n, const float* __restrict__ C, long 
     }
 }
 
-int grid_for(long long n) { return (int)((n + 255) / 256 < 152 * 16 ? (n + 255) / 256 : 152 * 16); }
+int grid_for(long long n)
+{
+    const long long cap = 16ll * msd_sm_count();
+    return (int)((n + 255) / 256 < cap ? (n + 255) / 256 : cap);
+}
 
 }  // namespace
 

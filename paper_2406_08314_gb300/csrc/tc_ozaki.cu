@@ -106,6 +106,7 @@ k_tc_ozaki(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUten
     const int m0 = blockIdx.x * OZ_BM, n0 = blockIdx.y * OZ_BN;
     const int nkb = a.Kp / OZ_BK;
     const int nch = (nkb + OZ_KCH_KB - 1) / OZ_KCH_KB;
+    const uint64_t wb = wait_budget(a.err);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < OZ_STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
@@ -132,7 +133,7 @@ k_tc_ozaki(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUten
             int kb = 0;
             for (; kb < nkb; ++kb) {
                 const int s = kb % OZ_STAGES;
-                if (!mbar_wait(&empty_bar[s], ((kb / OZ_STAGES) & 1) ^ 1) || *vfail) {
+                if (!mbar_wait(&empty_bar[s], ((kb / OZ_STAGES) & 1) ^ 1, wb) || *vfail) {
                     *vfail = 1;
                     atomicOr(a.err, MSD_DEV_ERR_TIMEOUT);
                     break;
@@ -148,7 +149,7 @@ k_tc_ozaki(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUten
             }
             // the copies issued last must land before the CTA may exit
             for (int k = kb - OZ_STAGES < 0 ? 0 : kb - OZ_STAGES; k < kb; ++k)
-                mbar_wait(&full_bar[k % OZ_STAGES], (k / OZ_STAGES) & 1);
+                mbar_drain(&full_bar[k % OZ_STAGES], (k / OZ_STAGES) & 1);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -157,12 +158,12 @@ k_tc_ozaki(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUten
             bool ok = true;
             for (int ch = 0; ch < nch && ok; ++ch) {
                 // the epilogue has taken the previous chunk out of TMEM
-                if (ch > 0 && !mbar_wait(&tempty, (ch - 1) & 1)) { ok = false; break; }
+                if (ch > 0 && !mbar_wait(&tempty, (ch - 1) & 1, wb)) { ok = false; break; }
                 tc_fence_after();
                 const int kb0 = ch * OZ_KCH_KB, kb1 = min(nkb, kb0 + OZ_KCH_KB);
                 for (int kb = kb0; kb < kb1; ++kb) {
                     const int s = kb % OZ_STAGES;
-                    if (!mbar_wait(&full_bar[s], (kb / OZ_STAGES) & 1) || *vfail) { ok = false; break; }
+                    if (!mbar_wait(&full_bar[s], (kb / OZ_STAGES) & 1, wb) || *vfail) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t sa = su32(smem + (size_t)s * OZ_STAGE);
                     const uint32_t sb = sa + OZ_S * OZ_A_SL;
@@ -199,7 +200,7 @@ k_tc_ozaki(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUten
             }
             // every product issued by this thread completes before TMEM is freed
             mma_commit(&drain_bar);
-            mbar_wait(&drain_bar, 0);
+            mbar_drain(&drain_bar, 0);
         }
     } else {
         // -------------------------------------------------------- epilogue
@@ -211,7 +212,7 @@ k_tc_ozaki(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUten
         for (int i = 0; i < OZ_HALF; ++i) acc[i] = 0;
         bool ok = true;
         for (int ch = 0; ch < nch; ++ch) {
-            const bool got = mbar_wait(&tfull, ch & 1) && !*vfail;
+            const bool got = mbar_wait(&tfull, ch & 1, wb) && !*vfail;
             if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
             tc_fence_after();
 #pragma unroll

@@ -58,14 +58,33 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t pari
     return ok != 0;
 }
 
-// Wait for the phase of the given parity to complete, for at most ~2 s.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+// Wait for the phase of the given parity to complete, for at most limit_ns
+// nanoseconds of %globaltimer; 0 makes it a single poll. Returns false when
+// the limit expires.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns)
 {
     if (mbar_try_wait(bar, parity)) return true;
+    if (limit_ns == 0) return false;
     const uint64_t t0 = global_ns();
-    while (!mbar_try_wait_sleep(bar, parity, 100000u))
-        if (global_ns() - t0 > 2000000000ull) return false;
-    return true;
+    for (;;) {
+        if (mbar_try_wait_sleep(bar, parity, 100000u)) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// Wait for this CTA's own copies or products already in flight, which
+// complete by themselves: a fixed limit of about 2 s, whatever the budget of
+// the pipeline waits.
+__device__ __forceinline__ bool mbar_drain(uint64_t* bar, uint32_t parity)
+{
+    return mbar_wait(bar, parity, 2000000000ull);
+}
+
+// The budget of the pipeline waits (nanoseconds), stored by the host beside
+// the error word: err[2..3] as one 64-bit value.
+__device__ __forceinline__ uint64_t wait_budget(const unsigned* err)
+{
+    return *reinterpret_cast<const volatile unsigned long long*>(err + 2);
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y)

@@ -21,8 +21,8 @@ _ERRORS = {-1: "MSD_ERR_ARG", -2: "MSD_ERR_SHAPE", -3: "MSD_ERR_CUDA", -4: "MSD_
            -5: "MSD_ERR_REF_SINGULAR", -6: "MSD_ERR_STATE", -7: "MSD_ERR_NOMEM"}
 EXPORTS = ["msd_create", "msd_destroy", "msd_last_error", "msd_set_hamiltonian", "msd_set_trial",
            "msd_set_precision", "msd_overlap", "msd_det_ratios", "msd_force_bias",
-           "msd_local_energy", "msd_evaluate", "msd_det_energies", "msd_info", "msd_set_timing", "msd_reset_stats",
-           "msd_kernel_count", "msd_kernel_stat", "msd_set_workspace_limit", "msd_set_sync", "msd_set_fused", "msd_set_pair_form", "msd_set_exact_reference", "msd_propagate",
+           "msd_local_energy", "msd_evaluate", "msd_det_energies", "msd_rdm1", "msd_info", "msd_set_timing", "msd_reset_stats",
+           "msd_kernel_count", "msd_kernel_stat", "msd_set_workspace_limit", "msd_set_sync", "msd_set_fused", "msd_set_pair_form", "msd_set_exact_reference", "msd_set_wait_budget", "msd_propagate",
            "msd_launch_count", "msd_overlap_noalloc", "msd_batch_create", "msd_batch_destroy",
            "msd_batch_last_error", "msd_batch_evaluate", "msd_batch_autotune", "msd_batch_config",
            "msd_batch_set_config", "msd_batch_graph_ready", "msd_batch_graph_kernels", "msd_features", "msd_features_rows",
@@ -69,7 +69,9 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.msd_set_fused.argtypes = [vp, ci]
     lib.msd_set_pair_form.argtypes = [vp, ci]
     lib.msd_set_exact_reference.argtypes = [vp, ci]
+    lib.msd_set_wait_budget.argtypes = [vp, ctypes.c_ulonglong]
     lib.msd_det_energies.argtypes = [vp, ci, vp, vp, ci, vp, vp, vp, vp]
+    lib.msd_rdm1.argtypes = [vp, ci, vp, vp, vp, vp]
     lib.msd_propagate.argtypes = [vp, ci, vp, vp, vp, vp, ctypes.c_double, ci, ci, vp, vp]
     lib.msd_launch_count.argtypes = []
     for f in EXPORTS:
@@ -284,6 +286,13 @@ class Context:
                                       self._stream(phi_a, stream)))
         return o, v, e
 
+    def rdm1(self, phi_a, phi_b, stream=None, out=None):
+        """Mixed one-body density matrices G_T [n_w][2][M][M] (complex)."""
+        n_w = self._walkers(phi_a, phi_b)
+        r = out if out is not None else self._alloc(phi_a, (n_w, 2, self.M, self.M))
+        self._check(_lib.msd_rdm1(self._h, n_w, _ptr(phi_a), _ptr(phi_b), _ptr(r), self._stream(phi_a, stream)))
+        return r
+
     def det_energies(self, phi_a, phi_b, w_idx, det_idx, stream=None):
         """E_I of the sampled (walker, determinant) pairs (w_idx[i], det_idx[i])
         from the energy path's own intermediates (complex, like phi_a)."""
@@ -296,6 +305,11 @@ class Context:
                                           wi.ctypes.data_as(ctypes.c_void_p), di.ctypes.data_as(ctypes.c_void_p),
                                           _ptr(out), self._stream(phi_a, stream)))
         return out
+
+    def set_wait_budget(self, ns: int):
+        """Budget (ns) of the tensor-core kernels' device-side waits;
+        2_000_000_000 by default, 0 = a single poll."""
+        self._check(_lib.msd_set_wait_budget(self._h, int(ns)))
 
     def set_exact_reference(self, on: bool):
         """Mixed precision: reference-determinant energy to FP64 accuracy
