@@ -112,9 +112,10 @@ int tc_fepi_fused(const SpinTables& tb, const TcFepiPlan& p, int nw, int M, int 
 
 // tc_ozaki.cu: the reference-determinant Cholesky sums of the mixed local
 // energy in FP64 accuracy (exact-integer BF16 slices on the tensor cores).
-// Constant operand of one spin: B = [V | W]^T sliced, NB = N Kv + G rows.
+// Constant operand of one spin: B = [V | 0 | W]^T sliced, V's N Kv rows padded
+// with zero rows to a whole number of column tiles (NVp), NB = NVp + G rows.
 struct OzConst {
-    int N = 0, Kv = 0, G = 0, NK = 0, NB = 0, NBp = 0, Kp = 0;
+    int N = 0, Kv = 0, G = 0, NK = 0, NVp = 0, NB = 0, NBp = 0, Kp = 0;   // V rows padded to NVp
     void* Bs = nullptr;   // [OZ_S][NBp][Kp] BF16
     int* eb = nullptr;    // [NBp] row exponents
 };
@@ -132,7 +133,8 @@ struct RefSpin {
 size_t oz_const_bytes(int N, int Kv, int G);
 int oz_rows_padded(int nrow);
 int oz_k_padded(int NK);
-int oz_parts(int NB);
+int oz_parts(int NB);                // partial-sum rows of a constant operand with NB rows
+int oz_parts_for(int NK, int G);     // the same from N (M - N) and n_chol
 int oz_slices();
 // d_XT: [N Kv][G] FP64, XT[r N + l][g] = L_g[v_r][o_l]. Allocates out's arrays.
 int oz_prepare_const(int N, int Kv, int G, const double* d_XT, OzConst& out, cudaStream_t st);

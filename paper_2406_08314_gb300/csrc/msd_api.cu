@@ -1015,7 +1015,7 @@ size_t en_bytes_per_walker(msd_ctx* ctx, bool fp32)
         for (int s = 0; s < 2; ++s) kp = std::max(kp, oz_k_padded(T1[s].N * (ctx->M - T1[s].N)));
         b += (size_t)2 * oz_slices() * kp * 2 + 2 * sizeof(int);
         for (int s = 0; s < 2; ++s)
-            b += (size_t)2 * oz_parts(T1[s].N * (ctx->M - T1[s].N) + G) * sizeof(double2) + 2 * sizeof(double) * G;
+            b += (size_t)2 * oz_parts_for(T1[s].N * (ctx->M - T1[s].N), G) * sizeof(double2) + 2 * sizeof(double) * G;
     }
     if (fp32) {
         size_t f = 0, a = 0;
@@ -1075,8 +1075,8 @@ int en_alloc(msd_ctx* ctx, int cap, bool fp32, EnWork& E)
         static const char* np_[2] = {"oz_part_a", "oz_part_b"};
         static const char* nt_[2] = {"oz_t1_a", "oz_t1_b"};
         for (int s = 0; s < 2; ++s) {
-            const int NB = T1[s].N * (ctx->M - T1[s].N) + G;
-            if ((rc = arena_get(ctx, np_[s], sizeof(double2) * oz_parts(NB) * Mpad, &E.ozP[s]))) return rc;
+            const int nparts = oz_parts_for(T1[s].N * (ctx->M - T1[s].N), G);
+            if ((rc = arena_get(ctx, np_[s], sizeof(double2) * nparts * Mpad, &E.ozP[s]))) return rc;
             if ((rc = arena_get(ctx, nt_[s], sizeof(double) * 2 * cap * (size_t)G, &E.ozT[s]))) return rc;
         }
     }

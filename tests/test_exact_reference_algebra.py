@@ -168,3 +168,38 @@ def test_slice_product_accuracy(K, seed):
     # far better than an FP32 product with FP32 accumulation
     f32 = (A.astype(np.float32) @ B.T.astype(np.float32)).astype(np.float64)
     assert np.max(np.abs(got - want)) < 1e-3 * np.max(np.abs(f32 - want))
+
+
+def test_symmetric_tile_schedule():
+    """The quadratic form over the symmetric V from column tiles of 96 that
+    contract only their diagonal block (once) and the blocks after it
+    (twice), with V's rows padded with zeros to a whole number of tiles so
+    that no tile mixes V and W columns; a W tile takes the full range."""
+    rng = np.random.default_rng(7)
+    n, g, tile = 300, 40, 96
+    X = rng.standard_normal((n, n))
+    V = X + X.T
+    W = rng.standard_normal((n, g))
+    u = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    npad = -(-n // tile) * tile
+    Vp = np.zeros((npad, npad)); Vp[:n, :n] = V
+    up = np.zeros(npad, complex); up[:n] = u
+    total = 0
+    for n0 in range(0, npad, tile):
+        cols = slice(n0, n0 + tile)
+        diag = up[cols] @ Vp[cols, cols]
+        later = up[n0 + tile:] @ Vp[n0 + tile:, cols]
+        total += (diag + 2 * later) @ up[cols]
+    assert abs(total - u @ V @ u) <= 1e-9 * abs(u @ V @ u)
+    t1 = u @ W                          # the W tiles: full range, no doubling
+    assert np.allclose(up[:n] @ W, t1)
+    # the mistake this layout avoids: a tile holding V and W columns with the
+    # full range counts its V columns' earlier rows a third time
+    bad = 0
+    for n0 in range(0, n, tile):
+        cols = slice(n0, min(n, n0 + tile))
+        if n0 + tile <= n:
+            bad += (u[cols] @ V[cols, cols] + 2 * u[n0 + tile:] @ V[n0 + tile:, cols]) @ u[cols]
+        else:
+            bad += (u @ V[:, cols]) @ u[cols]
+    assert abs(bad - u @ V @ u) > 1e-6 * abs(u @ V @ u)
