@@ -247,6 +247,16 @@ int msd_set_wait_budget(msd_ctx* ctx, unsigned long long ns);
    spins with N (M - N) above 16384 always take the FP32 traces. */
 int msd_set_exact_reference(msd_ctx* ctx, int on);
 
+/* Mixed precision only: with on = 1 the Gram matrices of the energy's Gram
+   form, K^{st} = sum_g Lambda^s_g (x) Lambda^t_g over the Cholesky vectors,
+   are formed on the tensor cores (a three-way TF32 split of both operands,
+   six products, FP32 accumulation in tensor memory) when 2 n_h n_p <= 256 per
+   spin; with on = 0 (the default), or larger active blocks, by FP32 FMAs.
+   On the iron-sulfur shape the tensor-core form is no faster (1.60 against
+   1.55 ms per step) and its accumulation adds about twice the error of the
+   FMA form to the local energy at a chemical energy scale. */
+int msd_set_tensor_gram(msd_ctx* ctx, int on);
+
 /* Mixed precision only: the form of the opposite-spin exchange term of the
    local energy (Sec. III, the alpha-beta part of the two-body Wick
    contraction),

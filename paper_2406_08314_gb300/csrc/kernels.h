@@ -175,6 +175,10 @@ struct GramJobs {
     GramJob j[3];
 };
 void launch_gram_f32(int nw, int n_chol, const GramJobs& jobs, int nj, cudaStream_t st);
+// tc_gram.cu: the same Gram matrices on the tensor cores (3xTF32, FP32
+// accumulation in TMEM) for 2 X <= 256 per spin; returns 0 or -1.
+bool tc_gram_ok(int Xa, int Xb);
+int tc_gram(int nw, int n_chol, const GramJobs& jobs, int nj, unsigned* err, cudaStream_t st);
 
 // k_batch.cu: per-determinant energy terms of many systems in one
 // persistent launch.

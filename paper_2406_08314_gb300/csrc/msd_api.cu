@@ -136,6 +136,7 @@ struct msd_ctx {
     int tc_bn = 0;                // tensor-core output tile width (0 = by shape)
     int Kv[2] = {0, 0};           // virtual orbitals per spin
     bool fuse = true;             // fused energy contraction + epilogue when the shape allows
+    bool tc_gram = false;         // Gram matrices on the tensor cores (msd_set_tensor_gram)
     int pair_form = -1;           // mixed mode, opposite-spin term: -1 auto, 0 per determinant, 1 per beta string
     bool pair_y_auto = false;     // the auto choice for the current trial (set_trial)
     bool fused_ok[2] = {false, false};
@@ -1177,7 +1178,12 @@ int en_chunk(msd_ctx* ctx, Chunk& c, EnWork& E, int w0, int nw, int cap, bool fp
         GramJobs jobs = {{{X[0], X[0], (float2*)E.La[0], (float2*)E.La[0], (float2*)E.Kaa},
                           {X[1], X[1], (float2*)E.La[1], (float2*)E.La[1], (float2*)E.Kbb},
                           {X[0], X[1], (float2*)E.La[0], (float2*)E.La[1], (float2*)E.Kab}}};
-        launch_gram_f32(nw, G, jobs, 3, st);
+        if (ctx->tc_gram && tc_gram_ok(X[0], X[1])) {
+            if (tc_gram(nw, G, jobs, 3, ctx->d_err, st))
+                return fail(ctx, MSD_ERR_CUDA, "tensor-core Gram launch failed");
+        } else {
+            launch_gram_f32(nw, G, jobs, 3, st);
+        }
     } else {
         launch_gram(nw, X[0], X[0], G, (double2*)E.La[0], (double2*)E.La[0], E.Kaa, false, st);
         launch_gram(nw, X[1], X[1], G, (double2*)E.La[1], (double2*)E.La[1], E.Kbb, false, st);
@@ -1970,6 +1976,13 @@ int msd_set_wait_budget(msd_ctx* ctx, unsigned long long ns)
     if (!ctx) return MSD_ERR_ARG;
     CK(cudaSetDevice(ctx->device));
     CK(cudaMemcpy(ctx->d_err + 2, &ns, sizeof ns, cudaMemcpyHostToDevice));
+    return MSD_OK;
+}
+
+int msd_set_tensor_gram(msd_ctx* ctx, int on)
+{
+    if (!ctx) return MSD_ERR_ARG;
+    ctx->tc_gram = on != 0;
     return MSD_OK;
 }
 

@@ -465,3 +465,20 @@ def test_fe2s2_full_size_chemical_scale_mixed_vs_fp64(msd):
     de = np.abs(out["mixed"] - out["fp64"])
     assert np.all(de <= 2e-8 * np.abs(out["fp64"])), (de / np.abs(out["fp64"])).max()
     assert np.median(de) <= 2e-6, np.median(de)
+
+
+def test_fe2s2_full_size_tensor_gram_matches_fma_gram(msd, fe2s2):
+    """Full size: the Gram matrices on the tensor cores (3xTF32, FP32
+    accumulation in TMEM) against the FP32-FMA kernel. Both are within
+    FP32 rounding of each other, far inside the mixed bound."""
+    s, w = fe2s2
+    da, db = _cuda(w.phi_a), _cuda(w.phi_b)
+    ctx = msd.Context(s, "mixed")
+    e0 = _np(ctx.local_energy(da, db))      # the default: FP32 FMAs
+    ctx.set_tensor_gram(True)
+    ctx.set_timing(True)
+    e1 = _np(ctx.local_energy(da, db))
+    assert ctx.kernel_stats()["k_gram"][0] == 1
+    ctx.close()
+    assert np.all(np.isfinite(e1))
+    assert np.all(np.abs(e1 - e0) <= 0.1 * MIX_E_ABS), np.abs(e1 - e0).max()
