@@ -86,8 +86,9 @@ def parse():
     # library options (alternative implementations of the same step)
     p.add_argument("--no-fused", action="store_true",
                    help="mixed: tensor-core GEMM + separate epilogue instead of the fused kernel")
-    p.add_argument("--pair-form", default="auto", choices=["auto", "0", "1"],
-                   help="mixed: opposite-spin term per determinant (0), per beta string (1) or chosen by the cost model")
+    p.add_argument("--pair-form", default="auto", choices=["auto", "0", "1", "2"],
+                   help="opposite-spin term per determinant (0), per beta string (1), over runs sharing a "
+                        "string (2) or chosen by the cost model")
     return p.parse_args()
 
 
@@ -254,6 +255,9 @@ def algorithmic_work(s, n_w):
     w["k_string_energy"] = sum(float(np.sum(sp["lv"] * (10 * k ** 4 + 16 * k ** 2))) for sp in spins) * n_w
     w["k_pair_cross"] = sum(8.0 * n * (ka * ka * kb * kb + ka * ka) for (ka, kb), n in pair_lv.items()
                             if ka and kb) * n_w
+    # the runs form evaluates the same term (the algorithmic work of the
+    # per-determinant form is the reference count)
+    w["k_pair_run"] = w["k_pair_cross"]
     # the per-beta-string form (mixed precision): Y_b over the alpha block
     # for every excited beta string, then k_a^2 per determinant
     w["k_pair_y"] = (8.0 * spins[0]["X"] * float(np.sum(spins[1]["lv"][1:] * k[1:] ** 2))
@@ -500,7 +504,8 @@ def run_ours(args, rank, world, local):
                                    f"N_det={n_det}, N_chol={s.n_chol}, {n_w} walkers/GPU",
                        "precision": args.precision, "n_walkers": n_w, "n_det": n_det,
                        "fused": args.precision == "mixed" and not args.no_fused,
-                       "opposite_spin_form": ("per beta string" if "k_pair_y" in kernels else "per determinant"),
+                       "opposite_spin_form": ("per beta string" if "k_pair_y" in kernels else
+                                              "runs sharing a string" if "k_pair_run" in kernels else "per determinant"),
                        "n_chol": s.n_chol, "M": s.M,
                        "step": "msd_evaluate: overlap + force bias + local energy",
                        "l2": "flushed between timed steps (256 MiB write)",

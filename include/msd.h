@@ -257,19 +257,22 @@ int msd_set_exact_reference(msd_ctx* ctx, int on);
    FMA form to the local energy at a chemical energy scale. */
 int msd_set_tensor_gram(msd_ctx* ctx, int on);
 
-/* Mixed precision only: the form of the opposite-spin exchange term of the
-   local energy (Sec. III, the alpha-beta part of the two-body Wick
-   contraction),
+/* The form of the opposite-spin exchange term of the local energy (Sec. III,
+   the alpha-beta part of the two-body Wick contraction),
      sum_I c_I r_a r_b sum_ij sum_kl Ba[i][j] Bb[k][l] K^ab[(h_j,p_i)][(h_l,p_k)].
-   form = 1: the inner sum is formed once per beta string b,
-   Y_b[x] = sum_kl Bb[k][l] K^ab[x][(h_l,p_k)], so a determinant costs k_a^2
-   instead of k_a^2 k_b^2 operations (pays when many determinants share a
-   beta string); form = 0: every determinant takes the double sum;
-   form = -1 (the default): chosen per trial by a cost model over the
-   trial's excitation levels. The two forms differ by FP32 summation order
-   only. A batch (msd_batch_create) sets its systems to 0, the form its
-   persistent kernel implements. FP64 contexts always take the
-   per-determinant form. MSD_ERR_ARG for other values. */
+   form = 0: every determinant takes the double sum (k_a^2 k_b^2 gathers of
+   K^ab); form = 1 (mixed precision only): the inner sum is formed once per
+   beta string, Y_b[x] = sum_kl Bb[k][l] K^ab[x][(h_l,p_k)], so a
+   determinant costs k_a^2; form = 2: within each excitation-level bucket
+   the determinants sharing one string (the side chosen per bucket when the
+   trial is set) form a run, its projection P_s = sum_e Bs[e] K^ab[x_e][.]
+   is formed once in shared memory and each determinant of the run costs
+   k_o^2 (buckets with too few determinants per string keep the double sum);
+   form = -1 (the default): 1 when a cost model over the trial's levels
+   prefers it to the double sum, else 2. The forms differ by the order of
+   the sums in the working precision only. A batch (msd_batch_create) sets
+   its systems to 0, the form its persistent kernel implements. MSD_ERR_ARG
+   for other values. */
 int msd_set_pair_form(msd_ctx* ctx, int form);
 
 /* Number of CUDA kernels the library has launched in this process (all

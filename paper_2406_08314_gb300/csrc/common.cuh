@@ -106,6 +106,12 @@ struct PairTables {
     const double* c;    // [n_det] coefficient
     const float* cf;    // [n_det] coefficient in FP32
     const int* det_index;  // [n_det] original position in the trial list
+    // runs form of the opposite-spin term: per bucket 0 (per determinant),
+    // 1 (runs sharing an alpha string) or 2 (runs sharing a beta string);
+    // runs[run_off[b] ..] the first determinant of each run of bucket b
+    int run_side[(MSD_KMAX + 1) * (MSD_KMAX + 1)];
+    int run_off[(MSD_KMAX + 1) * (MSD_KMAX + 1) + 1];
+    const int* runs;
 };
 
 // Workspace pointers for one chunk of walkers (nw walkers).

@@ -442,11 +442,16 @@ template <int KB>
 static void launch_pc_k(const SpinTables& ta, const SpinTables& tb, const PairTables& pt, int ka,
                         int nw, const void* ra, const void* rb, const void* Ba, const void* Bb,
                         const void* K, bool fp32, double2* part, int nslot, int& slot,
-                        cudaStream_t st)
+                        cudaStream_t st, bool use_runs)
 {
     const int idx = ka * (MSD_KMAX + 1) + KB;
     const int lo = pt.bucket[idx], n = pt.bucket[idx + 1] - lo;
     if (n <= 0) return;
+    if (use_runs && pt.run_side[idx]) {
+        launch_pair_run(ta, tb, pt, idx, ka, KB, nw, ra, rb, Ba, Bb, K, fp32, part, nslot, slot, st);
+        slot += pair_run_blocks(pt, idx);
+        return;
+    }
     const int nb = (n + PC_THREADS * PC_PER_THREAD - 1) / (PC_THREADS * PC_PER_THREAD);
     dim3 grid(nb, nw);
     const size_t smem = (fp32 ? sizeof(float2) : sizeof(double2)) * (size_t)(ta.nh * ta.np) * (tb.nh * tb.np);
@@ -467,27 +472,29 @@ static void launch_pc_k(const SpinTables& ta, const SpinTables& tb, const PairTa
 void launch_pair_cross(const SpinTables& ta, const SpinTables& tb, const PairTables& pt, int nw,
                        const void* ra, const void* rb, const void* Ba, const void* Bb,
                        const void* K, bool fp32, double2* part, int nslot, int slot0,
-                       cudaStream_t st)
+                       cudaStream_t st, bool use_runs)
 {
     int slot = slot0;
     for (int ka = 1; ka <= MSD_KMAX; ++ka) {
-        launch_pc_k<1>(ta, tb, pt, ka, nw, ra, rb, Ba, Bb, K, fp32, part, nslot, slot, st);
-        launch_pc_k<2>(ta, tb, pt, ka, nw, ra, rb, Ba, Bb, K, fp32, part, nslot, slot, st);
-        launch_pc_k<3>(ta, tb, pt, ka, nw, ra, rb, Ba, Bb, K, fp32, part, nslot, slot, st);
-        launch_pc_k<4>(ta, tb, pt, ka, nw, ra, rb, Ba, Bb, K, fp32, part, nslot, slot, st);
-        launch_pc_k<5>(ta, tb, pt, ka, nw, ra, rb, Ba, Bb, K, fp32, part, nslot, slot, st);
-        launch_pc_k<6>(ta, tb, pt, ka, nw, ra, rb, Ba, Bb, K, fp32, part, nslot, slot, st);
+        launch_pc_k<1>(ta, tb, pt, ka, nw, ra, rb, Ba, Bb, K, fp32, part, nslot, slot, st, use_runs);
+        launch_pc_k<2>(ta, tb, pt, ka, nw, ra, rb, Ba, Bb, K, fp32, part, nslot, slot, st, use_runs);
+        launch_pc_k<3>(ta, tb, pt, ka, nw, ra, rb, Ba, Bb, K, fp32, part, nslot, slot, st, use_runs);
+        launch_pc_k<4>(ta, tb, pt, ka, nw, ra, rb, Ba, Bb, K, fp32, part, nslot, slot, st, use_runs);
+        launch_pc_k<5>(ta, tb, pt, ka, nw, ra, rb, Ba, Bb, K, fp32, part, nslot, slot, st, use_runs);
+        launch_pc_k<6>(ta, tb, pt, ka, nw, ra, rb, Ba, Bb, K, fp32, part, nslot, slot, st, use_runs);
     }
 }
 
-int pair_cross_slots(const PairTables& pt)
+int pair_cross_slots(const PairTables& pt, bool use_runs)
 {
     int n = 0;
     for (int ka = 1; ka <= MSD_KMAX; ++ka)
         for (int kb = 1; kb <= MSD_KMAX; ++kb) {
             const int idx = ka * (MSD_KMAX + 1) + kb;
             const int c = pt.bucket[idx + 1] - pt.bucket[idx];
-            if (c > 0) n += (c + PC_THREADS * PC_PER_THREAD - 1) / (PC_THREADS * PC_PER_THREAD);
+            if (c <= 0) continue;
+            if (use_runs && pt.run_side[idx]) n += pair_run_blocks(pt, idx);
+            else n += (c + PC_THREADS * PC_PER_THREAD - 1) / (PC_THREADS * PC_PER_THREAD);
         }
     return n;
 }

@@ -52,7 +52,7 @@ int string_energy_slots(const SpinTables& tb);
 void launch_string_energy(const SpinTables& tb, int nw, const double2* wts,
                           const void* B, const void* K, const void* Y, bool fp32, double2* part,
                           int nslot, int slot0, cudaStream_t st);
-int pair_cross_slots(const PairTables& pt);
+int pair_cross_slots(const PairTables& pt, bool use_runs = false);
 // k_pair_y.cu: the opposite-spin term per beta string (mixed precision)
 bool pair_y_ok(const SpinTables& ta, const SpinTables& tb);
 int pair_y_slots(const SpinTables& tb);
@@ -61,10 +61,17 @@ void launch_pair_y(const SpinTables& ta, const SpinTables& tb, int nw, const flo
                    cudaStream_t st);
 // ra, rb: the string ratios in the working precision (double2 in FP64 mode,
 // their FP32 copies in mixed mode)
+// use_runs: buckets with run_side != 0 take the runs form (k_pair_run.cu).
 void launch_pair_cross(const SpinTables& ta, const SpinTables& tb, const PairTables& pt, int nw,
                        const void* ra, const void* rb, const void* Ba, const void* Bb,
                        const void* K, bool fp32, double2* part, int nslot, int slot0,
-                       cudaStream_t st);
+                       cudaStream_t st, bool use_runs = false);
+// k_pair_run.cu
+int pair_run_blocks(const PairTables& pt, int bidx);
+size_t pair_run_smem(const SpinTables& ta, const SpinTables& tb, bool fp32);
+void launch_pair_run(const SpinTables& ta, const SpinTables& tb, const PairTables& pt, int bidx, int ka, int kb,
+                     int nw, const void* ra, const void* rb, const void* Ba, const void* Bb, const void* K, bool fp32,
+                     double2* part, int nslot, int slot, cudaStream_t st);
 void launch_final(int nw, const double2* part, int nslot, int nR, double e0, const double2* e1a,
                   const double2* e1b, const double2* scal, const double2* O0a, const double2* O0b,
                   double2* eloc, double2* ovlp, cudaStream_t st);

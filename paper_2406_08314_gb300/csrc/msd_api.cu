@@ -81,6 +81,11 @@ struct PairHost {
     int *d_a = nullptr, *d_b = nullptr, *d_det_index = nullptr;
     double* d_c = nullptr;
     float* d_cf = nullptr;   // FP32 copy of c
+    // runs form of the opposite-spin term (see PairTables)
+    int run_side[(MSD_KMAX + 1) * (MSD_KMAX + 1)] = {0};
+    int run_off[(MSD_KMAX + 1) * (MSD_KMAX + 1) + 1] = {0};
+    std::vector<int> runs;
+    int* d_runs = nullptr;
 };
 
 struct Buf {
@@ -301,6 +306,9 @@ PairTables pair_tables(const PairHost& p)
     t.n_det = p.n_det;
     for (int i = 0; i < (MSD_KMAX + 1) * (MSD_KMAX + 1) + 1; ++i) t.bucket[i] = p.bucket[i];
     t.a = p.d_a; t.b = p.d_b; t.c = p.d_c; t.cf = p.d_cf; t.det_index = p.d_det_index;
+    for (int i = 0; i < (MSD_KMAX + 1) * (MSD_KMAX + 1); ++i) t.run_side[i] = p.run_side[i];
+    for (int i = 0; i <= (MSD_KMAX + 1) * (MSD_KMAX + 1); ++i) t.run_off[i] = p.run_off[i];
+    t.runs = p.d_runs;
     return t;
 }
 
@@ -989,17 +997,24 @@ bool fused(const msd_ctx* ctx, int s) { return ctx->fuse && ctx->fused_ok[s]; }
 int a_rows(const msd_ctx* ctx, int s) { return fused(ctx, s) ? ctx->fplan[s].RW : 2 * ctx->sp[s].N; }
 
 // The opposite-spin term takes the per-beta-string form (k_pair_y).
-bool use_pair_y(const msd_ctx* ctx)
+// The form of the opposite-spin term this call takes: 0 per determinant,
+// 1 per beta string (mixed precision only), 2 runs sharing a string.
+int pair_form_now(const msd_ctx* ctx)
 {
-    const bool want = ctx->pair_form < 0 ? ctx->pair_y_auto : ctx->pair_form != 0;
-    return ctx->prec == MSD_MIXED && want && pair_y_ok(tables(ctx->sp[0], 1), tables(ctx->sp[1], 1));
+    const int want = ctx->pair_form < 0 ? 2 : ctx->pair_form;
+    if (want == 1 && !(ctx->prec == MSD_MIXED && pair_y_ok(tables(ctx->sp[0], 1), tables(ctx->sp[1], 1))))
+        return 0;
+    return want;
 }
+
+bool use_pair_y(const msd_ctx* ctx) { return pair_form_now(ctx) == 1; }
+bool use_runs(const msd_ctx* ctx) { return pair_form_now(ctx) == 2; }
 
 int energy_slots(msd_ctx* ctx)
 {
     const SpinTables ta = tables(ctx->sp[0], 1), tb = tables(ctx->sp[1], 1);
     return string_energy_slots(ta) + string_energy_slots(tb) +
-           (use_pair_y(ctx) ? pair_y_slots(tb) : pair_cross_slots(pair_tables(ctx->pairs)));
+           (use_pair_y(ctx) ? pair_y_slots(tb) : pair_cross_slots(pair_tables(ctx->pairs), use_runs(ctx)));
 }
 
 size_t en_bytes_per_walker(msd_ctx* ctx, bool fp32)
@@ -1205,12 +1220,13 @@ int en_chunk(msd_ctx* ctx, Chunk& c, EnWork& E, int w0, int nw, int cap, bool fp
         th.begin("k_pair_y", st);
         launch_pair_y(T[0], T[1], nw, c.rf[0], c.rf[1], c.B[0], c.B[1], E.Kab, c.part, c.nslot, slot, st);
     } else {
-        th.begin("k_pair_cross", st);
+        const bool runs = use_runs(ctx);
+        th.begin(runs ? "k_pair_run" : "k_pair_cross", st);
         // the ratios in the working precision: FP32 copies in mixed mode
         const void* ra = fp32 ? (const void*)c.rf[0] : (const void*)c.r[0];
         const void* rb = fp32 ? (const void*)c.rf[1] : (const void*)c.r[1];
         launch_pair_cross(T[0], T[1], pair_tables(ctx->pairs), nw, ra, rb, c.B[0], c.B[1], E.Kab, fp32, c.part,
-                          c.nslot, slot, st);
+                          c.nslot, slot, st, runs);
     }
     th.end(st);
     CKLAUNCH();
@@ -1592,7 +1608,7 @@ void msd_destroy(msd_ctx* ctx)
     cudaDeviceSynchronize();
     for (auto& kv : ctx->arena) cudaFree(kv.second.p);
     for (int s = 0; s < 2; ++s) free_spin(ctx->sp[s]);
-    cudaFree(ctx->pairs.d_a); cudaFree(ctx->pairs.d_b); cudaFree(ctx->pairs.d_c);
+    cudaFree(ctx->pairs.d_a); cudaFree(ctx->pairs.d_b); cudaFree(ctx->pairs.d_c); cudaFree(ctx->pairs.d_runs);
     cudaFree(ctx->pairs.d_det_index); cudaFree(ctx->pairs.d_cf);
     free_mixed(ctx);
     free_prop(ctx);
@@ -1639,6 +1655,7 @@ int msd_set_trial(msd_ctx* ctx, int n_det, const double* coeff, const int32_t* o
     // determinants ordered by (level_a, level_b, a, b)
     PairHost& P = ctx->pairs;
     cudaFree(P.d_a); cudaFree(P.d_b); cudaFree(P.d_c); cudaFree(P.d_det_index); cudaFree(P.d_cf);
+    cudaFree(P.d_runs);
     P = PairHost{};
     P.n_det = n_det;
     std::vector<int> order(n_det);
@@ -1657,6 +1674,69 @@ int msd_set_trial(msd_ctx* ctx, int n_det, const double* coeff, const int32_t* o
         P.bucket[lv(0, I) * (MSD_KMAX + 1) + lv(1, I) + 1]++;
     }
     for (int i = 1; i < (MSD_KMAX + 1) * (MSD_KMAX + 1) + 1; ++i) P.bucket[i] += P.bucket[i - 1];
+    // runs form of the opposite-spin term: per bucket, project the string
+    // that the bucket's determinants share most (alpha: the order above
+    // already groups them; beta: the bucket is re-sorted by (b, a)), unless
+    // its determinants are too few per string to pay for the projection.
+    // Costs in warp instructions per walker (shared-memory gathers at random
+    // addresses ~3.5, a projection entry over a 32-lane chunk ~1.5, a
+    // (determinant, entry) pair ~8/32).
+    {
+        const int Xs[2] = {ctx->sp[0].nh * ctx->sp[0].np, ctx->sp[1].nh * ctx->sp[1].np};
+        // the runs kernel's shared memory in FP64 must fit (else no runs)
+        SpinTables t0 = tables(ctx->sp[0], 1), t1 = tables(ctx->sp[1], 1);
+        const bool runs_fit = pair_run_smem(t0, t1, false) <= 227 * 1024;
+        P.runs.clear();
+        for (int idx = 0; idx < (MSD_KMAX + 1) * (MSD_KMAX + 1); ++idx) {
+            const int ka = idx / (MSD_KMAX + 1), kb = idx % (MSD_KMAX + 1);
+            const int lo = P.bucket[idx], hi = P.bucket[idx + 1];
+            P.run_off[idx] = (int)P.runs.size();
+            P.run_side[idx] = 0;
+            if (ka == 0 || kb == 0 || hi <= lo || !runs_fit) continue;
+            const double n = hi - lo, qa = (Xs[0] + 31) / 32, qb = (Xs[1] + 31) / 32;
+            int na = 1;
+            for (int i = lo + 1; i < hi; ++i) na += P.a[i] != P.a[i - 1];
+            std::vector<int> bs(P.b.begin() + lo, P.b.begin() + hi);
+            std::sort(bs.begin(), bs.end());
+            const int nb = (int)(std::unique(bs.begin(), bs.end()) - bs.begin());
+            const double kka = ka * ka, kkb = kb * kb;
+            const double direct = n * (3.5 * kka * kkb + 2.0 * (kka + kkb)) / 32.0;
+            const double proj_a = na * (1.5 * kka * qb + kka + 4.0) + n * kkb * 8.0 / 32.0;
+            const double proj_b = nb * (1.5 * kkb * qa + kkb + 4.0) + n * kka * 8.0 / 32.0;
+            // measured: with ~10-17 determinants per string (the iron-sulfur
+            // trial) the projection only breaks even, with ~80 (the 1e6
+            // copper-oxo trial) the runs take 0.46 of the double sum's time
+            int side = 0;
+            const double per_a = n / na, per_b = n / nb;
+            if (proj_a < direct && proj_a <= proj_b && per_a >= 24.0) side = 1;
+            else if (proj_b < direct && per_b >= 24.0) side = 2;
+            P.run_side[idx] = side;
+            if (side == 2) {
+                std::vector<int> perm(hi - lo);
+                for (int i = 0; i < hi - lo; ++i) perm[i] = lo + i;
+                std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) {
+                    if (P.b[x] != P.b[y]) return P.b[x] < P.b[y];
+                    return P.a[x] < P.a[y];
+                });
+                std::vector<int> a2(hi - lo), b2(hi - lo), d2(hi - lo);
+                std::vector<double> c2(hi - lo);
+                for (int i = 0; i < hi - lo; ++i) {
+                    a2[i] = P.a[perm[i]]; b2[i] = P.b[perm[i]];
+                    c2[i] = P.c[perm[i]]; d2[i] = P.det_index[perm[i]];
+                }
+                std::copy(a2.begin(), a2.end(), P.a.begin() + lo);
+                std::copy(b2.begin(), b2.end(), P.b.begin() + lo);
+                std::copy(c2.begin(), c2.end(), P.c.begin() + lo);
+                std::copy(d2.begin(), d2.end(), P.det_index.begin() + lo);
+            }
+            if (side) {
+                const std::vector<int>& key = side == 1 ? P.a : P.b;
+                for (int i = lo; i < hi; ++i)
+                    if (i == lo || key[i] != key[i - 1]) P.runs.push_back(i);
+            }
+        }
+        P.run_off[(MSD_KMAX + 1) * (MSD_KMAX + 1)] = (int)P.runs.size();
+    }
     // CSR per spin: determinants containing each string
     for (int s = 0; s < 2; ++s) {
         SpinHost& S = ctx->sp[s];
@@ -1705,6 +1785,11 @@ int msd_set_trial(msd_ctx* ctx, int n_det, const double* coeff, const int32_t* o
         if ((rc = upload(ctx, &P.d_cf, cf))) return rc;
     }
     if ((rc = upload(ctx, &P.d_det_index, P.det_index))) return rc;
+    {
+        std::vector<int> runs = P.runs;
+        if (runs.empty()) runs.push_back(0);
+        if ((rc = upload(ctx, &P.d_runs, runs))) return rc;
+    }
     // shared-memory needs of the energy kernels
     for (int s = 0; s < 2; ++s) {
         const SpinTables t = tables(ctx->sp[s], 1);
@@ -1962,7 +2047,7 @@ int msd_set_sync(msd_ctx* ctx, int sync)
 int msd_set_pair_form(msd_ctx* ctx, int form)
 {
     if (!ctx) return MSD_ERR_ARG;
-    if (form < -1 || form > 1) return fail(ctx, MSD_ERR_ARG, "pair form must be -1 (auto), 0 or 1");
+    if (form < -1 || form > 2) return fail(ctx, MSD_ERR_ARG, "pair form must be -1 (auto), 0, 1 or 2");
     if (ctx->pair_form != form) {
         ctx->pair_form = form;
         ctx->chunk = 0;   // the partial-sum slots per walker may change

@@ -371,9 +371,10 @@ class Context:
         self._check(_lib.msd_set_fused(self._h, int(bool(fused))))
 
     def set_pair_form(self, form):
-        """Mixed precision: opposite-spin energy term formed per beta string
-        (True / 1), per determinant (False / 0) or chosen per trial by the
-        library's cost model ("auto" / -1, the default); msd_set_pair_form."""
+        """Opposite-spin energy term per determinant (False / 0), per beta
+        string (True / 1, mixed precision), over runs of determinants sharing
+        a string (2) or chosen per trial by the library's cost model ("auto" /
+        -1, the default); msd_set_pair_form."""
         f = -1 if form == "auto" else int(form)
         self._check(_lib.msd_set_pair_form(self._h, f))
 

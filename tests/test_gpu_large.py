@@ -99,10 +99,9 @@ def test_1e6_mixed_against_fp64(msd, big):
         ctx.set_timing(True)
         e, o = ctx.local_energy(da, db, ovlp=True)
         out[prec] = (_np(e), _np(o), _np(ctx.force_bias(da, db)))
-        if prec == "mixed":
-            # ~80 determinants per beta string: the cost model takes the
-            # opposite-spin term per beta string
-            assert "k_pair_y" in ctx.kernel_stats() and "k_pair_cross" not in ctx.kernel_stats()
+        # ~80 determinants per string: the opposite-spin term over runs
+        # sharing a string (projections)
+        assert "k_pair_run" in ctx.kernel_stats() and "k_pair_cross" not in ctx.kernel_stats()
         ctx.close()
     (e64, o64, v64), (em, om, vm) = out["fp64"], out["mixed"]
     assert np.all(np.abs(em - e64) <= 1e-6), np.abs(em - e64).max()
@@ -135,3 +134,19 @@ def test_1e6_workspace_budget(msd, big):
     assert np.allclose(_np(e1), _np(e0), rtol=1e-13, atol=0)
     assert np.allclose(_np(o1), _np(o0), rtol=1e-13, atol=0)
     assert np.allclose(_np(v1), _np(v0), rtol=1e-13, atol=0)
+
+
+def test_1e6_pair_forms_agree(msd, big):
+    """The three forms of the opposite-spin term at 1e6 determinants (runs
+    with projections, per beta string, per determinant): the same sum in a
+    different FP32 order."""
+    s, w = big
+    da, db = _cuda(w.phi_a), _cuda(w.phi_b)
+    ctx = msd.Context(s, "mixed")
+    out = {}
+    for form in (2, 1, 0):
+        ctx.set_pair_form(form)
+        out[form] = _np(ctx.local_energy(da, db))
+    ctx.close()
+    for form in (1, 0):
+        assert np.all(np.abs(out[form] - out[2]) <= 1e-7), (form, np.abs(out[form] - out[2]).max())

@@ -201,9 +201,9 @@ def test_edge_cases(msd):
     with pytest.raises(msd.MSDError) as ei:
         ctx.local_energy(_cuda(pa), _cuda(w.phi_b[:2]))
     assert ei.value.name == "MSD_ERR_REF_SINGULAR"
-    # opposite-spin form: -1, 0 or 1
+    # opposite-spin form: -1, 0, 1 or 2
     with pytest.raises(msd.MSDError) as ei:
-        ctx.set_pair_form(2)
+        ctx.set_pair_form(3)
     assert ei.value.name == "MSD_ERR_ARG"
     ctx.set_pair_form("auto")
     # unsorted occupations
@@ -278,8 +278,8 @@ def _check_mixed(m, sys_, pa, pb, ref, fused=True, per_beta=True, e_abs=MIX_E_AB
 # persistent tensor-core kernel (default); unfused: GEMM + epilogue kernel.
 # pairY: the opposite-spin term formed per beta string (default); perdet:
 # the double sum per determinant.
-FUSED = pytest.mark.parametrize("fused,per_beta", [(True, True), (False, True), (True, False)],
-                                ids=["fused-pairY", "unfused-pairY", "fused-perdet"])
+FUSED = pytest.mark.parametrize("fused,per_beta", [(True, True), (False, True), (True, False), (True, 2)],
+                                ids=["fused-pairY", "unfused-pairY", "fused-perdet", "fused-runs"])
 
 
 @FUSED
@@ -427,27 +427,27 @@ def test_fe2s2_full_size_fused_matches_unfused(msd, fe2s2):
 
 
 def test_fe2s2_full_size_pair_forms_agree(msd, fe2s2):
-    """Full size, bench launch configuration: the opposite-spin term per beta
-    string against the per-determinant double sum. Both FP32 with FP64 slot
-    sums; only the order of the FP32 sums differs."""
+    """Full size, bench launch configuration: the opposite-spin term over
+    runs sharing a string (the default here), per beta string and per
+    determinant. All FP32 with FP64 slot sums; only the order of the FP32
+    sums differs."""
     s, w = fe2s2
     da, db = _cuda(w.phi_a), _cuda(w.phi_b)
     ctx = msd.Context(s, "mixed")
     ctx.set_timing(True)
     ea = _np(ctx.local_energy(da, db))
-    # ~10 determinants per beta string: the cost model keeps the
-    # per-determinant form
-    assert "k_pair_cross" in ctx.kernel_stats() and "k_pair_y" not in ctx.kernel_stats()
-    ctx.set_pair_form(False)
-    e0 = _np(ctx.local_energy(da, db))
-    assert np.array_equal(ea, e0)
-    ctx.set_pair_form(True)
-    e1 = _np(ctx.local_energy(da, db))
+    # ~10 determinants per string: the cost model prefers the runs form
+    assert "k_pair_run" in ctx.kernel_stats() and "k_pair_y" not in ctx.kernel_stats()
+    out = {}
+    for form in (0, 1, 2):
+        ctx.set_pair_form(form)
+        out[form] = _np(ctx.local_energy(da, db))
     e2 = _np(ctx.local_energy(da, db))
     ctx.close()
-    assert np.all(np.isfinite(e1))
-    assert np.array_equal(e1, e2)   # deterministic
-    assert np.all(np.abs(e1 - e0) <= 0.1 * MIX_E_ABS), np.abs(e1 - e0).max()
+    assert np.array_equal(ea, out[2]) and np.array_equal(e2, out[2])   # deterministic
+    for form in (0, 1):
+        assert np.all(np.isfinite(out[form]))
+        assert np.all(np.abs(out[form] - out[2]) <= 0.1 * MIX_E_ABS), (form, np.abs(out[form] - out[2]).max())
 
 
 def test_fe2s2_full_size_chemical_scale_mixed_vs_fp64(msd):
