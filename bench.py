@@ -592,6 +592,50 @@ def run_batched(args, rank, world, local):
         e1.synchronize()
         ms_seq += e0.elapsed_time(e1)
     ms_seq /= max(1, args.steps // 2)
+    # the persistent kernel alone (CUDA events around it in one eager run)
+    batch.time_persistent(True)
+    batch.set_config(cfg["tile_n"], cfg["ctas_per_sm"], cfg["order"])   # next call runs eagerly
+    flush.fill_(1)
+    batch.evaluate(walkers, outs)
+    torch.cuda.synchronize(dev)
+    pk_ms = batch.time_persistent(False)
+    peaks, _ = load_peaks(dev)
+    # its algorithmic work: the per-determinant terms of every system
+    pk_work = 0.0
+    for (sy, wy) in sysw:
+        wk_, _ = algorithmic_work(sy, wy.n_w)
+        pk_work += wk_["k_string_energy"] + wk_["k_pair_cross"]
+    b_, pk_peak, pk_src = kernel_peak("k_det_batched", args.precision, peaks)
+    pk_gflops = pk_work / (pk_ms / 1e3) / 1e9 if pk_ms > 0 else None
+    roofline = {"kernel": "k_det_batched", "bound": b_, "achieved": pk_gflops, "peak": pk_peak,
+                "unit": "GFLOP/s", "frac": (pk_gflops / pk_peak) if pk_gflops else None, "traffic": None,
+                "peak_source": pk_src, "ms": pk_ms}
+    # end to end: walkers from pinned host memory into the graph's buffers,
+    # one graph launch, the local energies back to the host
+    host = [(torch.from_numpy(w.phi_a).pin_memory(), torch.from_numpy(w.phi_b).pin_memory()) for _, w in sysw]
+    e_host = [torch.empty(w.n_w, dtype=torch.complex128).pin_memory() for _, w in sysw]
+    batch.evaluate(walkers, outs)
+    torch.cuda.synchronize(dev)
+    n_e2e = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        for (a, b), (ha, hb) in zip(walkers, host):
+            a.copy_(ha, non_blocking=True)
+            b.copy_(hb, non_blocking=True)
+        batch.evaluate(walkers, outs)
+        for eh, (o, v, e) in zip(e_host, outs):
+            eh.copy_(e, non_blocking=True)
+        torch.cuda.synchronize(dev)
+    wall = (time.perf_counter() - t0) * 1e3
+    wall_max, u_e2e = aggregate(wall, units * n_e2e)
+    e2e = {"value": u_e2e / (wall_max / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(sum(ha.numel() * 16 + hb.numel() * 16 for ha, hb in host)),
+           "d2h_bytes_per_step": int(sum(eh.numel() * 16 for eh in e_host))}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        big = max(range(len(sysw)), key=lambda i: sysw[i][0].M)
+        cpu = cpu_baseline(sysw[big][0], sysw[big][1], args.cpu_seconds)
+        cpu["sample"] = f"system {big} of the batch (M={sysw[big][0].M}): " + cpu["sample"]
     if rank == 0:
         print(json.dumps({
             "metric": "walker*det overlap+energy evals/s, 32 batched uneven systems", "value": u / (ms_max / 1e3),
@@ -604,6 +648,7 @@ def run_batched(args, rank, world, local):
                        "precision": args.precision, "autotuned": cfg, "autotune_s": tune_s,
                        "total_walker_dets": units, "l2": "flushed between timed steps (256 MiB write)"},
             "sequential_ms_per_step": ms_seq, "speedup_vs_sequential": ms_seq / (ms_max / args.steps),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks}), flush=True)
     batch.close()
 
@@ -625,42 +670,35 @@ def run_cv(args, rank, world, local):
     from paper_2406_08314_gb300 import cv, msd
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    s, _ = synth.config_system("cu2o2", seed=rank, n_w=1)
+    s, w0 = synth.config_system("cu2o2", seed=rank, n_w=640)
     ctx = msd.Context(s, "mixed", device=local)
     rng = np.random.default_rng(100 + rank)
-    noise = (0.02, 0.15)
 
-    def data(n_batches, n=4096):
-        xs, xa, es = [], [], []
-        for _ in range(n_batches):
-            w = synth.make_walkers_varied(rng, s.M, s.n_alpha, s.n_beta, n, noise_range=noise)
-            da, db = torch.from_numpy(w.phi_a).to(dev), torch.from_numpy(w.phi_b).to(dev)
-            xs.append(ctx.features_rows(da, db))
-            xa.append(ctx.features(da, db, s.n_core, s.n_act_orb).reshape(n, -1))
-            es.append(ctx.local_energy(da, db).real.float())
-        return torch.cat(xs), torch.cat(xa), torch.cat(es)
-
+    # training pairs from the method's own runs: 8 seeded phaseless AFQMC
+    # runs of 640 walkers (the copper-oxo workload's walkers, dt = 0.005,
+    # 20 steps each, propagated on the GPU), one pair per walker and step
     t0 = time.perf_counter()
-    x, xa, e = data(24)                          # 98304 training pairs
-    gen_s = time.perf_counter() - t0
+    xs, es = [], []
+    for run in range(8):
+        da, db = torch.from_numpy(w0.phi_a).to(dev), torch.from_numpy(w0.phi_b).to(dev)
+        x_r, e_r, _ = cv.propagated_pairs(ctx, da, db, 20, dt=0.005, seed=1000 * rank + run)
+        xs.append(x_r)
+        es.append(e_r)
+    x, e = torch.cat(xs), torch.cat(es)          # 102400 training pairs
     torch.cuda.synchronize(dev)
+    gen_s = time.perf_counter() - t0
     t0 = time.perf_counter()
     net = cv.MLP(x.shape[1], 256, device=local, seed=1)
     hist = net.fit(x, e, epochs=20, batch=512, lr=1e-3, lr_final=3e-5)
     torch.cuda.synchronize(dev)
     train_s = time.perf_counter() - t0
-    net_a = cv.MLP(xa.shape[1], 256, device=local, seed=1)
-    net_a.fit(xa, e, epochs=20, batch=512, lr=1e-3, lr_final=3e-5)
-    # held-out population of 640 walkers
-    w = synth.make_walkers_varied(rng, s.M, s.n_alpha, s.n_beta, 640, noise_range=noise)
-    da, db = torch.from_numpy(w.phi_a).to(dev), torch.from_numpy(w.phi_b).to(dev)
+    # held-out population: the 640 walkers of a ninth run after its 20 steps
+    da, db = torch.from_numpy(w0.phi_a).to(dev), torch.from_numpy(w0.phi_b).to(dev)
+    cv.propagated_pairs(ctx, da, db, 20, dt=0.005, seed=1000 * rank + 99)
     e_all = ctx.local_energy(da, db).real.double().cpu().numpy()
     f_all = net.predict(ctx.features_rows(da, db)).double().cpu().numpy()
-    fa_all = net_a.predict(ctx.features(da, db, s.n_core, s.n_act_orb).reshape(640, -1)).double().cpu().numpy()
     study = cv.estimator_study(e_all, f_all, frac=0.125, draws=4000, seed=3)
-    study_a = cv.estimator_study(e_all, fa_all, frac=0.125, draws=4000, seed=3)
     r2 = 1 - np.mean((f_all - e_all) ** 2) / np.var(e_all)
-    r2_a = 1 - np.mean((fa_all - e_all) ** 2) / np.var(e_all)
     # cost: exact on all 640 vs surrogate on all + exact on 80
     sub = torch.from_numpy(np.sort(rng.choice(640, 80, replace=False))).to(dev)
     sa, sb = da[sub].contiguous(), db[sub].contiguous()
@@ -689,17 +727,18 @@ def run_cv(args, rank, world, local):
             "value": study["variance_reduction"], "unit": "x", "n_gpus": world, "higher_is_better": True,
             "data": "synthetic (seeded), copper-oxo-shaped system",
             "config": {"workload": "cu2o2: M=108, 16+16 e, N_det=1e4, N_chol=400; network 6912->256x3->1 GELU, "
-                                   "BF16 weights, FP32 accumulation; training pairs 98304 (walkers near the trial, "
-                                   "noise 0.02-0.15), 20 epochs; population 640 walkers, exact on a random 1/8",
-                       "features": "non-zero rows of the reference Green's function"},
+                                   "BF16 weights, FP32 accumulation; training pairs 102400 from 8 seeded phaseless "
+                                   "AFQMC runs (640 walkers x 20 steps, dt 0.005, msd_propagate), 20 epochs; "
+                                   "held-out population: a ninth run's 640 walkers after 20 steps, exact on a "
+                                   "random 1/8",
+                       "features": "non-zero rows of the reference Green's function",
+                       "n_train": int(x.shape[0])},
             "r2_heldout": float(r2), "bias": study["cv_bias"], "bias_stderr": study["cv_bias_stderr"],
             "plain_var": study["plain_var"], "cv_var": study["cv_var"],
             "train_s": train_s, "data_generation_s": gen_s, "train_mse_first_last": [hist[0]["train_mse"],
                                                                                      hist[-1]["train_mse"]],
             "ms_exact_640": ms_exact, "ms_surrogate_640_plus_exact_80": ms_cv,
-            "variance_per_cost_gain_vs_exact_640": eff,
-            "active_space_features": {"n_features": int(xa.shape[1]), "r2_heldout": float(r2_a),
-                                      "variance_reduction": study_a["variance_reduction"]}}), flush=True)
+            "variance_per_cost_gain_vs_exact_640": eff}), flush=True)
 
 
 # -------------------------------------------------------- CPU baseline

@@ -336,6 +336,11 @@ int msd_batch_autotune(msd_batch* b, const int* n_w, const double* const* phi_a,
                        double* const* e_loc, void* stream, const char* cache_path);
 int msd_batch_config(const msd_batch* b, int* tile_n, int* ctas_per_sm, int* order);
 int msd_batch_set_config(msd_batch* b, int tile_n, int ctas_per_sm, int order);
+/* With enable = 1 the next eager run of the batch (the first call with new
+   buffers or after msd_batch_set_config) brackets its persistent kernel with
+   CUDA events on the call's stream; last_ms (may be NULL) receives the time
+   of the last such run in milliseconds, or -1 if there is none. */
+int msd_batch_time_persistent(msd_batch* b, int enable, double* last_ms);
 /* 1 once a graph has been recorded for the current buffers, else 0. */
 int msd_batch_graph_ready(const msd_batch* b);
 /* Kernel nodes in the recorded graph (kernels one replay launches), or 0. */
@@ -343,7 +348,9 @@ long long msd_batch_graph_kernels(const msd_batch* b);
 
 /* ---- Learned control variate --------------------------------------------
    (The paper has no counterpart.) A small MLP predicts the real part of the
-   local energy from active-space features of the reference Green's function;
+   local energy from features of the reference Green's function (its
+   non-zero rows, msd_features_rows, or its active-space block,
+   msd_features);
    evaluated on every walker it serves as a control variate: the estimator
    mean_i f(x_i) + mean_{i in S}(E_L,i - f(x_i)) over a random subsample S
    stays unbiased while the exact path runs only on S. */

@@ -1,5 +1,6 @@
-// Learned control variate for the local energy: a small MLP on active-space
-// features of the reference Green's function, trained on local energies the
+// Learned control variate for the local energy: a small MLP on features of
+// the reference Green's function (its non-zero rows, or its active-space
+// block), trained on local energies the
 // library itself computes. Inference and training run in these kernels: BF16
 // weights and activations, FP32 accumulation (tcgen05 kind::f16 GEMMs),
 // FP32 master weights with Adam. The paper has no counterpart.

@@ -2245,6 +2245,9 @@ struct msd_batch {
     cudaStream_t aux[NSTREAM] = {};
     cudaEvent_t fork = nullptr, join[NSTREAM] = {};
     long long graph_kernels = 0;
+    // CUDA-event time of the persistent kernel in the next eager run
+    bool time_pk = false, pk_pending = false;
+    cudaEvent_t pk_ev[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -2380,9 +2383,15 @@ int batch_run(msd_batch* b, const int* n_w, const double* const* pa, const doubl
         BCK(cudaMemcpy(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice));
         b->n_items = (int)items.size();
     }
+    const bool timed = upload && b->time_pk && b->pk_ev[0];
+    if (timed) BCK(cudaEventRecord(b->pk_ev[0], st));
     if (launch_det_batched(b->d_sys, b->d_items, b->n_items, b->d_counter, b->smem, b->fp32,
                            b->ctas_per_sm * b->n_sm, st))
         return bfail(b, MSD_ERR_CUDA, "persistent batched launch failed");
+    if (timed) {
+        BCK(cudaEventRecord(b->pk_ev[1], st));
+        b->pk_pending = true;
+    }
     for (int i = 0; i < n; ++i) {
         msd_ctx* ctx = b->ctx[i];
         launch_final(n_w[i], d[i].c.part, d[i].c.nslot, d[i].c.nR, ctx->e0, (double2*)d[i].E.e1[0],
@@ -2503,6 +2512,7 @@ void msd_batch_destroy(msd_batch* b)
         if (b->join[k]) cudaEventDestroy(b->join[k]);
     }
     if (b->fork) cudaEventDestroy(b->fork);
+    if (b->pk_ev[0]) { cudaEventDestroy(b->pk_ev[0]); cudaEventDestroy(b->pk_ev[1]); }
     delete b;
 }
 
@@ -2629,6 +2639,27 @@ int msd_batch_set_config(msd_batch* b, int tile_n, int ctas_per_sm, int order)
         return b ? bfail(b, MSD_ERR_ARG, "bad batch configuration") : MSD_ERR_ARG;
     b->bn = tile_n; b->ctas_per_sm = ctas_per_sm; b->order = order;
     drop_graph(b);
+    return MSD_OK;
+}
+
+int msd_batch_time_persistent(msd_batch* b, int enable, double* last_ms)
+{
+    if (!b) return MSD_ERR_ARG;
+    BCK(cudaSetDevice(b->device));
+    if (enable && !b->pk_ev[0]) {
+        BCK(cudaEventCreate(&b->pk_ev[0]));
+        BCK(cudaEventCreate(&b->pk_ev[1]));
+    }
+    b->time_pk = enable != 0;
+    if (last_ms) {
+        *last_ms = -1.0;
+        if (b->pk_pending) {
+            BCK(cudaEventSynchronize(b->pk_ev[1]));
+            float ms = 0;
+            BCK(cudaEventElapsedTime(&ms, b->pk_ev[0], b->pk_ev[1]));
+            *last_ms = ms;
+        }
+    }
     return MSD_OK;
 }
 

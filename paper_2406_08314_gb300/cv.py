@@ -1,6 +1,6 @@
 """Learned control variate for the local energy (the paper has no
-counterpart): a small MLP f on active-space features x of the reference
-Green's function predicts Re E_L; on a walker population the estimator
+counterpart): a small MLP f on features x of the reference Green's function
+(its non-zero rows) predicts Re E_L; on a walker population the estimator
 
     E_cv = mean_i f(x_i) + mean_{i in S} (E_L,i - f(x_i)),
 
@@ -153,3 +153,26 @@ def estimator_study(e_all, f_all, frac=0.125, draws=4000, seed=0):
             "variance_reduction": float(plain.var() / max(cv.var(), 1e-300)),
             "cv_bias": float(cv.mean() - exact), "cv_bias_stderr": float(cv.std() / np.sqrt(draws)),
             "plain_bias": float(plain.mean() - exact)}
+
+
+def propagated_pairs(ctx, phi_a, phi_b, n_steps, dt=0.005, seed=0, qr_every=5, order=6):
+    """Features and exact local energies of a walker population along a
+    phaseless AFQMC run (msd_propagate: Gaussian fields, force bias,
+    Taylor propagator, phaseless weights, a QR every qr_every steps; Sec.
+    II A), one (features, Re E_L) pair per walker and step, all computed by
+    the library on the device. phi_a, phi_b: device walkers (modified in
+    place). Returns (features [n_steps n_w][ld] FP32, energies [n_steps n_w]
+    FP32, weights [n_steps n_w] FP64)."""
+    import torch
+    n_w = phi_a.shape[0]
+    gen = torch.Generator(device=phi_a.device)
+    gen.manual_seed(int(seed))
+    w = torch.ones(n_w, dtype=torch.float64, device=phi_a.device)
+    xs, es, ws = [], [], []
+    for step in range(n_steps):
+        x = torch.randn((n_w, ctx.n_chol), dtype=torch.float64, device=phi_a.device, generator=gen)
+        ctx.propagate(phi_a, phi_b, w, x, dt, order, (step + 1) % qr_every == 0)
+        xs.append(ctx.features_rows(phi_a, phi_b))
+        es.append(ctx.local_energy(phi_a, phi_b).real.float())
+        ws.append(w.clone())
+    return torch.cat(xs), torch.cat(es), torch.cat(ws)

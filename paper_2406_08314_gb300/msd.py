@@ -25,7 +25,7 @@ EXPORTS = ["msd_create", "msd_destroy", "msd_last_error", "msd_set_hamiltonian",
            "msd_kernel_count", "msd_kernel_stat", "msd_set_workspace_limit", "msd_set_sync", "msd_set_fused", "msd_set_pair_form", "msd_set_exact_reference", "msd_set_tensor_gram", "msd_set_wait_budget", "msd_propagate",
            "msd_launch_count", "msd_overlap_noalloc", "msd_batch_create", "msd_batch_destroy",
            "msd_batch_last_error", "msd_batch_evaluate", "msd_batch_autotune", "msd_batch_config",
-           "msd_batch_set_config", "msd_batch_graph_ready", "msd_batch_graph_kernels", "msd_features", "msd_features_rows",
+           "msd_batch_set_config", "msd_batch_time_persistent", "msd_batch_graph_ready", "msd_batch_graph_kernels", "msd_features", "msd_features_rows",
            "msd_mlp_create", "msd_mlp_destroy", "msd_mlp_last_error", "msd_mlp_param_count",
            "msd_mlp_set_params", "msd_mlp_get_params", "msd_mlp_forward", "msd_mlp_grad", "msd_mlp_adam_step"]
 INFO = {"n_det": 1, "n_chol": 2, "n_strings_a": 3, "n_strings_b": 4, "n_holes_a": 5,
@@ -89,6 +89,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.msd_batch_autotune.argtypes = [vp, ctypes.POINTER(ci), pp, pp, pp, pp, pp, vp, ctypes.c_char_p]
     lib.msd_batch_config.argtypes = [vp, ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(ci)]
     lib.msd_batch_set_config.argtypes = [vp, ci, ci, ci]
+    lib.msd_batch_time_persistent.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_double)]
     lib.msd_batch_graph_ready.argtypes = [vp]
     lib.msd_batch_graph_kernels.argtypes = [vp]
     lib.msd_batch_graph_kernels.restype = ctypes.c_longlong
@@ -446,6 +447,13 @@ class Batch:
 
     def set_config(self, tile_n=0, ctas_per_sm=2, order=0):
         self._check(_lib.msd_batch_set_config(self._h, tile_n, ctas_per_sm, order))
+
+    def time_persistent(self, enable=True):
+        """Enable CUDA-event timing of the persistent kernel in the next eager
+        run; returns the last such time (ms) or -1."""
+        ms = ctypes.c_double()
+        self._check(_lib.msd_batch_time_persistent(self._h, int(bool(enable)), ctypes.byref(ms)))
+        return ms.value
 
     def graph_ready(self) -> bool:
         return bool(_lib.msd_batch_graph_ready(self._h))

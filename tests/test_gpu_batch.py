@@ -103,3 +103,54 @@ def test_batch_autotune_keeps_results_and_caches(msd, tmp_path):
     assert len(cache.read_text().strip().splitlines()) == 1
     batch.close()
     batch2.close()
+
+
+def test_batch_at_spec_sizes(msd):
+    """Systems of the batched workload's full size range (M up to 160,
+    N_det up to 1e5, N_chol = 4 M): the batch against the per-system path on
+    all walkers, and with each trial cut to a sample of 200 determinants
+    against the oracle on two walkers."""
+    import copy
+    import torch
+    sysw = synth.batched_systems(n_systems=4, seed0=11, n_w=16)
+    Ms = [s.M for s, _ in sysw]
+    dets = [s.n_det for s, _ in sysw]
+    assert max(Ms) >= 120 and max(dets) >= 3e4, (Ms, dets)
+    ctxs = [msd.Context(s, "mixed") for s, _ in sysw]
+    walkers = [(_cuda(w.phi_a), _cuda(w.phi_b)) for _, w in sysw]
+    batch = msd.Batch(ctxs)
+    outs = batch.evaluate(walkers)
+    torch.cuda.synchronize()
+    for i, (c, (a, b)) in enumerate(zip(ctxs, walkers)):
+        o2, v2, e2 = (_np(x) for x in c.evaluate(a, b))
+        assert np.allclose(_np(outs[i][2]), e2, rtol=1e-12, atol=0), i
+        assert np.allclose(_np(outs[i][0]), o2, rtol=1e-12, atol=0), i
+        assert np.allclose(_np(outs[i][1]), v2, rtol=1e-12, atol=1e-14 * np.abs(v2).max()), i
+    batch.close()
+    for c in ctxs:
+        c.close()
+    # sampled trials at the same sizes against the oracle
+    subs = []
+    rng = np.random.default_rng(5)
+    for s, w in sysw:
+        idx = np.concatenate([[0], np.sort(rng.choice(np.arange(1, s.n_det), 199, replace=False))])
+        t = copy.copy(s)
+        t.coeff = np.ascontiguousarray(s.coeff[idx])
+        t.occ_a = np.ascontiguousarray(s.occ_a[idx])
+        t.occ_b = np.ascontiguousarray(s.occ_b[idx])
+        subs.append((t, w))
+    for precision, tol in (("fp64", 1e-10), ("mixed", 2e-6)):
+        ctxs = [msd.Context(t, precision) for t, _ in subs]
+        walkers = [(_cuda(w.phi_a[:2]), _cuda(w.phi_b[:2])) for _, w in subs]
+        batch = msd.Batch(ctxs)
+        outs = batch.evaluate(walkers)
+        torch.cuda.synchronize()
+        for i, (t, w) in enumerate(subs):
+            ref = oracle.msd(t, w.phi_a[:2], w.phi_b[:2], energy=True, vbias=True, per_det=True)
+            cO = t.coeff[None, :] * ref["det_ovlp"]
+            scale_e = np.sum(np.abs(cO * ref["det_e"]), axis=1) / np.abs(ref["ovlp"])
+            assert np.all(np.abs(_np(outs[i][2]) - ref["e_loc"]) <= tol * scale_e), (precision, i)
+            assert np.all(np.abs(_np(outs[i][0]) - ref["ovlp"]) <= 1e-10 * np.sum(np.abs(cO), axis=1)), i
+        batch.close()
+        for c in ctxs:
+            c.close()
