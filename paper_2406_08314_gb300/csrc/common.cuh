@@ -10,6 +10,11 @@
 #define MSD_NMAX 64         // electrons per spin
 #define MSD_XMAX 112        // n_h * n_p per spin (active hole x particle block)
 
+// Row pitch (complex FP32 entries) of the mixed path's Lambda / Xi rows per
+// (walker, Cholesky vector): X rounded up to 16 entries = 128 bytes, so that
+// each row starts a cache line and is written in whole lines.
+__host__ __device__ __forceinline__ int lam_pitch(int X) { return (X + 15) / 16 * 16; }
+
 // Work decomposition of the per-determinant kernels: threads per block and
 // strings (determinants) per thread. One block writes one partial-sum slot.
 #define SE_THREADS 256

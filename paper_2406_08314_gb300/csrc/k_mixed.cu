@@ -105,8 +105,8 @@ k_fepi_f32(SpinTables tb, int M, int n_chol, const float* __restrict__ dF, long 
                 tjl.x += f0[j * NC + l];
                 xi = fcfma(tjl, lam[l * np + p], xi);
             }
-            Lact[wg * X + e] = lam[j * np + p];
-            Xic[wg * X + e] = xi;
+            Lact[wg * lam_pitch(X) + e] = lam[j * np + p];
+            Xic[wg * lam_pitch(X) + e] = xi;
         }
     }
 }
@@ -129,11 +129,12 @@ void launch_fepi_f32(const SpinTables& tb, int nw, int M, int n_chol, const floa
 }
 
 // Y[x] = Lh[x] + sum_g V0_g Lact_g[x] - sum_g Xic_g[x] (FP32 terms, V0 in
-// FP64), and the FP64 scalar sums of the FP64 kernel. Warps split the
+// FP64), and (traces) the FP64 scalar sums of the FP64 kernel; without
+// traces scal is left to the exactly split reference sums. Warps split the
 // Cholesky vectors, lanes the active entries; the warp sums are added in a
 // fixed order.
 __global__ void __launch_bounds__(256)
-k_gamma_reduce_f32(int X, int n_chol, int spin, const double2* __restrict__ v0a,
+k_gamma_reduce_f32(int X, int n_chol, int spin, bool traces, const double2* __restrict__ v0a,
                    const double2* __restrict__ v0b, const double2* __restrict__ xx,
                    const float2* __restrict__ Lact, const float2* __restrict__ Xic,
                    const double2* __restrict__ Lh, float2* __restrict__ Y, double2* __restrict__ scal)
@@ -143,7 +144,7 @@ k_gamma_reduce_f32(int X, int n_chol, int spin, const double2* __restrict__ v0a,
     const int w = blockIdx.x, t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const size_t base = (size_t)w * n_chol;
     double2 s0 = cz(0, 0), s1 = cz(0, 0);
-    for (int g = t; g < n_chol; g += blockDim.x) {
+    for (int g = t; traces && g < n_chol; g += blockDim.x) {
         s0 = cadd(s0, xx[base + g]);
         const double2 V0 = cadd(v0a[base + g], v0b[base + g]);
         s1 = cfma(V0, V0, s1);
@@ -154,8 +155,8 @@ k_gamma_reduce_f32(int X, int n_chol, int spin, const double2* __restrict__ v0a,
     for (int g = warp; g < n_chol; g += 8) {
         const double2 V0d = cadd(v0a[base + g], v0b[base + g]);
         const float2 V0 = make_float2((float)V0d.x, (float)V0d.y);
-        const float2* la = Lact + (base + g) * X;
-        const float2* xi = Xic + (base + g) * X;
+        const float2* la = Lact + (base + g) * lam_pitch(X);
+        const float2* xi = Xic + (base + g) * lam_pitch(X);
 #pragma unroll
         for (int q = 0; q < (MSD_XMAX + 31) / 32; ++q) {
             const int x = q * 32 + lane;
@@ -184,7 +185,7 @@ k_gamma_reduce_f32(int X, int n_chol, int spin, const double2* __restrict__ v0a,
         if (t < o) { red[0][t] = cadd(red[0][t], red[0][t + o]); red[1][t] = cadd(red[1][t], red[1][t + o]); }
         __syncthreads();
     }
-    if (t == 0) {
+    if (t == 0 && traces) {
         scal[(size_t)w * 8 + spin] = red[0][0];
         if (spin == 0) scal[(size_t)w * 8 + 2] = red[1][0];
     }
@@ -192,9 +193,9 @@ k_gamma_reduce_f32(int X, int n_chol, int spin, const double2* __restrict__ v0a,
 
 void launch_gamma_reduce_f32(int nw, int X, int n_chol, int spin, const double2* v0a, const double2* v0b,
                              const double2* xx, const float2* Lact, const float2* Xic, const double2* Lh,
-                             float2* Y, double2* scal, cudaStream_t st)
+                             float2* Y, double2* scal, cudaStream_t st, bool traces)
 {
-    k_gamma_reduce_f32<<<nw, 256, 0, st>>>(X, n_chol, spin, v0a, v0b, xx, Lact, Xic, Lh, Y, scal);
+    k_gamma_reduce_f32<<<nw, 256, 0, st>>>(X, n_chol, spin, traces, v0a, v0b, xx, Lact, Xic, Lh, Y, scal);
     msd_note_launch();
 }
 
@@ -217,6 +218,7 @@ __device__ __forceinline__ void gram_body(int Xp, int Xq, int n_chol, const floa
     float2* ps = gsm;                                 // [GRAM_G][16 R]
     float2* qs = SYM ? gsm : gsm + GRAM_G * W;        // [GRAM_G][16 R]
     const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
+    const int Pp = lam_pitch(Xp), Qp = lam_pitch(Xq);
     float2 acc[R][R];
 #pragma unroll
     for (int i = 0; i < R; ++i)
@@ -226,8 +228,8 @@ __device__ __forceinline__ void gram_body(int Xp, int Xq, int n_chol, const floa
         __syncthreads();   // previous chunk consumed
         for (int e = t; e < GRAM_G * W; e += 256) {
             const int gg = e / W, xx = e - gg * W, g = g0 + gg;
-            ps[e] = (g < n_chol && xx < Xp) ? Pw[(size_t)g * Xp + xx] : make_float2(0.f, 0.f);
-            if (!SYM) qs[e] = (g < n_chol && xx < Xq) ? Qw[(size_t)g * Xq + xx] : make_float2(0.f, 0.f);
+            ps[e] = (g < n_chol && xx < Xp) ? Pw[(size_t)g * Pp + xx] : make_float2(0.f, 0.f);
+            if (!SYM) qs[e] = (g < n_chol && xx < Xq) ? Qw[(size_t)g * Qp + xx] : make_float2(0.f, 0.f);
         }
         __syncthreads();
 #pragma unroll 2
@@ -266,8 +268,8 @@ k_gram_f32(GramJobs jobs, int n_chol)
     if (Xp <= 0 || Xq <= 0) return;
     extern __shared__ float2 gsm[];
     const int w = blockIdx.x;
-    const float2* Pw = jb.P + (size_t)w * n_chol * Xp;
-    const float2* Qw = jb.Q + (size_t)w * n_chol * Xq;
+    const float2* Pw = jb.P + (size_t)w * n_chol * lam_pitch(Xp);
+    const float2* Qw = jb.Q + (size_t)w * n_chol * lam_pitch(Xq);
     float2* Kw = jb.K + (size_t)w * Xp * Xq;
     if (jb.P == jb.Q && Xp == Xq) gram_body<R, true>(Xp, Xq, n_chol, Pw, Qw, Kw, gsm);
     else gram_body<R, false>(Xp, Xq, n_chol, Pw, Qw, Kw, gsm);

@@ -92,11 +92,20 @@ int tc_gemm_3xtf32(const TcOperand& A, const TcOperand& B, int Mr, int Nc, int K
 int tc_gemm_bf16(const void* A, long long lda, const void* B, long long ldb, int Mr, int Nc, int K, float* C,
                  long long ldc, unsigned* err, cudaStream_t st);
 // part_rows: rows per (block, part) in the output (0: R; larger pads each
-// part with zero rows).
+// part with zero rows). eye0 >= 0: columns [eye0, eye0 + 2 part_rows) hold
+// two identity blocks on the real-part rows r < R (1 at column eye0 + r and
+// eye0 + part_rows + r), zero on the imaginary-part rows.
 void launch_split_complex_rows(int nb, int R, int Kg, int Kp, const double2* src, long long src_ld,
-                               const int* cols, float* hi, float* lo, cudaStream_t st, int part_rows = 0);
+                               const int* cols, float* hi, float* lo, cudaStream_t st, int part_rows = 0,
+                               int eye0 = -1);
 void launch_split_real_rows(long long R, int Kg, int Kp, const double* src, long long src_ld, const int* cols,
                             float* hi, float* lo, cudaStream_t st);
+// Slices of x[r][j] (r < R, j < n, FP64) into two column blocks of rows of
+// pitch ld: hi/lo[r][k0 + j] = (h, m) and hi/lo[r][k0 + RB + j] = (q, s),
+// h = tf32(x), m = tf32(x - h), q = tf32(x - h - m), s = tf32(x - h - m - q),
+// so that h + m + q + s equals x to about 44 bits.
+void launch_split_blocks(long long R, int n, int RB, int ld, int k0, const double* x, float* hi, float* lo,
+                         cudaStream_t st);
 void launch_pack_complex(int nw, int n, const float* C, long long ldc, int splits, long long split_stride,
                          const double* add, double2* out, long long ldo, cudaStream_t st);
 
@@ -115,7 +124,7 @@ bool tc_fepi_plan(const SpinTables& tb, TcFepiPlan& p);
 int tc_fepi_fused(const SpinTables& tb, const TcFepiPlan& p, int nw, int M, int n_chol, const float* a_hi,
                   const float* a_lo, const float* b_hi, const float* b_lo, int ld, int K, const double2* Gr,
                   const float* F0P, const double* c0, const double* x0, double2* v0, double2* xx,
-                  float2* Lact, float2* Xic, unsigned* err, cudaStream_t st);
+                  float2* Lact, float2* Xic, unsigned* err, cudaStream_t st, bool traces);
 
 // tc_ozaki.cu: the reference-determinant Cholesky sums of the mixed local
 // energy in FP64 accuracy (exact-integer BF16 slices on the tensor cores).
@@ -169,11 +178,11 @@ void launch_fepi_f32(const SpinTables& tb, int nw, int M, int n_chol, const floa
                      double2* xx, float2* Lact, float2* Xic, cudaStream_t st);
 void launch_gamma_reduce_f32(int nw, int X, int n_chol, int spin, const double2* v0a, const double2* v0b,
                              const double2* xx, const float2* Lact, const float2* Xic, const double2* Lh,
-                             float2* Y, double2* scal, cudaStream_t st);
+                             float2* Y, double2* scal, cudaStream_t st, bool traces);
 // K[w][x][y] = sum_g P[w][g][x] Q[w][g][y] (FP32) for up to three
 // (P, Q, K) products of shapes Xp x Xq in one launch.
 struct GramJob {
-    int Xp, Xq;
+    int Xp, Xq;          // entries; P and Q rows have the pitch lam_pitch(X)
     const float2* P;
     const float2* Q;
     float2* K;

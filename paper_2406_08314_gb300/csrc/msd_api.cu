@@ -135,6 +135,9 @@ struct msd_ctx {
     float* d_F0P[2] = {nullptr, nullptr};
     float *Lv_hi = nullptr, *Lv_lo = nullptr;
     int Kvp[2] = {0, 0};        // virtual orbitals (not in occ0) padded to 32
+    // fused path: contraction length Kv8 (Kv padded to 8), then two column
+    // blocks of RB for the F0 slices; Kfp = Kv8 + 2 RB is the operands' pitch
+    int Kv8[2] = {0, 0}, Kfp[2] = {0, 0};
     int* d_virt[2] = {nullptr, nullptr};
     double *d_c0[2] = {nullptr, nullptr}, *d_x0[2] = {nullptr, nullptr}, *d_c0sum = nullptr;
     float* d_F0T[2] = {nullptr, nullptr};   // [n_chol][N][N + np] = L_g[occ0_j][col]
@@ -649,6 +652,8 @@ int prepare_mixed(msd_ctx* ctx, cudaStream_t st)
         ctx->Kv[s] = Kv;
         ctx->Kvp[s] = std::max(32, (Kv + 31) / 32 * 32);
         ctx->fused_ok[s] = tc_fepi_plan(tables(S, 1), ctx->fplan[s]);
+        ctx->Kv8[s] = std::max(8, (Kv + 7) / 8 * 8);
+        ctx->Kfp[s] = ctx->fused_ok[s] ? ctx->Kv8[s] + 2 * ctx->fplan[s].RB : ctx->Kvp[s];
         if (Kv == 0) virt.push_back(0);   // keeps the gather pointer valid; Kg = 0 pads with zeros
         int rc = upload(ctx, &ctx->d_virt[s], virt);
         if (rc) return rc;
@@ -685,24 +690,33 @@ int prepare_mixed(msd_ctx* ctx, cudaStream_t st)
             const int RB = ctx->fplan[s].RB, NCf = RB + S.np, NCP = ctx->fplan[s].NCP, f0s = ctx->fplan[s].f0s;
             std::vector<double> lp((size_t)G * NCf * M, 0.0);
             std::vector<float> f0p((size_t)G * f0s, 0.f);   // [g][j NCP + col], the kernel's shared layout
+            std::vector<double> f0r((size_t)G * NCf * S.N, 0.0);   // [(g, col)][j] = F0_g[j][col] in FP64
             for (int g = 0; g < G; ++g)
                 for (int cc = 0; cc < NCf; ++cc) {
                     const int col = cc < S.N ? S.occ0[cc] : cc >= RB ? S.part_orb[cc - RB] : -1;
                     if (col < 0) continue;
                     const double* src = &ctx->h_L[((size_t)g * M + col) * M];
                     std::copy(src, src + M, &lp[((size_t)g * NCf + cc) * M]);
-                    for (int j = 0; j < S.N; ++j)
-                        f0p[(size_t)g * f0s + (size_t)j * NCP + cc] = (float)ctx->h_L[((size_t)g * M + S.occ0[j]) * M + col];
+                    for (int j = 0; j < S.N; ++j) {
+                        const double v = ctx->h_L[((size_t)g * M + S.occ0[j]) * M + col];
+                        f0p[(size_t)g * f0s + (size_t)j * NCP + cc] = (float)v;
+                        f0r[((size_t)g * NCf + cc) * S.N + j] = v;
+                    }
                 }
-            double* d_lp = nullptr;
+            double *d_lp = nullptr, *d_f0r = nullptr;
             if ((rc = upload(ctx, &d_lp, lp))) return rc;
-            if ((rc = upload(ctx, &ctx->d_F0P[s], f0p))) { cudaFree(d_lp); return rc; }
+            if ((rc = upload(ctx, &d_f0r, f0r))) { cudaFree(d_lp); return rc; }
+            if ((rc = upload(ctx, &ctx->d_F0P[s], f0p))) { cudaFree(d_lp); cudaFree(d_f0r); return rc; }
             const long long RP = (long long)G * NCf;
-            CK(cudaMalloc(&ctx->LhP_hi[s], sizeof(float) * RP * ctx->Kvp[s]));
-            CK(cudaMalloc(&ctx->LhP_lo[s], sizeof(float) * RP * ctx->Kvp[s]));
-            launch_split_real_rows(RP, Kv, ctx->Kvp[s], d_lp, M, ctx->d_virt[s], ctx->LhP_hi[s], ctx->LhP_lo[s], st);
+            CK(cudaMalloc(&ctx->LhP_hi[s], sizeof(float) * RP * ctx->Kfp[s]));
+            CK(cudaMalloc(&ctx->LhP_lo[s], sizeof(float) * RP * ctx->Kfp[s]));
+            launch_split_real_rows(RP, Kv, ctx->Kfp[s], d_lp, M, ctx->d_virt[s], ctx->LhP_hi[s], ctx->LhP_lo[s], st);
+            // the F0 slices behind the contraction columns (used when the
+            // contraction adds F0 itself)
+            launch_split_blocks(RP, S.N, RB, ctx->Kfp[s], ctx->Kv8[s], d_f0r, ctx->LhP_hi[s], ctx->LhP_lo[s], st);
             CK(cudaStreamSynchronize(st));
             cudaFree(d_lp);
+            cudaFree(d_f0r);
         }
     }
     int rc = upload(ctx, &ctx->d_c0sum, c0sum);
@@ -995,6 +1009,7 @@ bool fused(const msd_ctx* ctx, int s) { return ctx->fuse && ctx->fused_ok[s]; }
 
 // Rows of the split A operand per walker: 2N, or the fused kernel's padded RW.
 int a_rows(const msd_ctx* ctx, int s) { return fused(ctx, s) ? ctx->fplan[s].RW : 2 * ctx->sp[s].N; }
+int a_ld(const msd_ctx* ctx, int s) { return fused(ctx, s) ? ctx->Kfp[s] : ctx->Kvp[s]; }
 
 // The opposite-spin term takes the per-beta-string form (k_pair_y).
 // The form of the opposite-spin term this call takes: 0 per determinant,
@@ -1023,7 +1038,10 @@ size_t en_bytes_per_walker(msd_ctx* ctx, bool fp32)
     SpinTables T1[2] = {tables(ctx->sp[0], 1), tables(ctx->sp[1], 1)};
     const int X[2] = {T1[0].nh * T1[0].np, T1[1].nh * T1[1].np};
     size_t e = 8 + 2;
-    for (int s = 0; s < 2; ++s) e += (size_t)G * (2 + 2 * X[s]) + 3 * X[s] + 1;
+    // per vector: v0, xx and the two Lambda / Xi rows (FP64 rows of X entries,
+    // or FP32 rows of the pitch lam_pitch(X), counted in double2 units)
+    for (int s = 0; s < 2; ++s)
+        e += (size_t)G * (2 + std::max(2 * X[s], lam_pitch(std::max(1, X[s])))) + 3 * X[s] + 1;
     e += (size_t)X[0] * X[0] + (size_t)X[1] * X[1] + (size_t)X[0] * X[1];
     size_t b = e * sizeof(double2);
     if (fp32 && exact_ref_on(ctx)) {
@@ -1038,7 +1056,7 @@ size_t en_bytes_per_walker(msd_ctx* ctx, bool fp32)
         for (int s = 0; s < 2; ++s) {
             if (!fused(ctx, s))
                 f = std::max(f, sizeof(float) * 2 * T1[s].N * (size_t)G * (T1[s].N + T1[s].np));
-            a = std::max(a, sizeof(float) * 2 * a_rows(ctx, s) * (size_t)ctx->Kvp[s]);
+            a = std::max(a, sizeof(float) * 2 * a_rows(ctx, s) * (size_t)a_ld(ctx, s));
         }
         b += f + a;
     } else {
@@ -1060,7 +1078,7 @@ int en_alloc(msd_ctx* ctx, int cap, bool fp32, EnWork& E)
         size_t f = 0, a = 0;
         for (int s = 0; s < 2; ++s) {
             if (!fused(ctx, s)) f = std::max(f, sizeof(float) * 2 * T1[s].N * (size_t)G * NC[s]);
-            a = std::max(a, sizeof(float) * a_rows(ctx, s) * (size_t)ctx->Kvp[s]);
+            a = std::max(a, sizeof(float) * a_rows(ctx, s) * (size_t)a_ld(ctx, s));
         }
         if (f && (rc = arena_get(ctx, "F32", f * cap, &E.F32))) return rc;
         if ((rc = arena_get(ctx, "AF_hi", a * cap, &E.Ah))) return rc;
@@ -1072,8 +1090,10 @@ int en_alloc(msd_ctx* ctx, int cap, bool fp32, EnWork& E)
             return rc;
         if ((rc = arena_get(ctx, nm[s][1], sizeof(double2) * cap * (size_t)G, &E.v0[s]))) return rc;
         if ((rc = arena_get(ctx, nm[s][2], sizeof(double2) * cap * (size_t)G, &E.xx[s]))) return rc;
-        if ((rc = arena_get(ctx, nm[s][3], sizeof(double2) * cap * (size_t)G * xs, &E.La[s]))) return rc;
-        if ((rc = arena_get(ctx, nm[s][4], sizeof(double2) * cap * (size_t)G * xs, &E.Xi[s]))) return rc;
+        // FP64 rows of X entries, or FP32 rows of the pitch lam_pitch(X)
+        const size_t ls = fp32 ? sizeof(float2) * lam_pitch((int)xs) : sizeof(double2) * xs;
+        if ((rc = arena_get(ctx, nm[s][3], ls * cap * (size_t)G, &E.La[s]))) return rc;
+        if ((rc = arena_get(ctx, nm[s][4], ls * cap * (size_t)G, &E.Xi[s]))) return rc;
         if ((rc = arena_get(ctx, nm[s][5], sizeof(double2) * cap * xs, &E.Lh1[s]))) return rc;
         if ((rc = arena_get(ctx, nm[s][6], sizeof(double2) * cap, &E.e1[s]))) return rc;
         if ((rc = arena_get(ctx, nm[s][7], sizeof(double2) * cap * xs, &E.Y[s]))) return rc;
@@ -1107,19 +1127,22 @@ int en_chunk(msd_ctx* ctx, Chunk& c, EnWork& E, int w0, int nw, int cap, bool fp
     SpinTables T[2] = {tables(ctx->sp[0], cap), tables(ctx->sp[1], cap)};
     const int X[2] = {T[0].nh * T[0].np, T[1].nh * T[1].np};
     const int NC[2] = {T[0].N + T[0].np, T[1].N + T[1].np};
+    // with the exact reference sums the FP32 exchange traces are not needed
+    const bool traces = !(fp32 && exact_ref_on(ctx));
     for (int s = 0; s < 2; ++s) {
         const int N = T[s].N;
         if (fp32 && fused(ctx, s)) {
             th.begin("k_split_F", st);
-            launch_split_complex_rows(nw, N, M - N, ctx->Kvp[s], c.Gr[s], M, ctx->d_virt[s], (float*)E.Ah,
-                                      (float*)E.Al, st, ctx->fplan[s].RB);
+            // without the traces the contraction also adds F0 (identity blocks)
+            launch_split_complex_rows(nw, N, M - N, ctx->Kfp[s], c.Gr[s], M, ctx->d_virt[s], (float*)E.Ah,
+                                      (float*)E.Al, st, ctx->fplan[s].RB, traces ? -1 : ctx->Kv8[s]);
             th.end(st);
             th.begin("tc_fepi", st);
-            const int K = std::max(8, (ctx->Kv[s] + 7) / 8 * 8);
+            const int K = traces ? ctx->Kv8[s] : ctx->Kfp[s];
             const int g = tc_fepi_fused(T[s], ctx->fplan[s], nw, M, G, (float*)E.Ah, (float*)E.Al, ctx->LhP_hi[s],
-                                        ctx->LhP_lo[s], ctx->Kvp[s], K, c.Gr[s], ctx->d_F0P[s], ctx->d_c0[s],
+                                        ctx->LhP_lo[s], ctx->Kfp[s], K, c.Gr[s], ctx->d_F0P[s], ctx->d_c0[s],
                                         ctx->d_x0[s], (double2*)E.v0[s], (double2*)E.xx[s], (float2*)E.La[s],
-                                        (float2*)E.Xi[s], ctx->d_err, st);
+                                        (float2*)E.Xi[s], ctx->d_err, st, traces);
             th.end(st);
             if (g) return fail(ctx, MSD_ERR_CUDA, "fused tensor-core contraction launch failed (energy)");
         } else if (fp32) {
@@ -1160,7 +1183,7 @@ int en_chunk(msd_ctx* ctx, Chunk& c, EnWork& E, int w0, int nw, int cap, bool fp
         if (fp32)
             launch_gamma_reduce_f32(nw, X[s], G, s, (double2*)E.v0[0], (double2*)E.v0[1], (double2*)E.xx[s],
                                     (float2*)E.La[s], (float2*)E.Xi[s], (double2*)E.Lh1[s], (float2*)E.Y[s],
-                                    (double2*)E.scal, st);
+                                    (double2*)E.scal, st, traces);
         else
             launch_gamma_reduce(nw, X[s], G, s, (double2*)E.v0[0], (double2*)E.v0[1], (double2*)E.xx[s],
                                 (double2*)E.La[s], (double2*)E.Xi[s], (double2*)E.Lh1[s], E.Y[s], false,

@@ -6,7 +6,7 @@
 // on the tensor cores (3xTF32, FP32 accumulation in TMEM), followed on the
 // same SM, per (walker w, Cholesky vector g), by the algebra on
 // F = F0 + dF (T = F[:, occ0] = T0 + dT, F_P = F[:, P]):
-//   v0 = c0_g + tr dT,   x = x0_g + 2 tr(T0 dT) + tr(dT dT),
+//   v0 = c0_g + tr dT (= tr T),   x = x0_g + 2 tr(T0 dT) + tr(dT dT),
 //   Lambda[j][p] = F_P[j][p] - sum_l T[j][l] G[occ0_l][P_p],
 //   Lact[(h,p)] = Lambda[pos(h)][p],  Xic[(h,p)] = sum_l T[pos(h)][l] Lambda[l][p].
 // The FP32 products never reach device memory.
@@ -35,10 +35,15 @@
 //               second half. Operands common to all rows (G[occ0][P] and
 //               Lambda) are read as shared-memory broadcasts, the limiting
 //               resource, once per part rather than once per part and
-//               particle half. Each set prefetches the reference block F0 of
-//               its next vector with cp.async while it works on the current
-//               one; the epilogue reads no global memory but G[occ0][P] once
-//               a tile.
+//               particle half. With the exchange traces (XTR), each set
+//               prefetches the reference block F0 of its next vector with
+//               cp.async while it works on the current one and adds it to
+//               dF; without them (the exactly split reference sums supply
+//               sum_g x_g) the contraction adds F0 itself through two
+//               identity blocks of the A operand and F0 slices of the B
+//               operand, and the epilogue reads no F0. The epilogue reads no
+//               global memory but G[occ0][P] once a tile. Lambda and Xi rows
+//               are stored with a pitch of whole 128-byte lines.
 // Every wait is bounded (about 2 s); on expiry the kernel records
 // MSD_DEV_ERR_TIMEOUT, every role leaves its loop, issued copies and
 // products are drained and TMEM is freed.
@@ -75,7 +80,7 @@ struct FeArgs {
     int nw, M, n_chol, K;      // K: contraction length (multiple of 8)
     int BN, GPT, BNe, slot;    // B tile rows, vectors per tile, MMA N, floats per walker slot
     int NCf, NCP, f0s;         // B rows per vector, shared-memory pitch of an F0 row, floats per F0 block
-    int n_rt, n_tiles;
+    int n_rt, n_ct, n_tiles;   // row tiles (walker blocks), column tiles (vector blocks)
     const double2* Gr;
     const float* F0P;          // [n_chol][f0s]: F0[j][col] at [g][j NCP + col], zero padded
     const double* c0;
@@ -86,6 +91,14 @@ struct FeArgs {
     float2* Xic;
     unsigned* err;
 };
+
+// Tile order: the column tile (block of Cholesky vectors) runs fastest, so
+// the CTAs at work share one walker row tile and the whole Cholesky operand
+// (tens of MB) is what stays in L2 between its uses; with the row tile
+// fastest the larger walker operand is re-read from DRAM (0.95 GB against
+// 0.14 GB of reads per launch at 640 walkers x 800 vectors).
+__device__ __forceinline__ int tile_rt(const FeArgs& a, int t) { return t / a.n_ct; }
+__device__ __forceinline__ int tile_ct(const FeArgs& a, int t) { return t % a.n_ct; }
 
 template <int RB>
 __device__ __forceinline__ void tmem_ld_row(uint32_t taddr, float* v)
@@ -164,7 +177,14 @@ __device__ __forceinline__ float2 cdot_row(const unsigned long long* tr, const u
                        ((e.x + e.y) + (f.x + f.y)) + ((g.x + g.y) + (h.x + h.y)));
 }
 
-template <int RB>
+// XTR: form the exchange traces x_g (the T0.dT and dT.dT products); the
+// accumulator then holds dF and the epilogue adds F0 from shared memory.
+// Without XTR only v0 and Lambda/Xi are written (the caller takes sum_g x_g
+// from the exactly split reference sums), and the contraction itself adds
+// F0: the A operand carries two identity blocks on its real-part rows and
+// the B operand the matching slices of F0 (h + m, then r + r2), so that the
+// accumulator holds F = F0 + dF and the epilogue reads no F0 block.
+template <int RB, bool XTR>
 // Bounds of 512 threads cap registers at 128: with 14 warps, four share a
 // sub-partition's 16K-register file.
 __global__ void __launch_bounds__(512, 1)
@@ -216,7 +236,7 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
             // ------------------------------------------------ TMA producer
             int kbg = 0;
             for (int tile = blockIdx.x; tile < a.n_tiles && !*vfail; tile += gridDim.x) {
-                const int m0 = (tile % a.n_rt) * 128, n0 = (tile / a.n_rt) * a.GPT * NCf;
+                const int m0 = tile_rt(a, tile) * 128, n0 = tile_ct(a, tile) * a.GPT * NCf;
                 for (int kb = 0; kb < nkb; ++kb, ++kbg) {
                     const int s = kbg % FE_STAGES;
                     if (!mbar_wait(&empty_bar[s], ((kbg / FE_STAGES) & 1) ^ 1, wb) || *vfail) {
@@ -299,13 +319,13 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
         // work, takes the larger half)
         const int ph = np >> 1, p0 = c ? ph : 0, p1 = c ? np : ph;
         // this set's sequence of vectors: (tile, gl) for gl = set, set + FE_SETS, ...
-        // with g = (tile / n_rt) GPT + gl < n_chol, tiles in this CTA's order
+        // with g = ct(tile) GPT + gl < n_chol, tiles in this CTA's order
         auto next_vec = [&](int& tile, int& gl) {
             gl += FE_SETS;
-            if (gl >= a.GPT || (tile / a.n_rt) * a.GPT + gl >= a.n_chol) {
+            if (gl >= a.GPT || tile_ct(a, tile) * a.GPT + gl >= a.n_chol) {
                 tile += gridDim.x;
                 gl = set;
-                if (tile < a.n_tiles && (gl >= a.GPT || (tile / a.n_rt) * a.GPT + gl >= a.n_chol)) tile = a.n_tiles;
+                if (tile < a.n_tiles && (gl >= a.GPT || tile_ct(a, tile) * a.GPT + gl >= a.n_chol)) tile = a.n_tiles;
             }
         };
         // F0 block of vector g (the same layout in global and shared memory)
@@ -313,19 +333,21 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
         const int st_t = (ew & 3) * 32 + lane;        // thread index within the set
         auto prefetch = [&](int tile, int gl, int k) {
             if (tile >= a.n_tiles) return;
-            const float* src = a.F0P + (size_t)((tile / a.n_rt) * a.GPT + gl) * a.f0s;
+            const float* src = a.F0P + (size_t)(tile_ct(a, tile) * a.GPT + gl) * a.f0s;
             float* dst = f0buf + (set * 2 + k) * a.f0s;
             for (int e = st_t * 4; e < a.f0s; e += 128 * 4) cp_async16(dst + e, src + e);
             cp_async_commit();
         };
         int pf_tile = blockIdx.x, pf_gl = set;       // the next vector to prefetch
-        if (pf_tile < a.n_tiles && (pf_gl >= a.GPT || (pf_tile / a.n_rt) * a.GPT + pf_gl >= a.n_chol))
+        if (pf_tile < a.n_tiles && (pf_gl >= a.GPT || tile_ct(a, pf_tile) * a.GPT + pf_gl >= a.n_chol))
             pf_tile = a.n_tiles;
-        prefetch(pf_tile, pf_gl, 0);
-        next_vec(pf_tile, pf_gl);
+        if constexpr (XTR) {
+            prefetch(pf_tile, pf_gl, 0);
+            next_vec(pf_tile, pf_gl);
+        }
         int it = 0, vc = 0;
         for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
-            const int b = it & 1, rt = tile % a.n_rt, ct = tile / a.n_rt;
+            const int b = it & 1, rt = tile_rt(a, tile), ct = tile_ct(a, tile);
             // G[occ0_l][P_p] of the tile's walkers, transposed and zero padded
             // to RB rows; double buffered by tile parity (the sets may be
             // one tile apart)
@@ -358,11 +380,13 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
                 const int g = ct * a.GPT + gl;
                 if (g >= a.n_chol) break;
                 // this vector's F0 block has landed (own copies, then the set's)
-                cp_async_wait_all();
-                bar_sync(8 + set, 128);
                 const float* f0 = f0buf + (set * 2 + (vc & 1)) * a.f0s;   // T0[j][l] = f0[j NCP + l]
-                prefetch(pf_tile, pf_gl, (vc + 1) & 1);
-                next_vec(pf_tile, pf_gl);
+                if constexpr (XTR) {
+                    cp_async_wait_all();
+                    bar_sync(8 + set, 128);
+                    prefetch(pf_tile, pf_gl, (vc + 1) & 1);
+                    next_vec(pf_tile, pf_gl);
+                }
                 const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * FE_TCOLS + gl * NCf);
                 // -- this part's rows: dT (columns occ0, zero padded to RB) and dF_P;
                 // dT rows and the F_P parts (real part with F0) into the slot
@@ -377,19 +401,23 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
 #pragma unroll
                     for (int l = 0; l < RB; l += 2) {
                         *reinterpret_cast<float2*>(Sc + j * SP + l) = make_float2(t[l], t[l + 1]);
-                        z0 = fmaf(t[l], f0[l * NCP + j], z0);
-                        z1 = fmaf(t[l + 1], f0[(l + 1) * NCP + j], z1);
+                        if constexpr (XTR) {
+                            z0 = fmaf(t[l], f0[l * NCP + j], z0);
+                            z1 = fmaf(t[l + 1], f0[(l + 1) * NCP + j], z1);
+                        }
                     }
                     s_0 = z0 + z1;
 #pragma unroll
                     for (int p = 0; p < PW; ++p)
-                        if (p < np) FP[(c * np + p) * RB + j] = c ? fp[p] : fp[p] + f0[j * NCP + RB + p];
+                        if (p < np) FP[(c * np + p) * RB + j] = (c || !XTR) ? fp[p] : fp[p] + f0[j * NCP + RB + p];
                 }
                 pair_sync<RB>(pbar);
                 // -- traces from the rows and columns of S. real: s_a = sum_l A[j][l] A[l][j],
                 // s_b = sum_l A[j][l] B[l][j]; imaginary: s_b = sum_l B[j][l] B[l][j]
-                float s_diag, s_a, s_b;
-                {
+                float s_diag, s_a = 0.f, s_b = 0.f;
+                if constexpr (!XTR) {
+                    s_diag = Sc[j * SP + j];   // written by this lane above
+                } else {
                     const float* row = Sc + j * SP;
                     float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
 #pragma unroll 4
@@ -410,9 +438,11 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
 #pragma unroll
                 for (int o = RB >> 1; o; o >>= 1) {
                     s_diag += __shfl_xor_sync(0xffffffffu, s_diag, o);
-                    s_a += __shfl_xor_sync(0xffffffffu, s_a, o);
-                    s_b += __shfl_xor_sync(0xffffffffu, s_b, o);
-                    s_0 += __shfl_xor_sync(0xffffffffu, s_0, o);
+                    if constexpr (XTR) {
+                        s_a += __shfl_xor_sync(0xffffffffu, s_a, o);
+                        s_b += __shfl_xor_sync(0xffffffffu, s_b, o);
+                        s_0 += __shfl_xor_sync(0xffffffffu, s_0, o);
+                    }
                 }
                 if (j == 0) {
                     scal[c * 8 + 0] = s_diag;
@@ -421,8 +451,9 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
                     scal[c * 8 + 3] = s_b;
                 }
                 // -- the complex row T[j][:] = (T0 + dT_re) + i dT_im as FP32 pairs: this
-                // part's half from t, the other part's from S. (The warp barrier keeps
-                // these loads out of the trace phase's register budget.)
+                // part's half from t, the other part's from S (without XTR the real
+                // part already holds T0). (The warp barrier keeps these loads out of
+                // the trace phase's register budget.)
                 __syncwarp();
                 unsigned long long trp[RB / 2], tip[RB / 2];
                 {
@@ -431,8 +462,9 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
                     const unsigned long long* fr = reinterpret_cast<const unsigned long long*>(f0 + j * NCP);
 #pragma unroll
                     for (int k = 0; k < RB / 2; ++k) {
-                        const unsigned long long m = pack2(t[2 * k], t[2 * k + 1]), o = So[k], f = fr[k];
-                        trp[k] = add2(c ? o : m, f);   // T0 + dT_re
+                        const unsigned long long m = pack2(t[2 * k], t[2 * k + 1]), o = So[k];
+                        if constexpr (XTR) trp[k] = add2(c ? o : m, fr[k]);   // T0 + dT_re
+                        else trp[k] = c ? o : m;
                         tip[k] = c ? m : o;
                     }
                 }
@@ -452,18 +484,28 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
                 }
                 pair_sync<RB>(pbar);   // Xi complete
                 if (wv) {
+                    // whole 128-byte lines (the row pitch XS; zeros past X), so that
+                    // no partly written line is filled from DRAM; evict-first, so
+                    // that the output stream does not push the operands out of L2
                     const size_t wg = (size_t)w * a.n_chol + g;
-                    for (int e = c * RB + j; e < X; e += 2 * RB) {
-                        const int o = oe[e];
-                        a.Lact[wg * X + e] = make_float2(LamRe[o], LamIm[o]);
-                        a.Xic[wg * X + e] = make_float2(FP[o], FP[np * RB + o]);
+                    const int XS = lam_pitch(X);
+                    for (int e = c * RB + j; e < XS; e += 2 * RB) {
+                        float2 lv = make_float2(0.f, 0.f), xv = lv;
+                        if (e < X) {
+                            const int o = oe[e];
+                            lv = make_float2(LamRe[o], LamIm[o]);
+                            xv = make_float2(FP[o], FP[np * RB + o]);
+                        }
+                        __stcs(&a.Lact[wg * XS + e], lv);
+                        __stcs(&a.Xic[wg * XS + e], xv);
                     }
                     if (c == 0 && j == 0) {
                         // real part: diag A, T0.A, A.A, A.B; imaginary part: diag B, T0.B, -, B.B
                         const float ad = scal[0], t0a = scal[1], aa = scal[2], ab = scal[3];
                         const float bd = scal[8], t0b = scal[9], bb = scal[11];
-                        a.v0[wg] = make_double2(a.c0[g] + (double)ad, (double)bd);
-                        a.xx[wg] = make_double2(a.x0[g] + (double)(2.f * t0a + aa - bb), (double)(2.f * (t0b + ab)));
+                        a.v0[wg] = make_double2(XTR ? a.c0[g] + (double)ad : (double)ad, (double)bd);
+                        if constexpr (XTR)
+                            a.xx[wg] = make_double2(a.x0[g] + (double)(2.f * t0a + aa - bb), (double)(2.f * (t0b + ab)));
                     }
                 }
                 pair_sync<RB>(pbar);   // the slot is free for the next vector
@@ -482,17 +524,6 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
     if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * FE_TCOLS)
                      : "memory");
-}
-
-int sm_count()
-{
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
-    }
-    return n;
 }
 
 }  // namespace
@@ -537,7 +568,7 @@ bool tc_fepi_plan(const SpinTables& tb, TcFepiPlan& p)
 int tc_fepi_fused(const SpinTables& tb, const TcFepiPlan& p, int nw, int M, int n_chol, const float* a_hi,
                   const float* a_lo, const float* b_hi, const float* b_lo, int ld, int K, const double2* Gr,
                   const float* F0P, const double* c0, const double* x0, double2* v0, double2* xx,
-                  float2* Lact, float2* Xic, unsigned* err, cudaStream_t st)
+                  float2* Lact, float2* Xic, unsigned* err, cudaStream_t st, bool traces)
 {
     if (nw <= 0 || n_chol <= 0) return 0;
     if (K < 8 || K % 8 || K > ld || ld % 4) return -1;
@@ -552,17 +583,20 @@ int tc_fepi_fused(const SpinTables& tb, const TcFepiPlan& p, int nw, int M, int 
     a.nw = nw; a.M = M; a.n_chol = n_chol; a.K = K;
     a.BN = p.BN; a.GPT = p.GPT; a.BNe = p.BNe; a.slot = p.slot; a.NCf = p.NCf; a.NCP = p.NCP; a.f0s = p.f0s;
     a.n_rt = (nw + p.WPT - 1) / p.WPT;
-    a.n_tiles = a.n_rt * ((n_chol + p.GPT - 1) / p.GPT);
+    a.n_ct = (n_chol + p.GPT - 1) / p.GPT;
+    a.n_tiles = a.n_rt * a.n_ct;
     a.Gr = Gr; a.F0P = F0P; a.c0 = c0; a.x0 = x0;
     a.v0 = v0; a.xx = xx; a.Lact = Lact; a.Xic = Xic; a.err = err;
-    const int grid = std::min(a.n_tiles, sm_count());
+    const int grid = std::min(a.n_tiles, msd_sm_count());
     auto go = [&](auto kern) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem) != cudaSuccess)
             return -1;
         kern<<<grid, FE_THREADS, p.smem, st>>>(ah, al, bh, bl, a);
         return 0;
     };
-    int rc = p.RB == 32 ? go(k_tc_fepi<32>) : p.RB == 16 ? go(k_tc_fepi<16>) : go(k_tc_fepi<8>);
+    int rc;
+    if (traces) rc = p.RB == 32 ? go(k_tc_fepi<32, true>) : p.RB == 16 ? go(k_tc_fepi<16, true>) : go(k_tc_fepi<8, true>);
+    else rc = p.RB == 32 ? go(k_tc_fepi<32, false>) : p.RB == 16 ? go(k_tc_fepi<16, false>) : go(k_tc_fepi<8, false>);
     if (rc) return rc;
     msd_note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;

@@ -252,7 +252,7 @@ __device__ __forceinline__ void split3(double x, float& hi, float& lo)
 // Part c of block b starts at row (2b + c) PR (PR >= R; rows r >= R zero).
 __global__ void k_split_complex_rows(int nb, int R, int PR, int Kg, int Kp, const double2* __restrict__ src,
                                      long long src_ld, const int* __restrict__ cols, float* __restrict__ hi,
-                                     float* __restrict__ lo)
+                                     float* __restrict__ lo, int eye0)
 {
     const long long total = (long long)nb * 2 * PR * Kp;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
@@ -266,6 +266,8 @@ __global__ void k_split_complex_rows(int nb, int R, int PR, int Kg, int Kp, cons
         if (k < Kg && r < R) {
             const double2 v = src[(b * R + r) * src_ld + (cols ? cols[k] : k)];
             x = c ? v.y : v.x;
+        } else if (eye0 >= 0 && k >= eye0 && k < eye0 + 2 * PR && c == 0 && r < R && (k - eye0) % PR == r) {
+            x = 1.0;
         }
         float h, l;
         split3(x, h, l);
@@ -288,6 +290,30 @@ __global__ void k_split_real_rows(long long R, int Kg, int Kp, const double* __r
         split3(x, h, l);
         hi[e] = h;
         lo[e] = l;
+    }
+}
+
+__global__ void k_split_blocks(long long R, int n, int RB, int ld, int k0, const double* __restrict__ x,
+                               float* __restrict__ hi, float* __restrict__ lo)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < R * n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long r = e / n;
+        const int j = (int)(e - r * n);
+        double v = x[e];
+        const float h = to_tf32((float)v);
+        v -= (double)h;
+        const float m = to_tf32((float)v);
+        v -= (double)m;
+        const float q = to_tf32((float)v);
+        v -= (double)q;
+        const float s = to_tf32((float)v);
+        float* ph = hi + r * ld + k0 + j;
+        float* pl = lo + r * ld + k0 + j;
+        ph[0] = h;
+        pl[0] = m;
+        ph[RB] = q;
+        pl[RB] = s;
     }
 }
 
@@ -342,12 +368,20 @@ int tc_gemm_bf16(const void* A, long long lda, const void* B, long long ldb, int
 }
 
 void launch_split_complex_rows(int nb, int R, int Kg, int Kp, const double2* src, long long src_ld,
-                               const int* cols, float* hi, float* lo, cudaStream_t st, int part_rows)
+                               const int* cols, float* hi, float* lo, cudaStream_t st, int part_rows, int eye0)
 {
     const int PR = part_rows > R ? part_rows : R;
     if ((long long)nb * R * Kp <= 0) return;
     k_split_complex_rows<<<grid_for((long long)nb * 2 * PR * Kp), 256, 0, st>>>(nb, R, PR, Kg, Kp, src, src_ld,
-                                                                                 cols, hi, lo);
+                                                                                 cols, hi, lo, eye0);
+    msd_note_launch();
+}
+
+void launch_split_blocks(long long R, int n, int RB, int ld, int k0, const double* x, float* hi, float* lo,
+                         cudaStream_t st)
+{
+    if (R * n <= 0) return;
+    k_split_blocks<<<grid_for(R * n), 256, 0, st>>>(R, n, RB, ld, k0, x, hi, lo);
     msd_note_launch();
 }
 

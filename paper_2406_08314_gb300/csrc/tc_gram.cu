@@ -71,12 +71,14 @@ constexpr int GR_V2 = 14;   // float2 per thread: 32 vectors x 2 X <= 32 x 224 f
 __device__ __forceinline__ void gr_load(float2 (&r)[GR_V2], const float* src, int rows, int kb, int n_chol)
 {
     const int g0 = kb * GR_BK, ng = min(GR_BK, n_chol - g0);
-    const float2* b = reinterpret_cast<const float2*>(src + (size_t)g0 * rows);
-    const int n2 = ng * rows / 2;    // rows is even
+    const int x2 = rows / 2, pitch = lam_pitch(x2);   // rows is even: x2 complex entries per vector
+    const float2* b = reinterpret_cast<const float2*>(src) + (size_t)g0 * pitch;
+    const int n2 = ng * x2;
 #pragma unroll
     for (int i = 0; i < GR_V2; ++i) {
         const int f = threadIdx.x + i * GR_THREADS;
-        r[i] = f < n2 ? b[f] : make_float2(0.f, 0.f);
+        const int gg = f / x2;
+        r[i] = f < n2 ? b[(size_t)gg * pitch + (f - gg * x2)] : make_float2(0.f, 0.f);
     }
 }
 
@@ -144,8 +146,8 @@ k_tc_gram(GrJobs jobs, int n_chol, int n_stages, int NB, unsigned* err)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base_sh;
-    const float* Pw = reinterpret_cast<const float*>(jb.P + (size_t)w * n_chol * Xp);
-    const float* Qw = reinterpret_cast<const float*>(jb.Q + (size_t)w * n_chol * Xq);
+    const float* Pw = reinterpret_cast<const float*>(jb.P + (size_t)w * n_chol * lam_pitch(Xp));
+    const float* Qw = reinterpret_cast<const float*>(jb.Q + (size_t)w * n_chol * lam_pitch(Xq));
     const int nkb = (n_chol + GR_BK - 1) / GR_BK;
     const uint32_t idesc = idesc_tf32(128, NB);
     float2 ra[GR_V2], rb[GR_V2];
