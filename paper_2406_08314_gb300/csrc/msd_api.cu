@@ -1011,7 +1011,6 @@ bool fused(const msd_ctx* ctx, int s) { return ctx->fuse && ctx->fused_ok[s]; }
 int a_rows(const msd_ctx* ctx, int s) { return fused(ctx, s) ? ctx->fplan[s].RW : 2 * ctx->sp[s].N; }
 int a_ld(const msd_ctx* ctx, int s) { return fused(ctx, s) ? ctx->Kfp[s] : ctx->Kvp[s]; }
 
-// The opposite-spin term takes the per-beta-string form (k_pair_y).
 // The form of the opposite-spin term this call takes: 0 per determinant,
 // 1 per beta string (mixed precision only), 2 runs sharing a string.
 int pair_form_now(const msd_ctx* ctx)

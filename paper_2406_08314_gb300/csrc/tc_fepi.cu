@@ -202,7 +202,10 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
     float* gpRe = slots + FE_SETS * WPT * a.slot;                                 // [2][WPT][np][RB]
     float* gpIm = gpRe + 2 * WPT * np * RB;                                       // [2][WPT][np][RB]
     float* f0buf = gpIm + 2 * WPT * np * RB;                                      // [FE_SETS][2][f0s]
-    int* oe = reinterpret_cast<int*>(f0buf + FE_SETS * 2 * a.f0s);               // [X] p RB + pos(h)
+    int* oe = reinterpret_cast<int*>(f0buf + FE_SETS * 2 * a.f0s);               // [X] pos(h) np + p
+    const int GE = WPT * np * RB;                 // entries of a tile's G[occ0][P] block
+    // the next tile's G[occ0][P] block as FP64, copied ahead by cp.async
+    double2* gst = reinterpret_cast<double2*>(((uintptr_t)(oe + FE_XMAX) + 15) & ~(uintptr_t)15);
 
     __shared__ __align__(8) uint64_t full_bar[FE_STAGES], empty_bar[FE_STAGES];
     __shared__ __align__(8) uint64_t tfull[2], tempty[2], drain_bar;
@@ -212,7 +215,7 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
     const int nkb = (a.K + 15) / 16;
     const uint64_t wb = wait_budget(a.err);
 
-    for (int e = threadIdx.x; e < X; e += blockDim.x) oe[e] = (e % np) * RB + a.tb.hole_pos[e / np];
+    for (int e = threadIdx.x; e < X; e += blockDim.x) oe[e] = a.tb.hole_pos[e / np] * np + e % np;
     if (threadIdx.x == 0) {
         for (int s = 0; s < FE_STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
         for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], FE_EPI / 32); }
@@ -311,13 +314,25 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
         float* slot = slots + (size_t)(set * WPT + wi) * a.slot;
         float* S0 = slot;                             // [RB][SP] dT real part
         float* S1 = slot + RB * SP;                   // [RB][SP] dT imaginary part
-        float* FP = S1 + RB * SP;                     // [2][np][RB] F_P parts, later Xi parts
+        float* FP = S1 + RB * SP;                     // [2][np][RB] F_P parts
+        float2* XiRow = reinterpret_cast<float2*>(FP);   // later [RB][np] Xi, complex, row-major
         float* LamRe = FP + 2 * np * RB;              // [np][RB] Lambda, transposed
         float* LamIm = LamRe + np * RB;
+        // [RB][np] Lambda, complex, row-major: the output reads the entries
+        // (pos(h), p) of consecutive (h, p) from consecutive words
+        float2* LamRow = reinterpret_cast<float2*>(LamIm + np * RB);
         float* scal = slot + a.slot - 16;             // [2][8] trace partials of the two parts
-        // this part's particles (the imaginary part, which has less trace
-        // work, takes the larger half)
-        const int ph = np >> 1, p0 = c ? ph : 0, p1 = c ? np : ph;
+        // this part's particles: Lambda for [l0, l1) (and np - 1 when lx),
+        // Xi for [x0, x1). With the traces the imaginary part, which has
+        // less trace work, takes the larger half of both. Without them an
+        // odd last particle is split: its Lambda goes to the real part, its
+        // Xi (which needs the whole Lambda column, complete at the barrier
+        // between the two phases) to the imaginary part.
+        const int ph = np >> 1;
+        const bool split_last = !XTR && (np & 1);
+        const int l0 = c ? ph : 0, l1 = c ? np - (split_last ? 1 : 0) : ph;
+        const bool lx = split_last && c == 0;
+        const int x0 = c ? ph : 0, x1 = c ? np : ph;
         // this set's sequence of vectors: (tile, gl) for gl = set, set + FE_SETS, ...
         // with g = ct(tile) GPT + gl < n_chol, tiles in this CTA's order
         auto next_vec = [&](int& tile, int& gl) {
@@ -338,6 +353,31 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
             for (int e = st_t * 4; e < a.f0s; e += 128 * 4) cp_async16(dst + e, src + e);
             cp_async_commit();
         };
+        // G block of a tile: cp.async of its valid entries into the stage,
+        // then (each thread its own entries) FP32 parts into buffer b
+        auto g_issue = [&](int tile) {
+            if (tile >= a.n_tiles) return;
+            const int rt = tile_rt(a, tile);
+            for (int e = et; e < GE; e += FE_EPI) {
+                const int wj = e / (np * RB), r = e % (np * RB), p = r / RB, l = r % RB;
+                const int ww = rt * WPT + wj;
+                if (ww < a.nw && l < N) cp_async16(gst + e, a.Gr + ((size_t)ww * N + l) * a.M + a.tb.part_orb[p]);
+            }
+            cp_async_commit();
+        };
+        auto g_convert = [&](int tile, int b) {
+            const int rt = tile_rt(a, tile);
+            float* gr = gpRe + b * GE;
+            float* gi = gpIm + b * GE;
+            for (int e = et; e < GE; e += FE_EPI) {
+                const int wj = e / (np * RB), l = e % RB;
+                const bool v = rt * WPT + wj < a.nw && l < N;
+                const double2 d = v ? gst[e] : make_double2(0.0, 0.0);
+                gr[e] = (float)d.x;
+                gi[e] = (float)d.y;
+            }
+        };
+        g_issue(blockIdx.x);
         int pf_tile = blockIdx.x, pf_gl = set;       // the next vector to prefetch
         if (pf_tile < a.n_tiles && (pf_gl >= a.GPT || tile_ct(a, pf_tile) * a.GPT + pf_gl >= a.n_chol))
             pf_tile = a.n_tiles;
@@ -348,23 +388,13 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
         int it = 0, vc = 0;
         for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
             const int b = it & 1, rt = tile_rt(a, tile), ct = tile_ct(a, tile);
+            const float* gbr = gpRe + b * GE;
+            const float* gbi = gpIm + b * GE;
             // G[occ0_l][P_p] of the tile's walkers, transposed and zero padded
-            // to RB rows; double buffered by tile parity (the sets may be
-            // one tile apart)
-            float* gbr = gpRe + b * WPT * np * RB;
-            float* gbi = gpIm + b * WPT * np * RB;
-            for (int e = et; e < WPT * np * RB; e += FE_EPI) {
-                const int wj = e / (np * RB), r = e % (np * RB), p = r / RB, l = r % RB;
-                const int ww = rt * WPT + wj;
-                float re = 0.f, im = 0.f;
-                if (ww < a.nw && l < N) {
-                    const double2 d = a.Gr[((size_t)ww * N + l) * a.M + a.tb.part_orb[p]];
-                    re = (float)d.x;
-                    im = (float)d.y;
-                }
-                gbr[e] = re;
-                gbi[e] = im;
-            }
+            // to RB rows, from this thread's own copies of the FP64 block;
+            // double buffered by tile parity (the sets may be one tile apart)
+            cp_async_wait_all();
+            g_convert(tile, b);
             bool ok = mbar_wait(&tfull[b], (it >> 1) & 1, wb);
             ok = bar_and(1, FE_EPI, ok && !*vfail);
             if (!ok) {
@@ -372,6 +402,8 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
                 break;
             }
             tc_fence_after();
+            // every set is past the previous tile: the stage is free for the next one
+            g_issue(tile + gridDim.x);
             const int w = rt * WPT + wi;
             const bool wv = w < a.nw;
             const float* gwr = gbr + wi * np * RB;
@@ -470,18 +502,19 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
                 }
                 // -- Lambda[j][p] = F_P[j][p] - sum_l T[j][l] G[occ0_l][P_p], this
                 // part's particles (rows j >= N: zero rows of F and T give zero)
-                for (int p = p0; p < p1; ++p) {
+                for (int u = l0; u < l1 + (lx ? 1 : 0); ++u) {
+                    const int p = u < l1 ? u : np - 1;
                     const float2 d = cdot_row<RB>(trp, tip, gwr + p * RB, gwi + p * RB);
-                    LamRe[p * RB + j] = FP[p * RB + j] - d.x;
-                    LamIm[p * RB + j] = FP[(np + p) * RB + j] - d.y;
+                    const float lr = FP[p * RB + j] - d.x, li = FP[(np + p) * RB + j] - d.y;
+                    LamRe[p * RB + j] = lr;
+                    LamIm[p * RB + j] = li;
+                    LamRow[j * np + p] = make_float2(lr, li);
                 }
                 pair_sync<RB>(pbar);   // Lambda complete; F_P and S reads done
-                // -- Xi[j][p] = sum_l T[j][l] Lambda[l][p] (all rows; holes kept), into FP
-                for (int p = p0; p < p1; ++p) {
-                    const float2 d = cdot_row<RB>(trp, tip, LamRe + p * RB, LamIm + p * RB);
-                    FP[p * RB + j] = d.x;
-                    FP[(np + p) * RB + j] = d.y;
-                }
+                // -- Xi[j][p] = sum_l T[j][l] Lambda[l][p] (all rows; holes kept), over
+                // the F_P parts (read by both parts before the barrier above)
+                for (int p = x0; p < x1; ++p)
+                    XiRow[j * np + p] = cdot_row<RB>(trp, tip, LamRe + p * RB, LamIm + p * RB);
                 pair_sync<RB>(pbar);   // Xi complete
                 if (wv) {
                     // whole 128-byte lines (the row pitch XS; zeros past X), so that
@@ -493,8 +526,8 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
                         float2 lv = make_float2(0.f, 0.f), xv = lv;
                         if (e < X) {
                             const int o = oe[e];
-                            lv = make_float2(LamRe[o], LamIm[o]);
-                            xv = make_float2(FP[o], FP[np * RB + o]);
+                            lv = LamRow[o];
+                            xv = XiRow[o];
                         }
                         __stcs(&a.Lact[wg * XS + e], lv);
                         __stcs(&a.Xic[wg * XS + e], xv);
@@ -526,6 +559,7 @@ k_tc_fepi(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUt
                      : "memory");
 }
 
+
 }  // namespace
 
 // Tile shape of the fused kernel for one spin; false when the shape is not
@@ -540,9 +574,10 @@ bool tc_fepi_plan(const SpinTables& tb, TcFepiPlan& p)
     p.RW = 2 * p.RB;
     p.WPT = 64 / p.RB;
     p.NCf = p.RB + np;                               // B rows per vector: occ0 padded to RB, particles
-    // per-walker slot: the two [RB][RB + 2] dT parts, the F_P (later Xi)
-    // parts [2][np][RB], Lambda^T as [np][RB] real and imaginary rows, 16 scalars
-    p.slot = 2 * p.RB * (p.RB + 2) + 4 * np * p.RB + 16;
+    // per-walker slot: the two [RB][RB + 2] dT parts, the F_P parts
+    // [2][np][RB] (later Xi as [RB][np] complex), Lambda^T as [np][RB] real and
+    // imaginary rows, Lambda as [RB][np] complex, 16 scalars
+    p.slot = 2 * p.RB * (p.RB + 2) + 6 * np * p.RB + 16;
     p.NCP = (p.NCf + 1) / 4 * 4 + 2;                 // = 2 mod 4: conflict-free 64-bit row reads
     p.f0s = (p.RB * p.NCP + 3) / 4 * 4;
     // columns read per vector: RB from its start (occ0 part) and 16 from
@@ -554,7 +589,8 @@ bool tc_fepi_plan(const SpinTables& tb, TcFepiPlan& p)
         const int bn = std::max(16, std::min(BN, ((gpt - 1) * p.NCf + span + 15) / 16 * 16));
         const size_t smem = 1024 + (size_t)FE_STAGES * 2 * (FE_A_BYTES + (size_t)bn * 64) +
                             4 * (size_t)FE_SETS * p.WPT * p.slot + 4 * (size_t)4 * p.WPT * np * p.RB +
-                            4 * (size_t)FE_SETS * 2 * p.f0s + 4 * FE_XMAX;
+                            4 * (size_t)FE_SETS * 2 * p.f0s + 4 * FE_XMAX +
+                            16 * ((size_t)p.WPT * np * p.RB + 1);   // G block stage, 16-byte aligned
         if (smem + 128 > 227 * 1024) continue;   // 128: static shared memory of the kernel
         p.BN = bn;
         p.GPT = gpt;
