@@ -148,10 +148,11 @@ void launch_fepi(const SpinTables& tb, int nw, int M, int n_chol, const double2*
 
 // ------------------------------------------------------------------------
 // One-body pieces per (walker, spin): e1 = tr(h G), and
-// Lambda_h[(h,p)] = (G h (I - G))[H_h][P_p].
+// Lambda_h[(h,p)] = (G hl (I - G))[H_h][P_p] with hl = h, or the matrix the
+// caller gives (linear in it: hl = h + J adds sum_g C_g Lambda_g).
 __global__ void __launch_bounds__(128)
-k_onebody(SpinTables tb, int M, const double* __restrict__ h1, const double2* __restrict__ Gr,
-          double2* __restrict__ e1, double2* __restrict__ Lh)
+k_onebody(SpinTables tb, int M, const double* __restrict__ h1, const double* __restrict__ hl,
+          const double2* __restrict__ Gr, double2* __restrict__ e1, double2* __restrict__ Lh)
 {
     extern __shared__ double2 sm[];
     const int N = tb.N, np = tb.np, nh = tb.nh, NC = N + np;
@@ -169,7 +170,7 @@ k_onebody(SpinTables tb, int M, const double* __restrict__ h1, const double2* __
         const int col = c < N ? tb.occ0[c] : tb.part_orb[c - N];
         const double2* gj = gr + (size_t)tb.hole_pos[h] * M;
         double2 v = cz(0, 0);
-        for (int r = 0; r < M; ++r) v = cadd(v, cscale(gj[r], h1[(size_t)col * M + r]));
+        for (int r = 0; r < M; ++r) v = cadd(v, cscale(gj[r], hl[(size_t)col * M + r]));
         fh[e] = v;
     }
     red[t] = a;
@@ -188,11 +189,11 @@ k_onebody(SpinTables tb, int M, const double* __restrict__ h1, const double2* __
 }
 
 void launch_onebody(const SpinTables& tb, int nw, int M, const double* h1, const double2* Gr,
-                    double2* e1, double2* Lh, cudaStream_t st)
+                    double2* e1, double2* Lh, cudaStream_t st, const double* hl)
 {
     size_t smem = sizeof(double2) * tb.nh * (tb.N + tb.np);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_onebody, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_onebody<<<nw, 128, smem, st>>>(tb, M, h1, Gr, e1, Lh); msd_note_launch();
+    k_onebody<<<nw, 128, smem, st>>>(tb, M, h1, hl ? hl : h1, Gr, e1, Lh); msd_note_launch();
 }
 
 // ------------------------------------------------------------------------

@@ -130,14 +130,18 @@ void launch_fepi_f32(const SpinTables& tb, int nw, int M, int n_chol, const floa
 
 // Y[x] = Lh[x] + sum_g V0_g Lact_g[x] - sum_g Xic_g[x] (FP32 terms, V0 in
 // FP64), and (traces) the FP64 scalar sums of the FP64 kernel; without
-// traces scal is left to the exactly split reference sums. Warps split the
-// Cholesky vectors, lanes the active entries; the warp sums are added in a
-// fixed order.
+// traces scal is left to the exactly split reference sums. With v0w (the
+// exactly split walker parts t1_g of V0_g = C_g + t1_g, [nw][G]) the FP32
+// sum runs over t1_g only; the caller's Lh then holds the reference part
+// sum_g C_g Lambda_g[x] as well (the one-body term of h + J, J = sum_g C_g
+// L_g, FP64). Warps split the Cholesky vectors, lanes the active entries;
+// the warp sums are added in a fixed order.
 __global__ void __launch_bounds__(256)
 k_gamma_reduce_f32(int X, int n_chol, int spin, bool traces, const double2* __restrict__ v0a,
                    const double2* __restrict__ v0b, const double2* __restrict__ xx,
                    const float2* __restrict__ Lact, const float2* __restrict__ Xic,
-                   const double2* __restrict__ Lh, float2* __restrict__ Y, double2* __restrict__ scal)
+                   const double2* __restrict__ Lh, float2* __restrict__ Y, double2* __restrict__ scal,
+                   const float2* __restrict__ v0w)
 {
     __shared__ float2 part[8][MSD_XMAX];
     __shared__ double2 red[2][256];
@@ -153,8 +157,13 @@ k_gamma_reduce_f32(int X, int n_chol, int spin, bool traces, const double2* __re
 #pragma unroll
     for (int q = 0; q < (MSD_XMAX + 31) / 32; ++q) acc[q] = make_float2(0, 0);
     for (int g = warp; g < n_chol; g += 8) {
-        const double2 V0d = cadd(v0a[base + g], v0b[base + g]);
-        const float2 V0 = make_float2((float)V0d.x, (float)V0d.y);
+        float2 V0;
+        if (v0w) {
+            V0 = v0w[base + g];
+        } else {
+            const double2 V0d = cadd(v0a[base + g], v0b[base + g]);
+            V0 = make_float2((float)V0d.x, (float)V0d.y);
+        }
         const float2* la = Lact + (base + g) * lam_pitch(X);
         const float2* xi = Xic + (base + g) * lam_pitch(X);
 #pragma unroll
@@ -193,9 +202,9 @@ k_gamma_reduce_f32(int X, int n_chol, int spin, bool traces, const double2* __re
 
 void launch_gamma_reduce_f32(int nw, int X, int n_chol, int spin, const double2* v0a, const double2* v0b,
                              const double2* xx, const float2* Lact, const float2* Xic, const double2* Lh,
-                             float2* Y, double2* scal, cudaStream_t st, bool traces)
+                             float2* Y, double2* scal, cudaStream_t st, bool traces, const float2* v0w)
 {
-    k_gamma_reduce_f32<<<nw, 256, 0, st>>>(X, n_chol, spin, traces, v0a, v0b, xx, Lact, Xic, Lh, Y, scal);
+    k_gamma_reduce_f32<<<nw, 256, 0, st>>>(X, n_chol, spin, traces, v0a, v0b, xx, Lact, Xic, Lh, Y, scal, v0w);
     msd_note_launch();
 }
 

@@ -39,8 +39,9 @@ size_t fepi_smem(const SpinTables& tb);
 void launch_fepi(const SpinTables& tb, int nw, int M, int n_chol, const double2* F, long long ldf,
                  const double2* Gr, double2* v0, double2* xx, double2* Lact, double2* Xic,
                  cudaStream_t st);
+// hl (optional): the matrix of the Lambda_h part instead of h1.
 void launch_onebody(const SpinTables& tb, int nw, int M, const double* h1, const double2* Gr,
-                    double2* e1, double2* Lh, cudaStream_t st);
+                    double2* e1, double2* Lh, cudaStream_t st, const double* hl = nullptr);
 void launch_gamma_reduce(int nw, int X, int n_chol, int spin, const double2* v0a, const double2* v0b,
                          const double2* xx, const double2* Lact, const double2* Xic,
                          const double2* Lh, void* Y, bool fp32, double2* scal, cudaStream_t st);
@@ -159,8 +160,9 @@ void oz_free_const(OzConst& c);
 // [oz_parts(NB)][pad(2 nw)] and t1 [2 nw][G].
 int oz_spin(const OzConst& K, int nw, int M, const double2* Gr, const int* virt, void* As, int* ea, double2* part,
             double* t1, unsigned* err, cudaStream_t st);
+// Also writes the walker parts t1a_g + t1b_g of V0_g as FP32 pairs v0w[w][g].
 void launch_ref_reduce(int nw, int G, const RefSpin& a, const RefSpin& b, double C2sum, double2* scal,
-                       cudaStream_t st);
+                       float2* v0w, cudaStream_t st);
 
 // k_debug.cu: E_I of sampled (walker, determinant) pairs.
 struct DetRec {
@@ -178,7 +180,8 @@ void launch_fepi_f32(const SpinTables& tb, int nw, int M, int n_chol, const floa
                      double2* xx, float2* Lact, float2* Xic, cudaStream_t st);
 void launch_gamma_reduce_f32(int nw, int X, int n_chol, int spin, const double2* v0a, const double2* v0b,
                              const double2* xx, const float2* Lact, const float2* Xic, const double2* Lh,
-                             float2* Y, double2* scal, cudaStream_t st, bool traces);
+                             float2* Y, double2* scal, cudaStream_t st, bool traces,
+                             const float2* v0w = nullptr);
 // K[w][x][y] = sum_g P[w][g][x] Q[w][g][y] (FP32) for up to three
 // (P, Q, K) products of shapes Xp x Xq in one launch.
 struct GramJob {

@@ -155,6 +155,7 @@ struct msd_ctx {
     bool oz_shared = false;       // spin 1 uses spin 0's constants (same reference orbitals)
     OzConst oz[2];
     double *d_JJ[2] = {nullptr, nullptr}, *d_KK[2] = {nullptr, nullptr};
+    double* d_hJ = nullptr;       // [2][M][M] h_s + J, J = sum_g C_g L_g (C_g = sum_s tr(L_g D0_s D0_s^T))
     double oz_x0sum[2] = {0, 0}, oz_C2sum = 0;
     TcFepiPlan fplan[2];
     long long gen = 0;            // bumped whenever a device buffer may move
@@ -536,6 +537,8 @@ void free_exact_ref(msd_ctx* ctx)
         cudaFree(ctx->d_JJ[s]); cudaFree(ctx->d_KK[s]);
         ctx->d_JJ[s] = ctx->d_KK[s] = nullptr;
     }
+    cudaFree(ctx->d_hJ);
+    ctx->d_hJ = nullptr;
     ctx->oz_shared = false;
     ctx->oz_ready = ctx->oz_ok = false;
 }
@@ -619,6 +622,20 @@ int prepare_exact_ref(msd_ctx* ctx, cudaStream_t st)
         cudaFree(d_XT);
         if (pr) return fail(ctx, MSD_ERR_NOMEM, "exact reference constants (%lld bytes) could not be built",
                             (long long)oz_const_bytes(N, Kv, G));
+    }
+    {
+        // J = sum_g C_g L_g: the reference part of sum_g V0_g Lambda_g is the
+        // one-body term of J, (G J (I - G))[H][P]; kept as h_s + J
+        std::vector<double> hJ(ctx->h_h1.begin(), ctx->h_h1.begin() + (size_t)2 * M * M);
+        for (int g = 0; g < G; ++g) {
+            const double* Lg = L + (size_t)g * M * M;
+            for (size_t e = 0; e < (size_t)M * M; ++e) {
+                hJ[e] += C[g] * Lg[e];
+                hJ[(size_t)M * M + e] += C[g] * Lg[e];
+            }
+        }
+        int rc;
+        if ((rc = upload(ctx, &ctx->d_hJ, hJ))) return rc;
     }
     ctx->oz_ok = true;
     return MSD_OK;
@@ -1002,6 +1019,7 @@ struct EnWork {
     void *F[2] = {nullptr, nullptr}, *F32 = nullptr, *Ah = nullptr, *Al = nullptr;
     void *v0[2], *xx[2], *La[2], *Xi[2], *Lh1[2], *e1[2], *Y[2], *Kaa, *Kbb, *Kab, *scal;
     void *ozA = nullptr, *ozE = nullptr, *ozP[2] = {nullptr, nullptr}, *ozT[2] = {nullptr, nullptr};
+    void* v0w = nullptr;   // [nw][G] FP32 walker parts of V0_g (exact reference sums)
 };
 
 // The fused tensor-core contraction + epilogue serves spin s.
@@ -1047,6 +1065,7 @@ size_t en_bytes_per_walker(msd_ctx* ctx, bool fp32)
         int kp = 0;
         for (int s = 0; s < 2; ++s) kp = std::max(kp, oz_k_padded(T1[s].N * (ctx->M - T1[s].N)));
         b += (size_t)2 * oz_slices() * kp * 2 + 2 * sizeof(int);
+        b += sizeof(float2) * (size_t)G;   // v0w
         for (int s = 0; s < 2; ++s)
             b += (size_t)2 * oz_parts_for(T1[s].N * (ctx->M - T1[s].N), G) * sizeof(double2) + 2 * sizeof(double) * G;
     }
@@ -1114,6 +1133,7 @@ int en_alloc(msd_ctx* ctx, int cap, bool fp32, EnWork& E)
             if ((rc = arena_get(ctx, np_[s], sizeof(double2) * nparts * Mpad, &E.ozP[s]))) return rc;
             if ((rc = arena_get(ctx, nt_[s], sizeof(double) * 2 * cap * (size_t)G, &E.ozT[s]))) return rc;
         }
+        if ((rc = arena_get(ctx, "v0w", sizeof(float2) * cap * (size_t)G, &E.v0w))) return rc;
     }
     return MSD_OK;
 }
@@ -1127,7 +1147,9 @@ int en_chunk(msd_ctx* ctx, Chunk& c, EnWork& E, int w0, int nw, int cap, bool fp
     const int X[2] = {T[0].nh * T[0].np, T[1].nh * T[1].np};
     const int NC[2] = {T[0].N + T[0].np, T[1].N + T[1].np};
     // with the exact reference sums the FP32 exchange traces are not needed
-    const bool traces = !(fp32 && exact_ref_on(ctx));
+    const bool exact = fp32 && exact_ref_on(ctx);
+    if (exact && !ctx->oz_ok) return fail(ctx, MSD_ERR_STATE, "exact reference constants missing");
+    const bool traces = !exact;
     for (int s = 0; s < 2; ++s) {
         const int N = T[s].N;
         if (fp32 && fused(ctx, s)) {
@@ -1173,27 +1195,17 @@ int en_chunk(msd_ctx* ctx, Chunk& c, EnWork& E, int w0, int nw, int cap, bool fp
         }
         th.begin("k_onebody", st);
         launch_onebody(T[s], nw, M, ctx->d_h1 + (size_t)s * M * M, c.Gr[s], (double2*)E.e1[s],
-                       (double2*)E.Lh1[s], st);
+                       (double2*)E.Lh1[s], st, exact && ctx->d_hJ ? ctx->d_hJ + (size_t)s * M * M : nullptr);
         th.end(st);
         CKLAUNCH();
     }
-    th.begin("k_gamma_reduce", st);
-    for (int s = 0; s < 2; ++s) {
-        if (fp32)
-            launch_gamma_reduce_f32(nw, X[s], G, s, (double2*)E.v0[0], (double2*)E.v0[1], (double2*)E.xx[s],
-                                    (float2*)E.La[s], (float2*)E.Xi[s], (double2*)E.Lh1[s], (float2*)E.Y[s],
-                                    (double2*)E.scal, st, traces);
-        else
-            launch_gamma_reduce(nw, X[s], G, s, (double2*)E.v0[0], (double2*)E.v0[1], (double2*)E.xx[s],
-                                (double2*)E.La[s], (double2*)E.Xi[s], (double2*)E.Lh1[s], E.Y[s], false,
-                                (double2*)E.scal, st);
-    }
-    th.end(st);
-    if (fp32 && exact_ref_on(ctx)) {
-        // the reference-determinant sums again, exactly split on the tensor
-        // cores: they replace the FP32 traces in scal[0..2]
-        if (!ctx->oz_ok) return fail(ctx, MSD_ERR_STATE, "exact reference constants missing");
-        RefSpin rs[2];
+    RefSpin rs[2];
+    if (exact) {
+        // the reference-determinant sums exactly split on the tensor cores:
+        // they replace the FP32 traces in scal[0..2], and their walker parts
+        // t1_g of V0_g leave only the small part of sum_g V0_g Lambda_g to
+        // the FP32 sum (the reference part C_g is in Lh1, the one-body term
+        // of h + J)
         for (int s = 0; s < 2; ++s) {
             const OzConst& K = ctx->oz[s];
             th.begin("tc_ozaki", st);
@@ -1206,10 +1218,22 @@ int en_chunk(msd_ctx* ctx, Chunk& c, EnWork& E, int w0, int nw, int cap, bool fp
                             ctx->oz_x0sum[s]};
         }
         th.begin("k_ref_reduce", st);
-        launch_ref_reduce(nw, G, rs[0], rs[1], ctx->oz_C2sum, (double2*)E.scal, st);
+        launch_ref_reduce(nw, G, rs[0], rs[1], ctx->oz_C2sum, (double2*)E.scal, (float2*)E.v0w, st);
         th.end(st);
         CKLAUNCH();
     }
+    th.begin("k_gamma_reduce", st);
+    for (int s = 0; s < 2; ++s) {
+        if (fp32)
+            launch_gamma_reduce_f32(nw, X[s], G, s, (double2*)E.v0[0], (double2*)E.v0[1], (double2*)E.xx[s],
+                                    (float2*)E.La[s], (float2*)E.Xi[s], (double2*)E.Lh1[s], (float2*)E.Y[s],
+                                    (double2*)E.scal, st, traces, exact ? (const float2*)E.v0w : nullptr);
+        else
+            launch_gamma_reduce(nw, X[s], G, s, (double2*)E.v0[0], (double2*)E.v0[1], (double2*)E.xx[s],
+                                (double2*)E.La[s], (double2*)E.Xi[s], (double2*)E.Lh1[s], E.Y[s], false,
+                                (double2*)E.scal, st);
+    }
+    th.end(st);
     th.begin("k_gram", st);
     if (fp32) {
         GramJobs jobs = {{{X[0], X[0], (float2*)E.La[0], (float2*)E.La[0], (float2*)E.Kaa},

@@ -420,9 +420,11 @@ k_gemm_dd(int Mr, int Nc, int K, const double* __restrict__ A, long long lda, co
 // Per walker: the reference energy's Cholesky sums from both spins
 //   scal[w][s] = sum_g x_g^s = x0sum_s + 2 u_s . KK_s + x2_s
 //   scal[w][2] = sum_g V0_g^2 = C2sum + 2 sum_s u_s . JJ_s + sum_g (t1a_g + t1b_g)^2
-// (FP64, fixed summation order).
+// (FP64, fixed summation order), and the walker parts t1a_g + t1b_g of V0_g
+// as FP32 pairs, v0w[w][g].
 __global__ void __launch_bounds__(256)
-k_ref_reduce(int nw, int G, RefSpin sa, RefSpin sb, double C2sum, double2* __restrict__ scal)
+k_ref_reduce(int nw, int G, RefSpin sa, RefSpin sb, double C2sum, double2* __restrict__ scal,
+             float2* __restrict__ v0w)
 {
     __shared__ double2 red[4][256];
     const int w = blockIdx.x, t = threadIdx.x;
@@ -444,6 +446,7 @@ k_ref_reduce(int nw, int G, RefSpin sa, RefSpin sb, double C2sum, double2* __res
         const double2 v = cz(sa.t1[(size_t)(2 * w) * G + g] + sb.t1[(size_t)(2 * w) * G + g],
                              sa.t1[(size_t)(2 * w + 1) * G + g] + sb.t1[(size_t)(2 * w + 1) * G + g]);
         q = cfma(v, v, q);
+        v0w[(size_t)w * G + g] = make_float2((float)v.x, (float)v.y);
     }
     red[0][t] = cadd(lj[0], lj[1]);
     red[1][t] = lk[0];
@@ -552,8 +555,8 @@ int oz_spin(const OzConst& K, int nw, int M, const double2* Gr, const int* virt,
 }
 
 void launch_ref_reduce(int nw, int G, const RefSpin& a, const RefSpin& b, double C2sum, double2* scal,
-                       cudaStream_t st)
+                       float2* v0w, cudaStream_t st)
 {
-    k_ref_reduce<<<nw, 256, 0, st>>>(nw, G, a, b, C2sum, scal);
+    k_ref_reduce<<<nw, 256, 0, st>>>(nw, G, a, b, C2sum, scal, v0w);
     msd_note_launch();
 }
