@@ -110,6 +110,39 @@ def test_split_catches_a_dropped_exchange_matrix():
     assert abs(bad - want) > 1e-6 * max(1.0, abs(want))
 
 
+def _lambda(L, occ, part, hole_pos, phi):
+    """Lambda_g[(h, p)] = (G L_g (I - G))[H_h][P_p] from the rows occ of G,
+    per vector g (the definition the energy's Gram form uses)."""
+    Gr = (phi @ np.linalg.inv(phi[occ])).T
+    F = np.einsum("jq,gqr->gjr", Gr, L)
+    T, FP, GP = F[:, :, occ], F[:, :, part], Gr[:, part]
+    lam = FP - np.einsum("gjl,lp->gjp", T, GP)
+    return lam[:, hole_pos, :].reshape(L.shape[0], -1), Gr
+
+
+@pytest.mark.parametrize("M,n,G,seed", [(9, 3, 5, 4), (12, 5, 8, 5)])
+def test_reference_part_of_v0_lambda_sum_is_a_one_body_term(M, n, G, seed):
+    """sum_g C_g Lambda_g equals the one-body term (G J (I - G))[H][P] of
+    J = sum_g C_g L_g, for any weights C_g: the mixed path forms it in FP64
+    with h + J and sums only the walker parts t1_g of V0_g in FP32. A
+    version without the -G[occ][P] part of (I - G) fails."""
+    rng = np.random.default_rng(seed)
+    occ = np.sort(rng.permutation(M)[:n])
+    virt = np.setdiff1d(np.arange(M), occ)
+    part = virt[: max(1, len(virt) // 2)]
+    hole_pos = np.arange(n - min(n, 3), n)
+    L, (phi, _) = _system(rng, M, n, n, G, occ, occ)
+    C = rng.standard_normal(G) + np.einsum("gjj->g", L[:, occ][:, :, occ])
+    lam, Gr = _lambda(L, occ, part, hole_pos, phi)
+    want = C @ lam
+    J = np.einsum("g,gpq->pq", C, L)
+    GJ = Gr @ J                                          # rows occ of G J
+    one = (GJ[:, part] - GJ[:, occ] @ Gr[:, part])[hole_pos].reshape(-1)
+    assert np.allclose(one, want, rtol=1e-12, atol=1e-12 * np.abs(want).max())
+    bad = GJ[:, part][hole_pos].reshape(-1)
+    assert not np.allclose(bad, want, rtol=1e-6, atol=1e-6 * np.abs(want).max())
+
+
 # ---------------------------------------------------------------- slicing
 BETA, S, KCH = 7, 5, 512
 
