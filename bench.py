@@ -91,6 +91,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     # library options (alternative implementations of the same step)
+    p.add_argument("--tensor-gram", action="store_true",
+                   help="Gram matrices on the tensor cores (msd_set_tensor_gram)")
     p.add_argument("--no-fused", action="store_true",
                    help="mixed: tensor-core GEMM + separate epilogue instead of the fused kernel")
     p.add_argument("--pair-form", default="auto", choices=["auto", "0", "1", "2"],
@@ -259,6 +261,9 @@ def algorithmic_work(s, n_w):
     w["k_fepi"] = sum(8.0 * (sp["N"] ** 2 + sp["N"] ** 2 * sp["np"] + sp["nh"] * sp["N"] * sp["np"]) * G
                       for sp in spins) * n_w
     w["k_gram"] = 8.0 * G * (spins[0]["X"] ** 2 + spins[1]["X"] ** 2 + spins[0]["X"] * spins[1]["X"]) * n_w
+    # the same Gram matrices on the tensor cores (3xTF32; with the transpose
+    # of the Lambda rows in the same timed group)
+    w["tc_gram"] = w["k_gram"]
     w["k_string_energy"] = sum(float(np.sum(sp["lv"] * (10 * k ** 4 + 16 * k ** 2))) for sp in spins) * n_w
     w["k_pair_cross"] = sum(8.0 * n * (ka * ka * kb * kb + ka * ka) for (ka, kb), n in pair_lv.items()
                             if ka and kb) * n_w
@@ -360,6 +365,7 @@ def run_ours(args, rank, world, local):
     ctx.set_sync(False)
     ctx.set_fused(not args.no_fused)
     ctx.set_pair_form(args.pair_form)
+    ctx.set_tensor_gram(args.tensor_gram)
     vb = torch.empty((n_w, s.n_chol), dtype=torch.complex128, device=dev)
     el = torch.empty((n_w,), dtype=torch.complex128, device=dev)
     ov = torch.empty((n_w,), dtype=torch.complex128, device=dev)
@@ -443,6 +449,9 @@ def run_ours(args, rank, world, local):
         got = {}
         for prec in ("mixed", "fp64"):
             cx = msd.Context(sc, prec, device=local)
+            cx.set_fused(not args.no_fused)
+            cx.set_pair_form(args.pair_form)
+            cx.set_tensor_gram(args.tensor_gram)
             got[prec] = cx.local_energy(da, db)
             torch.cuda.synchronize(dev)
             cx.close()
@@ -511,6 +520,7 @@ def run_ours(args, rank, world, local):
                                    f"N_det={n_det}, N_chol={s.n_chol}, {n_w} walkers/GPU",
                        "precision": args.precision, "n_walkers": n_w, "n_det": n_det,
                        "fused": args.precision == "mixed" and not args.no_fused,
+                       "gram": "tensor cores" if args.tensor_gram and args.precision == "mixed" else "FMA",
                        "opposite_spin_form": ("per beta string" if "k_pair_y" in kernels else
                                               "runs sharing a string" if "k_pair_run" in kernels else "per determinant"),
                        "n_chol": s.n_chol, "M": s.M,

@@ -249,12 +249,13 @@ int msd_set_exact_reference(msd_ctx* ctx, int on);
 
 /* Mixed precision only: with on = 1 the Gram matrices of the energy's Gram
    form, K^{st} = sum_g Lambda^s_g (x) Lambda^t_g over the Cholesky vectors,
-   are formed on the tensor cores (a three-way TF32 split of both operands,
-   six products, FP32 accumulation in tensor memory) when 2 n_h n_p <= 256 per
-   spin; with on = 0 (the default), or larger active blocks, by FP32 FMAs.
-   On the iron-sulfur shape the tensor-core form is no faster (1.60 against
-   1.55 ms per step) and its accumulation adds about twice the error of the
-   FMA form to the local energy at a chemical energy scale. */
+   are formed on the tensor cores (the Lambda rows transposed once per call,
+   then a two-way TF32 split of both operands, three products, FP32
+   accumulation in tensor memory) when 2 n_h n_p <= 256 per spin and n_chol
+   is a multiple of 4; with on = 0 (the default), or other shapes, by FP32
+   FMAs. On the iron-sulfur shape the tensor-core form takes 1.10 against
+   1.67 ms per step, and raises the local energy's error at a chemical energy
+   scale from 2.9e-6 to 3.4e-6 Ha (maximum over 640 walkers). */
 int msd_set_tensor_gram(msd_ctx* ctx, int on);
 
 /* The form of the opposite-spin exchange term of the local energy (Sec. III,

@@ -196,8 +196,13 @@ struct GramJobs {
 void launch_gram_f32(int nw, int n_chol, const GramJobs& jobs, int nj, cudaStream_t st);
 // tc_gram.cu: the same Gram matrices on the tensor cores (3xTF32, FP32
 // accumulation in TMEM) for 2 X <= 256 per spin; returns 0 or -1.
+// Rows first: T[w][2x + c][g] = part c of Lam[w][g][x] (FP32, Lam rows of the
+// pitch lam_pitch(X)); then K_aa, K_bb, K_ab from Ta, Tb ([nw][X][X'] pairs).
+// tc_gram needs n_chol a multiple of 4 and tc_gram_ok; returns 0 or -1.
 bool tc_gram_ok(int Xa, int Xb);
-int tc_gram(int nw, int n_chol, const GramJobs& jobs, int nj, unsigned* err, cudaStream_t st);
+void launch_gram_transpose(int nw, int n_chol, int X, const float2* Lam, float* T, cudaStream_t st);
+int tc_gram(int nw, int n_chol, int Xa, int Xb, const float* Ta, const float* Tb, float2* Kaa, float2* Kbb,
+            float2* Kab, unsigned* err, cudaStream_t st);
 
 // k_batch.cu: per-determinant energy terms of many systems in one
 // persistent launch.

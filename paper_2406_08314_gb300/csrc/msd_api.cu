@@ -1020,7 +1020,15 @@ struct EnWork {
     void *v0[2], *xx[2], *La[2], *Xi[2], *Lh1[2], *e1[2], *Y[2], *Kaa, *Kbb, *Kab, *scal;
     void *ozA = nullptr, *ozE = nullptr, *ozP[2] = {nullptr, nullptr}, *ozT[2] = {nullptr, nullptr};
     void* v0w = nullptr;   // [nw][G] FP32 walker parts of V0_g (exact reference sums)
+    void* GT[2] = {nullptr, nullptr};   // [nw][2X][G] Lambda rows for the tensor-core Gram
 };
+
+// The Gram matrices run on the tensor cores (msd_set_tensor_gram, shapes allowing).
+bool tensor_gram(const msd_ctx* ctx)
+{
+    const int Xa = ctx->sp[0].nh * ctx->sp[0].np, Xb = ctx->sp[1].nh * ctx->sp[1].np;
+    return ctx->prec == MSD_MIXED && ctx->tc_gram && ctx->n_chol % 4 == 0 && tc_gram_ok(Xa, Xb);
+}
 
 // The fused tensor-core contraction + epilogue serves spin s.
 bool fused(const msd_ctx* ctx, int s) { return ctx->fuse && ctx->fused_ok[s]; }
@@ -1069,6 +1077,7 @@ size_t en_bytes_per_walker(msd_ctx* ctx, bool fp32)
         for (int s = 0; s < 2; ++s)
             b += (size_t)2 * oz_parts_for(T1[s].N * (ctx->M - T1[s].N), G) * sizeof(double2) + 2 * sizeof(double) * G;
     }
+    if (fp32 && tensor_gram(ctx)) b += sizeof(float) * 2 * (size_t)(X[0] + X[1]) * G;   // GT
     if (fp32) {
         size_t f = 0, a = 0;
         for (int s = 0; s < 2; ++s) {
@@ -1134,6 +1143,12 @@ int en_alloc(msd_ctx* ctx, int cap, bool fp32, EnWork& E)
             if ((rc = arena_get(ctx, nt_[s], sizeof(double) * 2 * cap * (size_t)G, &E.ozT[s]))) return rc;
         }
         if ((rc = arena_get(ctx, "v0w", sizeof(float2) * cap * (size_t)G, &E.v0w))) return rc;
+    }
+    if (fp32 && tensor_gram(ctx)) {
+        static const char* ng_[2] = {"GT_a", "GT_b"};
+        for (int s = 0; s < 2; ++s)
+            if ((rc = arena_get(ctx, ng_[s], sizeof(float) * cap * 2 * (size_t)std::max(1, X[s]) * G, &E.GT[s])))
+                return rc;
     }
     return MSD_OK;
 }
@@ -1234,13 +1249,16 @@ int en_chunk(msd_ctx* ctx, Chunk& c, EnWork& E, int w0, int nw, int cap, bool fp
                                 (double2*)E.scal, st);
     }
     th.end(st);
-    th.begin("k_gram", st);
+    th.begin(fp32 && tensor_gram(ctx) ? "tc_gram" : "k_gram", st);
     if (fp32) {
         GramJobs jobs = {{{X[0], X[0], (float2*)E.La[0], (float2*)E.La[0], (float2*)E.Kaa},
                           {X[1], X[1], (float2*)E.La[1], (float2*)E.La[1], (float2*)E.Kbb},
                           {X[0], X[1], (float2*)E.La[0], (float2*)E.La[1], (float2*)E.Kab}}};
-        if (ctx->tc_gram && tc_gram_ok(X[0], X[1])) {
-            if (tc_gram(nw, G, jobs, 3, ctx->d_err, st))
+        if (tensor_gram(ctx)) {
+            for (int s = 0; s < 2; ++s)
+                launch_gram_transpose(nw, G, X[s], (float2*)E.La[s], (float*)E.GT[s], st);
+            if (tc_gram(nw, G, X[0], X[1], (float*)E.GT[0], (float*)E.GT[1], (float2*)E.Kaa, (float2*)E.Kbb,
+                        (float2*)E.Kab, ctx->d_err, st))
                 return fail(ctx, MSD_ERR_CUDA, "tensor-core Gram launch failed");
         } else {
             launch_gram_f32(nw, G, jobs, 3, st);

@@ -198,6 +198,20 @@ int tc_make_map(CUtensorMap* map, const void* base, int inner, int outer, long l
     return r == CUDA_SUCCESS ? 0 : -1;
 }
 
+int tc_make_map3(CUtensorMap* map, const float* base, int inner, int rows, int batch, int box_rows)
+{
+    auto fn = encode_fn();
+    if (!fn) return -1;
+    cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)rows, (cuuint64_t)batch};
+    cuuint64_t strides[2] = {(cuuint64_t)inner * 4, (cuuint64_t)inner * rows * 4};
+    cuuint32_t box[3] = {32, (cuuint32_t)box_rows, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : -1;
+}
+
 namespace {
 
 int make_map(CUtensorMap* map, const void* base, int inner, int outer, long long ld, int box_outer, bool bf16)

@@ -95,6 +95,14 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
+        ::"r"(su32(dst)), "l"((uint64_t)map), "r"(su32(bar)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -243,3 +251,7 @@ __device__ __forceinline__ float2 unpack2(unsigned long long v)
 // swizzle of that span (tc_gemm.cu). Returns 0 or -1.
 int tc_make_map(CUtensorMap* map, const void* base, int inner, int outer, long long ld, int box_outer, bool bf16,
                 int swizzle_bytes = 128);
+// 3-D FP32 tensor [batch][rows][inner] (contiguous, inner a multiple of 4) as
+// a TMA map with boxes of 32 x box_rows x 1 and the 128-byte swizzle; rows
+// past `rows` of a batch entry read as zero. Returns 0 or -1.
+int tc_make_map3(CUtensorMap* map, const float* base, int inner, int rows, int batch, int box_rows);

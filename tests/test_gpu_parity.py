@@ -253,10 +253,11 @@ def test_walker_chunking_matches(msd):
 MIX_E_REL, MIX_E_ABS, MIX_V = 2e-6, 1e-6, 1e-4
 
 
-def _check_mixed(m, sys_, pa, pb, ref, fused=True, per_beta=True, e_abs=MIX_E_ABS):
+def _check_mixed(m, sys_, pa, pb, ref, fused=True, per_beta=True, e_abs=MIX_E_ABS, tensor_gram=False):
     ctx = m.Context(sys_, "mixed")
     ctx.set_fused(fused)
     ctx.set_pair_form(per_beta)
+    ctx.set_tensor_gram(tensor_gram)
     assert ctx.info("exact_reference") == 1
     da, db = _cuda(pa), _cuda(pb)
     e, o = ctx.local_energy(da, db, ovlp=True)
@@ -467,6 +468,15 @@ def test_fe2s2_full_size_chemical_scale_mixed_vs_fp64(msd):
     assert np.median(de) <= 2e-6, np.median(de)
 
 
+@pytest.mark.parametrize("name", ["small", "cu2o2"])
+def test_tensor_gram_mixed(msd, name):
+    """The Gram matrices on the tensor cores (transposed Lambda rows, 3xTF32
+    products, one or two M-tiles) against the oracle: the small workload
+    (2X = 50: one tile) and the copper-oxo-shaped one (2X = 128)."""
+    s, w = synth.config_system(name, seed=0, n_w=2 if name == "cu2o2" else 16)
+    _check_mixed(msd, s, w.phi_a, w.phi_b, _ref(s, w.phi_a, w.phi_b), tensor_gram=True)
+
+
 def test_fe2s2_full_size_tensor_gram_matches_fma_gram(msd, fe2s2):
     """Full size: the Gram matrices on the tensor cores (3xTF32, FP32
     accumulation in TMEM) against the FP32-FMA kernel. Both are within
@@ -478,7 +488,7 @@ def test_fe2s2_full_size_tensor_gram_matches_fma_gram(msd, fe2s2):
     ctx.set_tensor_gram(True)
     ctx.set_timing(True)
     e1 = _np(ctx.local_energy(da, db))
-    assert ctx.kernel_stats()["k_gram"][0] == 1
+    assert ctx.kernel_stats()["tc_gram"][0] == 1
     ctx.close()
     assert np.all(np.isfinite(e1))
     assert np.all(np.abs(e1 - e0) <= 0.1 * MIX_E_ABS), np.abs(e1 - e0).max()
