@@ -358,32 +358,53 @@ void launch_strings(const SpinTables& tb, int nw, const double2* Gact, double2* 
 // CI weights per string: w_s = sum over determinants I containing string s
 // of c_I * r_other(I), so that sum_I c_I r_a r_b = sum_a r_a w_a. Stored is
 // the product r_s w_s (what every consumer needs); for spin alpha the block
-// also reduces it into per-walker partial sums.
+// also reduces it into per-walker partial sums. A thread takes one string
+// for WB walkers: each entry of the string's determinant list (index and
+// coefficient) is read once and feeds WB independent gathers; every
+// walker's sum runs in list order as with one walker per thread.
+template <int WB>
 __global__ void __launch_bounds__(256)
-k_weights(SpinTables tb, const double2* __restrict__ r_self, const double2* __restrict__ r_other,
+k_weights(SpinTables tb, int nw, const double2* __restrict__ r_self, const double2* __restrict__ r_other,
           int n_other, double2* __restrict__ wts, double2* __restrict__ part, int nslot,
           int slot0)
 {
-    const int w = blockIdx.y;
+    const int w0 = blockIdx.y * WB;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    double2 rw = cz(0, 0);
+    double2 rw[WB];
+#pragma unroll
+    for (int k = 0; k < WB; ++k) rw[k] = cz(0, 0);
     if (s < tb.n_str) {
-        double2 acc = cz(0, 0);
-        const double2* ro = r_other + (size_t)w * n_other;
-        for (int e = tb.csr_off[s]; e < tb.csr_off[s + 1]; ++e)
-            acc = cadd(acc, cscale(ro[tb.csr_other[e]], tb.csr_c[e]));
-        rw = cmul(r_self[(size_t)w * tb.n_str + s], acc);
-        wts[(size_t)w * tb.n_str + s] = rw;
+        double2 acc[WB];
+#pragma unroll
+        for (int k = 0; k < WB; ++k) acc[k] = cz(0, 0);
+        const double2* ro = r_other + (size_t)w0 * n_other;
+        const int e1 = tb.csr_off[s + 1];
+        for (int e = tb.csr_off[s]; e < e1; ++e) {
+            const int o = tb.csr_other[e];
+            const double c = tb.csr_c[e];
+#pragma unroll
+            for (int k = 0; k < WB; ++k)
+                if (w0 + k < nw) acc[k] = cadd(acc[k], cscale(ro[(size_t)k * n_other + o], c));
+        }
+#pragma unroll
+        for (int k = 0; k < WB; ++k)
+            if (w0 + k < nw) {
+                rw[k] = cmul(r_self[(size_t)(w0 + k) * tb.n_str + s], acc[k]);
+                wts[(size_t)(w0 + k) * tb.n_str + s] = rw[k];
+            }
     }
     if (part) {
         __shared__ double2 red[256];
-        red[threadIdx.x] = rw;
-        __syncthreads();
-        for (int o = blockDim.x / 2; o; o >>= 1) {
-            if (threadIdx.x < o) red[threadIdx.x] = cadd(red[threadIdx.x], red[threadIdx.x + o]);
+        for (int k = 0; k < WB && w0 + k < nw; ++k) {
+            red[threadIdx.x] = rw[k];
             __syncthreads();
+            for (int o = blockDim.x / 2; o; o >>= 1) {
+                if (threadIdx.x < o) red[threadIdx.x] = cadd(red[threadIdx.x], red[threadIdx.x + o]);
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) part[(size_t)(w0 + k) * nslot + slot0 + blockIdx.x] = red[0];
+            __syncthreads();   // red is reused by the next walker
         }
-        if (threadIdx.x == 0) part[(size_t)w * nslot + slot0 + blockIdx.x] = red[0];
     }
 }
 
@@ -392,8 +413,10 @@ int weights_blocks(const SpinTables& tb) { return (tb.n_str + 255) / 256; }
 void launch_weights(const SpinTables& tb, int nw, const double2* r_self, const double2* r_other,
                     int n_other, double2* wts, double2* part, int nslot, int slot0, cudaStream_t st)
 {
-    dim3 grid(weights_blocks(tb), nw);
-    k_weights<<<grid, 256, 0, st>>>(tb, r_self, r_other, n_other, wts, part, nslot, slot0); msd_note_launch();
+    constexpr int WB = 4;
+    dim3 grid(weights_blocks(tb), (nw + WB - 1) / WB);
+    k_weights<WB><<<grid, 256, 0, st>>>(tb, nw, r_self, r_other, n_other, wts, part, nslot, slot0);
+    msd_note_launch();
 }
 
 // ------------------------------------------------------------------------
