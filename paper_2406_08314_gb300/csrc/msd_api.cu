@@ -123,6 +123,10 @@ struct msd_ctx {
     std::vector<cudaEvent_t> ev_pool;
     int open_k = -1;
     cudaEvent_t open_ev = nullptr;
+    // host inputs: the beta walkers are copied on their own stream while the
+    // alpha spin's first kernels run (created on first use)
+    cudaStream_t copy_st = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_b = nullptr;
     TimerHook hook;
     // TF32 hi/lo splits of the half-rotated Cholesky vectors (mixed path)
     bool mixed_ready = false;
@@ -772,14 +776,25 @@ struct Staged {
     const double2* pa;
     const double2* pb;
     bool host_any;
+    cudaEvent_t b_ready = nullptr;   // the beta copy has landed (wait before its first use)
 };
 
+// With defer_b, host beta walkers are copied on the context's copy stream
+// (after the work already on st, which may still use the staging buffer);
+// out.b_ready then marks the copy's completion.
 int stage_inputs(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b,
-                 cudaStream_t st, Staged& out)
+                 cudaStream_t st, Staged& out, bool defer_b = false)
 {
     const size_t ba = sizeof(double2) * (size_t)n_w * ctx->M * ctx->n[0];
     const size_t bb = sizeof(double2) * (size_t)n_w * ctx->M * ctx->n[1];
     out.host_any = false;
+    out.b_ready = nullptr;
+    if (defer_b && !is_device_ptr(phi_b) && !ctx->copy_st) {
+        if (cudaStreamCreateWithFlags(&ctx->copy_st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->ev_b, cudaEventDisableTiming) != cudaSuccess)
+            return fail(ctx, MSD_ERR_CUDA, "copy stream could not be created");
+    }
     if (is_device_ptr(phi_a)) out.pa = (const double2*)phi_a;
     else {
         void* p; int rc = arena_get(ctx, "stage_phi_a", ba, &p); if (rc) return rc;
@@ -789,7 +804,15 @@ int stage_inputs(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_b
     if (is_device_ptr(phi_b)) out.pb = (const double2*)phi_b;
     else {
         void* p; int rc = arena_get(ctx, "stage_phi_b", bb, &p); if (rc) return rc;
-        CK(cudaMemcpyAsync(p, phi_b, bb, cudaMemcpyHostToDevice, st));
+        if (defer_b) {
+            CK(cudaEventRecord(ctx->ev_in, st));
+            CK(cudaStreamWaitEvent(ctx->copy_st, ctx->ev_in, 0));
+            CK(cudaMemcpyAsync(p, phi_b, bb, cudaMemcpyHostToDevice, ctx->copy_st));
+            CK(cudaEventRecord(ctx->ev_b, ctx->copy_st));
+            out.b_ready = ctx->ev_b;
+        } else {
+            CK(cudaMemcpyAsync(p, phi_b, bb, cudaMemcpyHostToDevice, st));
+        }
         out.pb = (const double2*)p; out.host_any = true;
     }
     return MSD_OK;
@@ -895,6 +918,7 @@ int run_overlap_part(msd_ctx* ctx, const Staged& in, int w0, int nw, int cap, Ch
     SpinTables T[2] = {tables(ctx->sp[0], cap), tables(ctx->sp[1], cap)};
     const double2* phi[2] = {in.pa + (size_t)w0 * M * ctx->n[0], in.pb + (size_t)w0 * M * ctx->n[1]};
     for (int s = 0; s < 2; ++s) {
+        if (s == 1 && in.b_ready) CK(cudaStreamWaitEvent(st, in.b_ready, 0));
         th.begin("k_ref", st);
         launch_ref(phi[s], nw, M, ctx->n[s], T[s], c.Gr[s], c.O0[s], c.Gact[s], ctx->d_err, st);
         th.end(st);
@@ -1322,7 +1346,13 @@ int evaluate_impl(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_
     if (fp32 && (rc = prepare_mixed(ctx, st))) return rc;
     if (fp32 && e_loc && exact_ref_on(ctx) && (rc = prepare_exact_ref(ctx, st))) return rc;
     Staged in;
-    if ((rc = stage_inputs(ctx, n_w, phi_a, phi_b, st, in))) return rc;
+    if ((rc = stage_inputs(ctx, n_w, phi_a, phi_b, st, in, true))) return rc;
+    // the caller's beta buffer is read by the copy stream: it has been read
+    // completely before this call returns, on every path
+    struct CopyDone {
+        cudaEvent_t e;
+        ~CopyDone() { if (e) cudaEventSynchronize(e); }
+    } copy_done{in.b_ready};
     Out o_v, o_e, o_ov;
     if ((rc = stage_output(ctx, "out_vbias", vbias, (size_t)n_w * ctx->n_chol, o_v))) return rc;
     if ((rc = stage_output(ctx, "out_eloc", e_loc, n_w, o_e))) return rc;
@@ -1680,6 +1710,9 @@ void msd_destroy(msd_ctx* ctx)
     cudaFreeHost(ctx->h_err);
     for (auto& p : ctx->pending) { ctx->ev_pool.push_back(p.a); ctx->ev_pool.push_back(p.b); }
     for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+    if (ctx->copy_st) cudaStreamDestroy(ctx->copy_st);
+    if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+    if (ctx->ev_b) cudaEventDestroy(ctx->ev_b);
     delete ctx;
 }
 
