@@ -264,7 +264,12 @@ def algorithmic_work(s, n_w):
     # the same Gram matrices on the tensor cores (3xTF32; with the transpose
     # of the Lambda rows in the same timed group)
     w["tc_gram"] = w["k_gram"]
-    w["k_string_energy"] = sum(float(np.sum(sp["lv"] * (10 * k ** 4 + 16 * k ** 2))) for sp in spins) * n_w
+    # same-spin string term in its antisymmetrized pair form: per string the
+    # linear part (k^2 complex MACs) and, per pair of index pairs, a 2x2
+    # minor of B (two complex products and a difference) times the pair
+    # table entry: 8 k^2 + 22 C(k,2)^2 flops
+    w["k_string_energy"] = sum(float(np.sum(sp["lv"] * (8 * k ** 2 + 22 * (k * (k - 1) // 2) ** 2)))
+                               for sp in spins) * n_w
     w["k_pair_cross"] = sum(8.0 * n * (ka * ka * kb * kb + ka * ka) for (ka, kb), n in pair_lv.items()
                             if ka and kb) * n_w
     # the runs form evaluates the same term (the algorithmic work of the

@@ -6,9 +6,8 @@
 //   r_s w_s e_s,  e_s = sum_ij B_ij Y[h_j][p_i] + 1/2 (Qc - Qx),
 //   Qc = sum_ijkl B_ij B_kl K[(h_j,p_i)][(h_l,p_k)],
 //   Qx = sum_ijkl B_ij B_kl K[(h_j,p_k)][(h_l,p_i)]
-// (K = the walker's same-spin Gram matrix and Y its linear coefficients, in
-// shared memory). The outer (i, j) loop runs at run time; the inner (k, l)
-// loop is unrolled over the inverse minor held in registers.
+// (K = the walker's same-spin Gram matrix and Y its linear coefficients),
+// evaluated through the antisymmetrized pair table (below).
 //
 // pair_cross_term: opposite-spin term of determinant I = (a, b) with levels
 // (ka, KB) of walker w (pair_cross_value: X_ab alone):
@@ -23,118 +22,90 @@
 template <typename T>
 using cplx_t = typename std::conditional<std::is_same<T, float>::value, float2, double2>::type;
 
+// Index of the pair (a, b), a < b < n, among the n (n - 1) / 2 pairs in
+// lexicographic order.
+__host__ __device__ __forceinline__ int pair_index(int a, int b, int n) { return a * n - a * (a + 1) / 2 + (b - a - 1); }
+
 // e_s of string s = bucket[KL] + sl (unweighted); string_energy_term below
-// multiplies it by r_s w_s.
-template <int KL, typename T>
+// multiplies it by r_s w_s. K is symmetric (a same-spin Gram matrix), so
+//   A[h,h';p,p'] = K[(h,p)][(h',p')] - K[(h,p')][(h',p)]
+// is antisymmetric in (h, h') and in (p, p'), and the four orderings of two
+// index pairs collapse:
+//   (Qc - Qx) / 2 = sum_{i<k} sum_{j<l} (b_ij b_kl - b_il b_kj) A[h_j,h_l;p_i,p_k]
+// (the holes and particles of a string are ascending), C(k,2)^2 terms
+// instead of 2 k^4 gathers. ATAB: kt is A as a table [C(nh,2)][C(np,2)]
+// (pair_index order, computed in precision T); otherwise kt is K and each
+// difference is formed where it is used, in the same precision, so both
+// give the same value.
+template <int KL, typename T, bool ATAB = false>
 __device__ __forceinline__ double2 string_energy_value(const SpinTables& tb, int w, int sl, int ns,
-                                                       const void* __restrict__ Bin, const cplx_t<T>* ks,
+                                                       const void* __restrict__ Bin, const cplx_t<T>* kt,
                                                        const cplx_t<T>* ys)
 {
     using T2 = cplx_t<T>;
-    const int X = tb.nh * tb.np, np = tb.np;
+    const int X = tb.nh * tb.np, np = tb.np, nh = tb.nh, npp = np * (np - 1) / 2;
     const int s = tb.bucket[KL] + sl;
     const uint8_t* sh = tb.str_h + (size_t)s * MSD_KMAX;
     const uint8_t* sp = tb.str_p + (size_t)s * MSD_KMAX;
-    int hx[KL], px[KL];   // hole row offset h*np, particle index p
+    int hh[KL], pp[KL];   // hole and particle indices, ascending
 #pragma unroll
-    for (int i = 0; i < KL; ++i) { hx[i] = sh[i] * np; px[i] = sp[i]; }
+    for (int i = 0; i < KL; ++i) { hh[i] = sh[i]; pp[i] = sp[i]; }
     const T2* B = reinterpret_cast<const T2*>(Bin) + (size_t)tb.b_off[KL] + ((size_t)w * ns + sl) * (KL * KL);
-    T2 b[KL][KL];
+    constexpr bool REG = KL <= 4;   // the inverse minor in registers (levels 5, 6: from memory)
+    T2 b[REG ? KL : 1][REG ? KL : 1];
+    if constexpr (REG) {
+#pragma unroll
+        for (int i = 0; i < KL; ++i)
+#pragma unroll
+            for (int j = 0; j < KL; ++j) b[i][j] = B[i * KL + j];
+    }
+    auto bij = [&](int i, int j) -> T2 {
+        if constexpr (REG) return b[i][j];
+        else return B[i * KL + j];
+    };
+    T lr = 0, li = 0;      // linear part sum_ij b_ij Y[(h_j, p_i)]
 #pragma unroll
     for (int i = 0; i < KL; ++i)
 #pragma unroll
-        for (int j = 0; j < KL; ++j) b[i][j] = B[i * KL + j];
-    T lr = 0, li = 0;      // linear part
-    T qr = 0, qi = 0;      // Qc - Qx
-    if constexpr (KL <= 4) {
-        // fully unrolled: every index and B value is in registers, the loop
-        // body reads shared memory only. K is symmetric (a same-spin Gram
-        // matrix), and so is each summand of Q under (i, j) <-> (k, l):
-        // b_ij b_kl K[(j,i)][(l,k)] and b_ij b_kl K[(j,k)][(l,i)] map to
-        // themselves. So only the pairs (k, l) >= (i, j) (row-major order)
-        // are summed, the others counted by doubling: k^2 (k^2 + 1) / 2
-        // instead of k^4 pairs (the skipped pairs vanish at compile time).
-#pragma unroll
-        for (int i = 0; i < KL; ++i) {
-#pragma unroll
-            for (int j = 0; j < KL; ++j) {
-                const int xij = hx[j] + px[i];
-                const T2 bij = b[i][j];
-                const T2 y = ys[xij];
-                lr += bij.x * y.x - bij.y * y.y;
-                li += bij.x * y.y + bij.y * y.x;
-                const T2* kc_row = ks + (size_t)xij * X;
-                T zr = 0, zi = 0;      // pairs after (i, j)
-                T dgr = 0, dgi = 0;    // the pair (i, j) itself
-#pragma unroll
-                for (int k = 0; k < KL; ++k) {
-                    const T2* kx_row = ks + (size_t)(hx[j] + px[k]) * X + px[i];
-#pragma unroll
-                    for (int l = 0; l < KL; ++l) {
-                        if (k * KL + l < i * KL + j) continue;
-                        // K[(h_j,p_i)][(h_l,p_k)] - K[(h_j,p_k)][(h_l,p_i)]
-                        const T2 kc = kc_row[hx[l] + px[k]];
-                        const T2 kx = kx_row[hx[l]];
-                        const T dr = kc.x - kx.x, di = kc.y - kx.y;
-                        const T tr = b[k][l].x * dr - b[k][l].y * di;
-                        const T ti = b[k][l].x * di + b[k][l].y * dr;
-                        if (k * KL + l == i * KL + j) {
-                            dgr = tr;
-                            dgi = ti;
-                        } else {
-                            zr += tr;
-                            zi += ti;
-                        }
-                    }
-                }
-                zr = dgr + 2 * zr;
-                zi = dgi + 2 * zi;
-                qr += bij.x * zr - bij.y * zi;
-                qi += bij.x * zi + bij.y * zr;
-            }
+        for (int j = 0; j < KL; ++j) {
+            const T2 bv = bij(i, j), y = ys[hh[j] * np + pp[i]];
+            lr += bv.x * y.x - bv.y * y.y;
+            li += bv.x * y.y + bv.y * y.x;
         }
-    } else {
-        // levels 5 and 6 (rare strings): (i, j) at run time, so their
-        // indices and B values come from memory
-#pragma unroll 1
-        for (int i = 0; i < KL; ++i) {
-            const int pi = sp[i];
-#pragma unroll 1
-            for (int j = 0; j < KL; ++j) {
-                const int hj = sh[j] * np;
-                const int xij = hj + pi;
-                const T2 bij = B[i * KL + j];
-                const T2 y = ys[xij];
-                lr += bij.x * y.x - bij.y * y.y;
-                li += bij.x * y.y + bij.y * y.x;
-                const T2* kc_row = ks + (size_t)xij * X;
-                T zr = 0, zi = 0;
+    T qr = 0, qi = 0;      // (Qc - Qx) / 2
 #pragma unroll
-                for (int k = 0; k < KL; ++k) {
-                    const T2* kx_row = ks + (size_t)(hj + px[k]) * X + pi;
+    for (int i = 0; i < KL; ++i)
 #pragma unroll
-                    for (int l = 0; l < KL; ++l) {
-                        const T2 kc = kc_row[hx[l] + px[k]];
-                        const T2 kx = kx_row[hx[l]];
-                        const T dr = kc.x - kx.x, di = kc.y - kx.y;
-                        zr += b[k][l].x * dr - b[k][l].y * di;
-                        zi += b[k][l].x * di + b[k][l].y * dr;
+        for (int k = i + 1; k < KL; ++k) {
+            const int pik = pair_index(pp[i], pp[k], np);
+#pragma unroll
+            for (int j = 0; j < KL; ++j)
+#pragma unroll
+                for (int l = j + 1; l < KL; ++l) {
+                    T2 a;
+                    if constexpr (ATAB) {
+                        a = kt[(size_t)pair_index(hh[j], hh[l], nh) * npp + pik];
+                    } else {
+                        const T2 kc = kt[(size_t)(hh[j] * np + pp[i]) * X + hh[l] * np + pp[k]];
+                        const T2 kx = kt[(size_t)(hh[j] * np + pp[k]) * X + hh[l] * np + pp[i]];
+                        a = T2{kc.x - kx.x, kc.y - kx.y};
                     }
+                    const T2 b1 = bij(i, j), b2 = bij(k, l), b3 = bij(i, l), b4 = bij(k, j);
+                    const T mr = (b1.x * b2.x - b1.y * b2.y) - (b3.x * b4.x - b3.y * b4.y);
+                    const T mi = (b1.x * b2.y + b1.y * b2.x) - (b3.x * b4.y + b3.y * b4.x);
+                    qr += mr * a.x - mi * a.y;
+                    qi += mr * a.y + mi * a.x;
                 }
-                qr += bij.x * zr - bij.y * zi;
-                qi += bij.x * zi + bij.y * zr;
-            }
         }
-    }
-    return cz((double)lr + 0.5 * (double)qr, (double)li + 0.5 * (double)qi);
+    return cz((double)lr + (double)qr, (double)li + (double)qi);
 }
 
-template <int KL, typename T>
+template <int KL, typename T, bool ATAB = false>
 __device__ __forceinline__ double2 string_energy_term(const SpinTables& tb, int w, int sl, int ns,
-                                                      const void* __restrict__ Bin, const cplx_t<T>* ks,
+                                                      const void* __restrict__ Bin, const cplx_t<T>* kt,
                                                       const cplx_t<T>* ys, const double2* __restrict__ wts)
 {
-    const double2 e_s = string_energy_value<KL, T>(tb, w, sl, ns, Bin, ks, ys);
+    const double2 e_s = string_energy_value<KL, T, ATAB>(tb, w, sl, ns, Bin, kt, ys);
     return cmul(wts[(size_t)w * tb.n_str + tb.bucket[KL] + sl], e_s);   // wts holds r_s w_s
 }
 

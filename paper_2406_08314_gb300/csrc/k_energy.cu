@@ -308,9 +308,10 @@ void launch_gram(int nw, int Xp, int Xq, int n_chol, const double2* P, const dou
 // Same-spin per-string energy (get_ss and the one-body / Coulomb linear
 // parts): e_s = sum_ij B_ij Y[h_j][p_i] + 1/2 (Qc - Qx), accumulated as
 // r_s w_s e_s into per-walker partial sums. Precision T for B, K and the
-// arithmetic; the block sum is FP64. The outer (i, j) loop runs at run
-// time (its operands are read once); the inner (k, l) loop is unrolled over
-// the string's inverse minor held in registers.
+// arithmetic; the block sum is FP64. The block first forms the walker's
+// antisymmetrized pair table of K (C(nh,2) C(np,2) entries, against X^2 for
+// K) in shared memory; each string then takes C(k,2)^2 gathers of it for
+// (Qc - Qx) / 2 (string_energy_value).
 template <int KL, typename T>
 __global__ void __launch_bounds__(SE_THREADS)
 k_string_energy(SpinTables tb, const double2* __restrict__ wts,
@@ -319,13 +320,23 @@ k_string_energy(SpinTables tb, const double2* __restrict__ wts,
 {
     using T2 = typename std::conditional<std::is_same<T, float>::value, float2, double2>::type;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int X = tb.nh * tb.np, np = tb.np;
-    T2* ks = reinterpret_cast<T2*>(smraw);   // [X][X]
-    T2* ys = ks + X * X;                     // [X]
+    const int X = tb.nh * tb.np, np = tb.np, nh = tb.nh;
+    const int nhp = nh * (nh - 1) / 2, npp = np * (np - 1) / 2;
+    T2* as = reinterpret_cast<T2*>(smraw);   // [C(nh,2)][C(np,2)] antisymmetrized pairs of K
+    T2* ys = as + nhp * npp;                 // [X]
     __shared__ double2 red[SE_THREADS];
     const int w = blockIdx.y, t = threadIdx.x;
     const T2* Kw = reinterpret_cast<const T2*>(Kin) + (size_t)w * X * X;
-    for (int e = t; e < X * X; e += blockDim.x) ks[e] = Kw[e];
+    // A[(h,h')][(p,p')] = K[(h,p)][(h',p')] - K[(h,p')][(h',p)], h < h', p < p'
+    for (int e = t; e < nhp * npp; e += blockDim.x) {
+        int a = e / npp, c = e - a * npp, h = 0, p = 0;
+        while (a >= nh - 1 - h) { a -= nh - 1 - h; ++h; }
+        while (c >= np - 1 - p) { c -= np - 1 - p; ++p; }
+        const int h2 = h + 1 + a, p2 = p + 1 + c;
+        const T2 kc = Kw[(size_t)(h * np + p) * X + h2 * np + p2];
+        const T2 kx = Kw[(size_t)(h * np + p2) * X + h2 * np + p];
+        as[e] = T2{kc.x - kx.x, kc.y - kx.y};
+    }
     const T2* Yw = reinterpret_cast<const T2*>(Yin) + (size_t)w * X;
     for (int e = t; e < X; e += blockDim.x) ys[e] = Yw[e];
     __syncthreads();
@@ -334,7 +345,7 @@ k_string_energy(SpinTables tb, const double2* __restrict__ wts,
     for (int it = 0; it < SE_PER_THREAD; ++it) {
         const int sl = blockIdx.x * (SE_THREADS * SE_PER_THREAD) + it * SE_THREADS + t;
         if (sl >= ns) break;
-        contrib = cadd(contrib, string_energy_term<KL, T>(tb, w, sl, ns, Bin, ks, ys, wts));
+        contrib = cadd(contrib, string_energy_term<KL, T, true>(tb, w, sl, ns, Bin, as, ys, wts));
     }
     red[t] = contrib;
     __syncthreads();
@@ -354,7 +365,8 @@ int string_energy_blocks(const SpinTables& tb, int k)
 size_t string_energy_smem(const SpinTables& tb, bool fp32)
 {
     const int X = tb.nh * tb.np;
-    return (fp32 ? sizeof(float2) : sizeof(double2)) * (size_t)(X * X + X);
+    const size_t pairs = (size_t)(tb.nh * (tb.nh - 1) / 2) * (tb.np * (tb.np - 1) / 2);
+    return (fp32 ? sizeof(float2) : sizeof(double2)) * (pairs + X);
 }
 
 template <int KL>

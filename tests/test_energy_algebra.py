@@ -9,7 +9,10 @@ in numpy on random inputs, independent of the library and the oracle:
 * same-spin quadratic part: with K symmetric, each summand
     b_ij b_kl (K[(j,i)][(l,k)] - K[(j,k)][(l,i)])
   is symmetric under (i, j) <-> (k, l), so the full sum equals the diagonal
-  pairs plus twice the pairs (k, l) > (i, j).
+  pairs plus twice the pairs (k, l) > (i, j);
+* same-spin quadratic part, antisymmetrized: with K symmetric,
+    Qc - Qx = 2 sum_{i<k} sum_{j<l} (b_ij b_kl - b_il b_kj) A[h_j,h_l;p_i,p_k],
+    A[h,h';p,p'] = K[(h,p)][(h',p')] - K[(h,p')][(h',p)].
 """
 import numpy as np
 import pytest
@@ -84,3 +87,58 @@ def test_pair_swap_needs_symmetric_k():
     full = _same_spin_q(b, K, h, p, np_, half=False)
     half = _same_spin_q(b, K, h, p, np_, half=True)
     assert abs(full - half) > 1e-6 * abs(full)
+
+
+def _q_direct(B, K, h, p, npp):
+    k = len(h)
+    x = lambda hh, pp: hh * npp + pp
+    qc = qx = 0
+    for i in range(k):
+        for j in range(k):
+            for kk in range(k):
+                for l in range(k):
+                    qc += B[i, j] * B[kk, l] * K[x(h[j], p[i]), x(h[l], p[kk])]
+                    qx += B[i, j] * B[kk, l] * K[x(h[j], p[kk]), x(h[l], p[i])]
+    return qc - qx
+
+
+def _q_antisym(B, K, h, p, npp):
+    """2 sum_{i<k} sum_{j<l} (B_ij B_kl - B_il B_kj) A[h_j,h_l;p_i,p_k],
+    A[h,h';p,p'] = K[(h,p)][(h',p')] - K[(h,p')][(h',p)]."""
+    k = len(h)
+    x = lambda hh, pp: hh * npp + pp
+    q = 0
+    for i in range(k):
+        for kk in range(i + 1, k):
+            for j in range(k):
+                for l in range(j + 1, k):
+                    a = K[x(h[j], p[i]), x(h[l], p[kk])] - K[x(h[j], p[kk]), x(h[l], p[i])]
+                    q += (B[i, j] * B[kk, l] - B[i, l] * B[kk, j]) * a
+    return 2 * q
+
+
+@pytest.mark.parametrize("k,seed", [(1, 0), (2, 1), (3, 2), (4, 3), (5, 4), (6, 5)])
+def test_same_spin_antisymmetrized_pair_form(k, seed):
+    """With K symmetric, Qc - Qx is carried by the 2x2 minors of B against the
+    pair table A, antisymmetric in the holes and in the particles (the holes
+    and particles of a string ascending): C(k,2)^2 terms."""
+    rng = np.random.default_rng(seed)
+    nh, npp = 8, 7
+    Kr = _cplx(rng, nh * npp, nh * npp)
+    K = Kr + Kr.T
+    h = np.sort(rng.choice(nh, k, replace=False))
+    p = np.sort(rng.choice(npp, k, replace=False))
+    B = _cplx(rng, k, k)
+    want = _q_direct(B, K, h, p, npp)
+    got = _q_antisym(B, K, h, p, npp)
+    assert abs(got - want) <= 1e-12 * max(1.0, abs(want))
+
+
+def test_antisymmetrized_form_needs_symmetric_k():
+    """For a general (non-symmetric) K the rearrangement does not hold."""
+    rng = np.random.default_rng(9)
+    nh, npp, k = 6, 6, 3
+    K = _cplx(rng, nh * npp, nh * npp)
+    h, p = np.array([0, 2, 5]), np.array([1, 3, 4])
+    B = _cplx(rng, k, k)
+    assert abs(_q_antisym(B, K, h, p, npp) - _q_direct(B, K, h, p, npp)) > 1e-3
