@@ -87,8 +87,9 @@ struct SpinTables {
     const int* pos0;    // [M] position of an orbital in occ0, or -1
     const int* hole_pos;   // [nh] position in occ0 of each hole orbital
     const int* part_orb;   // [np] orbital of each particle
-    const uint8_t* str_h;  // [n_str][KMAX] hole indices (0..nh-1), ascending
-    const uint8_t* str_p;  // [n_str][KMAX] particle indices (0..np-1), ascending
+    const uint4* str_hp;   // [n_str] one 16-byte record per string: hole indices (0..nh-1,
+                           // ascending) in bytes 0..5, particle indices (0..np-1,
+                           // ascending) in bytes 8..13, so one vector load fetches both
     const int8_t* str_sign;    // [n_str] parity of the in-place -> sorted reordering
     const int* csr_off;    // [n_str+1] determinants containing each string
     const int* csr_other;  // [nnz] string of the opposite spin in that determinant
@@ -101,6 +102,11 @@ struct SpinTables {
     long long b_per_walker;         // sum_k k^2 * (strings of level k)
     long long cmx_off[MSD_KMAX + 2];  // offset of each bucket's entries in cmx
 };
+
+// Hole / particle index i (< MSD_KMAX) of a string record.
+__device__ __forceinline__ int rec_h(const uint4& r, int i) { return (int)(((i < 4 ? r.x : r.y) >> (8 * (i & 3))) & 0xffu); }
+__device__ __forceinline__ int rec_p(const uint4& r, int i) { return (int)(((i < 4 ? r.z : r.w) >> (8 * (i & 3))) & 0xffu); }
+
 
 // Pair (determinant) tables for the opposite-spin cross term.
 struct PairTables {

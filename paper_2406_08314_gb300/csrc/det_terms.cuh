@@ -45,11 +45,10 @@ __device__ __forceinline__ double2 string_energy_value(const SpinTables& tb, int
     using T2 = cplx_t<T>;
     const int X = tb.nh * tb.np, np = tb.np, nh = tb.nh, npp = np * (np - 1) / 2;
     const int s = tb.bucket[KL] + sl;
-    const uint8_t* sh = tb.str_h + (size_t)s * MSD_KMAX;
-    const uint8_t* sp = tb.str_p + (size_t)s * MSD_KMAX;
+    const uint4 rec = tb.str_hp[s];
     int hh[KL], pp[KL];   // hole and particle indices, ascending
 #pragma unroll
-    for (int i = 0; i < KL; ++i) { hh[i] = sh[i]; pp[i] = sp[i]; }
+    for (int i = 0; i < KL; ++i) { hh[i] = rec_h(rec, i); pp[i] = rec_p(rec, i); }
     const T2* B = reinterpret_cast<const T2*>(Bin) + (size_t)tb.b_off[KL] + ((size_t)w * ns + sl) * (KL * KL);
     constexpr bool REG = KL <= 4;   // the inverse minor in registers (levels 5, 6: from memory)
     T2 b[REG ? KL : 1][REG ? KL : 1];
@@ -134,11 +133,11 @@ __device__ __forceinline__ cplx_t<T> pair_cross_value(const SpinTables& ta, cons
     const int nsa = ta.bucket[ka + 1] - ta.bucket[ka], sa = a - ta.bucket[ka];
     const int nsb = tbb.bucket[KB + 1] - tbb.bucket[KB], sb = b - tbb.bucket[KB];
     int xb[KB][KB];
+    const uint4 rb_rec = tbb.str_hp[b];
 #pragma unroll
     for (int k = 0; k < KB; ++k)
 #pragma unroll
-        for (int l = 0; l < KB; ++l)
-            xb[k][l] = tbb.str_h[(size_t)b * MSD_KMAX + l] * tbb.np + tbb.str_p[(size_t)b * MSD_KMAX + k];
+        for (int l = 0; l < KB; ++l) xb[k][l] = rec_h(rb_rec, l) * tbb.np + rec_p(rb_rec, k);
     const T2* Ba = reinterpret_cast<const T2*>(Ba_in) + (size_t)ta.b_off[ka] + ((size_t)w * nsa + sa) * (ka * ka);
     const T2* Bb = reinterpret_cast<const T2*>(Bb_in) + (size_t)tbb.b_off[KB] + ((size_t)w * nsb + sb) * (KB * KB);
     T2 bb[KB][KB];
@@ -146,15 +145,14 @@ __device__ __forceinline__ cplx_t<T> pair_cross_value(const SpinTables& ta, cons
     for (int k = 0; k < KB; ++k)
 #pragma unroll
         for (int l = 0; l < KB; ++l) bb[k][l] = Bb[k * KB + l];
-    const uint8_t* ah = ta.str_h + (size_t)a * MSD_KMAX;
-    const uint8_t* ap = ta.str_p + (size_t)a * MSD_KMAX;
+    const uint4 ra_rec = ta.str_hp[a];
     T xr = 0, xim = 0;
 #pragma unroll 1
     for (int i = 0; i < ka; ++i)
 #pragma unroll 1
         for (int j = 0; j < ka; ++j) {
             const T2 ba = Ba[i * ka + j];
-            const T2* krow = ks + (size_t)(ah[j] * ta.np + ap[i]) * Xb;
+            const T2* krow = ks + (size_t)(rec_h(ra_rec, j) * ta.np + rec_p(ra_rec, i)) * Xb;
             T zr = 0, zi = 0;
 #pragma unroll
             for (int k = 0; k < KB; ++k)
@@ -196,17 +194,18 @@ __device__ __forceinline__ cplx_t<T> pair_cross_term2(const SpinTables& ta, cons
     const int nsa = ta.bucket[KA + 1] - ta.bucket[KA], sa = a - ta.bucket[KA];
     const int nsb = tbb.bucket[KB + 1] - tbb.bucket[KB], sb = b - tbb.bucket[KB];
     int ha[KA], pa[KA], xb[KB][KB];
+    const uint4 ra_rec = ta.str_hp[a], rb_rec = tbb.str_hp[b];
 #pragma unroll
     for (int i = 0; i < KA; ++i) {
-        ha[i] = ta.str_h[(size_t)a * MSD_KMAX + i] * ta.np;
-        pa[i] = ta.str_p[(size_t)a * MSD_KMAX + i];
+        ha[i] = rec_h(ra_rec, i) * ta.np;
+        pa[i] = rec_p(ra_rec, i);
     }
     {
         int hb[KB], pb[KB];
 #pragma unroll
         for (int k = 0; k < KB; ++k) {
-            hb[k] = tbb.str_h[(size_t)b * MSD_KMAX + k] * tbb.np;
-            pb[k] = tbb.str_p[(size_t)b * MSD_KMAX + k];
+            hb[k] = rec_h(rb_rec, k) * tbb.np;
+            pb[k] = rec_p(rb_rec, k);
         }
 #pragma unroll
         for (int k = 0; k < KB; ++k)

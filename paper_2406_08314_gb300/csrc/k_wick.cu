@@ -200,13 +200,12 @@ k_strings(SpinTables tb, int nw, const double2* __restrict__ Gact, double2* __re
     const int sl = blockIdx.x * blockDim.x + threadIdx.x;
     if (sl >= ns) return;
     const int s = tb.bucket[K] + sl;
-    const uint8_t* sh = tb.str_h + (size_t)s * MSD_KMAX;
-    const uint8_t* sp = tb.str_p + (size_t)s * MSD_KMAX;
+    const uint4 rec = tb.str_hp[s];
     double2 a[K][K];
 #pragma unroll
     for (int i = 0; i < K; ++i)
 #pragma unroll
-        for (int j = 0; j < K; ++j) a[i][j] = g[sh[i] * tb.np + sp[j]];
+        for (int j = 0; j < K; ++j) a[i][j] = g[rec_h(rec, i) * tb.np + rec_p(rec, j)];
     int perm[K];
 #pragma unroll
     for (int i = 0; i < K; ++i) perm[i] = i;
@@ -258,9 +257,9 @@ k_strings(SpinTables tb, int nw, const double2* __restrict__ Gact, double2* __re
         // FP32 elimination of the rows in the FP64 pivot order
 #pragma unroll
         for (int i = 0; i < K; ++i) {
-            const int ro = sh[perm[i]] * tb.np;
+            const int ro = rec_h(rec, perm[i]) * tb.np;
 #pragma unroll
-            for (int j = 0; j < K; ++j) lu[i][j] = gf[ro + sp[j]];
+            for (int j = 0; j < K; ++j) lu[i][j] = gf[ro + rec_p(rec, j)];
         }
 #pragma unroll
         for (int k = 0; k < K; ++k) {

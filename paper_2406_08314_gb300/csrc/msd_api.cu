@@ -62,7 +62,7 @@ struct SpinHost {
     long long b_per_walker = 0;
     // device copies
     int *d_occ0 = nullptr, *d_hole_pos = nullptr, *d_part_orb = nullptr;
-    uint8_t *d_str_h = nullptr, *d_str_p = nullptr;
+    uint8_t* d_str_hp = nullptr;   // [n_str][16] packed records (SpinTables::str_hp)
     int8_t* d_str_sign = nullptr;
     int *d_csr_off = nullptr, *d_csr_other = nullptr;
     double* d_csr_c = nullptr;
@@ -290,7 +290,7 @@ SpinTables tables(const SpinHost& s, int cap)
     t.N = s.N; t.nh = s.nh; t.np = s.np; t.n_str = s.n_str;
     for (int k = 0; k < MSD_KMAX + 2; ++k) t.bucket[k] = s.bucket[k];
     t.occ0 = s.d_occ0; t.pos0 = s.d_pos0; t.hole_pos = s.d_hole_pos; t.part_orb = s.d_part_orb;
-    t.str_h = s.d_str_h; t.str_p = s.d_str_p; t.str_sign = s.d_str_sign;
+    t.str_hp = reinterpret_cast<const uint4*>(s.d_str_hp); t.str_sign = s.d_str_sign;
     t.csr_off = s.d_csr_off; t.csr_other = s.d_csr_other; t.csr_c = s.d_csr_c;
     t.cmx = s.d_cmx;
     t.kx = s.d_kx;
@@ -428,8 +428,15 @@ int upload_spin(msd_ctx* ctx, SpinHost& S)
     if ((rc = upload(ctx, &S.d_occ0, S.occ0))) return rc;
     if ((rc = upload(ctx, &S.d_hole_pos, S.hole_pos))) return rc;
     if ((rc = upload(ctx, &S.d_part_orb, S.part_orb))) return rc;
-    if ((rc = upload(ctx, &S.d_str_h, S.str_h))) return rc;
-    if ((rc = upload(ctx, &S.d_str_p, S.str_p))) return rc;
+    {
+        std::vector<uint8_t> rec((size_t)S.n_str * 16, 0);
+        for (int f = 0; f < S.n_str; ++f)
+            for (int i = 0; i < MSD_KMAX; ++i) {
+                rec[(size_t)f * 16 + i] = S.str_h[(size_t)f * MSD_KMAX + i];
+                rec[(size_t)f * 16 + 8 + i] = S.str_p[(size_t)f * MSD_KMAX + i];
+            }
+        if ((rc = upload(ctx, &S.d_str_hp, rec))) return rc;
+    }
     if ((rc = upload(ctx, &S.d_str_sign, S.str_sign))) return rc;
     if ((rc = upload(ctx, &S.d_csr_off, S.csr_off))) return rc;
     if ((rc = upload(ctx, &S.d_csr_other, S.csr_other))) return rc;
@@ -462,8 +469,8 @@ int upload_spin(msd_ctx* ctx, SpinHost& S)
 
 void free_spin(SpinHost& S)
 {
-    cudaFree(S.d_occ0); cudaFree(S.d_hole_pos); cudaFree(S.d_part_orb); cudaFree(S.d_str_h);
-    cudaFree(S.d_str_p); cudaFree(S.d_str_sign); cudaFree(S.d_csr_off); cudaFree(S.d_csr_other);
+    cudaFree(S.d_occ0); cudaFree(S.d_hole_pos); cudaFree(S.d_part_orb); cudaFree(S.d_str_hp);
+    cudaFree(S.d_str_sign); cudaFree(S.d_csr_off); cudaFree(S.d_csr_other);
     cudaFree(S.d_csr_c); cudaFree(S.d_Lh); cudaFree(S.d_pos0);
     cudaFree(S.d_cmx); cudaFree(S.d_kx); cudaFree(S.d_csr_cf);
     S.d_cmx = nullptr;
@@ -471,7 +478,7 @@ void free_spin(SpinHost& S)
     S.d_csr_cf = nullptr;
     S.d_pos0 = nullptr;
     S.d_occ0 = S.d_hole_pos = S.d_part_orb = nullptr;
-    S.d_str_h = S.d_str_p = nullptr;
+    S.d_str_hp = nullptr;
     S.d_str_sign = nullptr;
     S.d_csr_off = S.d_csr_other = nullptr;
     S.d_csr_c = nullptr;
