@@ -99,9 +99,14 @@ struct SpinTables {
     const uint8_t* kx;     // same layout: h_j np + p_i, the row/column of the Gram matrices
     const float* csr_cf;   // [nnz] csr_c in FP32
     long long b_off[MSD_KMAX + 2];  // per-walker offset (complex units) of each bucket's B block
-    long long b_per_walker;         // sum_k k^2 * (strings of level k)
+    long long b_per_walker;         // sum_k b_stride(k) * (strings of level k)
     long long cmx_off[MSD_KMAX + 2];  // offset of each bucket's entries in cmx
 };
+
+// Complex entries per string in the inverse-minor arrays B: k^2 rounded up
+// to even, so that in FP32 every string's block starts on a 16-byte boundary
+// and two entries load as one 16-byte vector (the pad entry is zero).
+__host__ __device__ __forceinline__ constexpr int b_stride(int k) { return k * k + (k & 1); }
 
 // Hole / particle index i (< MSD_KMAX) of a string record.
 __device__ __forceinline__ int rec_h(const uint4& r, int i) { return (int)(((i < 4 ? r.x : r.y) >> (8 * (i & 3))) & 0xffu); }

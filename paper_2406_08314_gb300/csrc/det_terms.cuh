@@ -22,6 +22,27 @@
 template <typename T>
 using cplx_t = typename std::conditional<std::is_same<T, float>::value, float2, double2>::type;
 
+// The K x K inverse minor of one string (row-major, at a b_stride(K) offset)
+// into registers; in FP32 two entries per 16-byte load.
+template <int K, typename T>
+__device__ __forceinline__ void load_minor(const cplx_t<T>* __restrict__ B, cplx_t<T> (&b)[K][K])
+{
+    if constexpr (std::is_same<T, float>::value) {
+        const float4* B4 = reinterpret_cast<const float4*>(B);
+#pragma unroll
+        for (int v = 0; v < (K * K + 1) / 2; ++v) {
+            const float4 q = B4[v];
+            b[(2 * v) / K][(2 * v) % K] = make_float2(q.x, q.y);
+            if (2 * v + 1 < K * K) b[(2 * v + 1) / K][(2 * v + 1) % K] = make_float2(q.z, q.w);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < K; ++i)
+#pragma unroll
+            for (int j = 0; j < K; ++j) b[i][j] = B[i * K + j];
+    }
+}
+
 // Index of the pair (a, b), a < b < n, among the n (n - 1) / 2 pairs in
 // lexicographic order.
 __host__ __device__ __forceinline__ int pair_index(int a, int b, int n) { return a * n - a * (a + 1) / 2 + (b - a - 1); }
@@ -49,15 +70,10 @@ __device__ __forceinline__ double2 string_energy_value(const SpinTables& tb, int
     int hh[KL], pp[KL];   // hole and particle indices, ascending
 #pragma unroll
     for (int i = 0; i < KL; ++i) { hh[i] = rec_h(rec, i); pp[i] = rec_p(rec, i); }
-    const T2* B = reinterpret_cast<const T2*>(Bin) + (size_t)tb.b_off[KL] + ((size_t)w * ns + sl) * (KL * KL);
+    const T2* B = reinterpret_cast<const T2*>(Bin) + (size_t)tb.b_off[KL] + ((size_t)w * ns + sl) * b_stride(KL);
     constexpr bool REG = KL <= 4;   // the inverse minor in registers (levels 5, 6: from memory)
     T2 b[REG ? KL : 1][REG ? KL : 1];
-    if constexpr (REG) {
-#pragma unroll
-        for (int i = 0; i < KL; ++i)
-#pragma unroll
-            for (int j = 0; j < KL; ++j) b[i][j] = B[i * KL + j];
-    }
+    if constexpr (REG) load_minor<KL, T>(B, b);
     auto bij = [&](int i, int j) -> T2 {
         if constexpr (REG) return b[i][j];
         else return B[i * KL + j];
@@ -138,13 +154,10 @@ __device__ __forceinline__ cplx_t<T> pair_cross_value(const SpinTables& ta, cons
     for (int k = 0; k < KB; ++k)
 #pragma unroll
         for (int l = 0; l < KB; ++l) xb[k][l] = rec_h(rb_rec, l) * tbb.np + rec_p(rb_rec, k);
-    const T2* Ba = reinterpret_cast<const T2*>(Ba_in) + (size_t)ta.b_off[ka] + ((size_t)w * nsa + sa) * (ka * ka);
-    const T2* Bb = reinterpret_cast<const T2*>(Bb_in) + (size_t)tbb.b_off[KB] + ((size_t)w * nsb + sb) * (KB * KB);
+    const T2* Ba = reinterpret_cast<const T2*>(Ba_in) + (size_t)ta.b_off[ka] + ((size_t)w * nsa + sa) * b_stride(ka);
+    const T2* Bb = reinterpret_cast<const T2*>(Bb_in) + (size_t)tbb.b_off[KB] + ((size_t)w * nsb + sb) * b_stride(KB);
     T2 bb[KB][KB];
-#pragma unroll
-    for (int k = 0; k < KB; ++k)
-#pragma unroll
-        for (int l = 0; l < KB; ++l) bb[k][l] = Bb[k * KB + l];
+    load_minor<KB, T>(Bb, bb);
     const uint4 ra_rec = ta.str_hp[a];
     T xr = 0, xim = 0;
 #pragma unroll 1
@@ -212,17 +225,11 @@ __device__ __forceinline__ cplx_t<T> pair_cross_term2(const SpinTables& ta, cons
 #pragma unroll
             for (int l = 0; l < KB; ++l) xb[k][l] = hb[l] + pb[k];
     }
-    const T2* Ba = reinterpret_cast<const T2*>(Ba_in) + (size_t)ta.b_off[KA] + ((size_t)w * nsa + sa) * (KA * KA);
-    const T2* Bb = reinterpret_cast<const T2*>(Bb_in) + (size_t)tbb.b_off[KB] + ((size_t)w * nsb + sb) * (KB * KB);
+    const T2* Ba = reinterpret_cast<const T2*>(Ba_in) + (size_t)ta.b_off[KA] + ((size_t)w * nsa + sa) * b_stride(KA);
+    const T2* Bb = reinterpret_cast<const T2*>(Bb_in) + (size_t)tbb.b_off[KB] + ((size_t)w * nsb + sb) * b_stride(KB);
     T2 ba[KA][KA], bb[KB][KB];
-#pragma unroll
-    for (int i = 0; i < KA; ++i)
-#pragma unroll
-        for (int j = 0; j < KA; ++j) ba[i][j] = Ba[i * KA + j];
-#pragma unroll
-    for (int k = 0; k < KB; ++k)
-#pragma unroll
-        for (int l = 0; l < KB; ++l) bb[k][l] = Bb[k * KB + l];
+    load_minor<KA, T>(Ba, ba);
+    load_minor<KB, T>(Bb, bb);
     const cplx_t<T> rav = ra[(size_t)w * ta.n_str + a], rbv = rb[(size_t)w * tbb.n_str + b];
     T xr = 0, xim = 0;
 #pragma unroll

@@ -78,7 +78,7 @@ k_pair_run(SpinTables ta, SpinTables tbb, PairTables pt, int bidx, int ka, int k
         T2 be = T2{0, 0};
         int xe = 0;
         if (lane < kks) {
-            be = Bs_all[(size_t)ts.b_off[ks] + ((size_t)w * ns_s + sl) * kks + lane];
+            be = Bs_all[(size_t)ts.b_off[ks] + ((size_t)w * ns_s + sl) * b_stride(ks) + lane];
             xe = ts.kx[ts.cmx_off[ks] + (size_t)sl * kks + lane] * Xo;
         }
         T2 pq[PR_QMAX];
@@ -106,7 +106,7 @@ k_pair_run(SpinTables ta, SpinTables tbb, PairTables pt, int bidx, int ka, int k
         while (d < d1) {
             const int o = SIDE_B ? pt.a[d] : pt.b[d];
             const int so = o - to.bucket[ko];
-            const T2 bo = Bo_all[(size_t)to.b_off[ko] + ((size_t)w * ns_o + so) * kko + f];
+            const T2 bo = Bo_all[(size_t)to.b_off[ko] + ((size_t)w * ns_o + so) * b_stride(ko) + f];
             const T2 pv = P[to.kx[to.cmx_off[ko] + (size_t)so * kko + f]];
             const T2 ro = ro_arr[(size_t)w * to.n_str + o];
             const T c = std::is_same<T, float>::value ? (T)pt.cf[d] : (T)pt.c[d];

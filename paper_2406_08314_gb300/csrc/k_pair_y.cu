@@ -104,7 +104,7 @@ k_pair_y(SpinTables ta, SpinTables tbb, const float2* __restrict__ rfa, const fl
                 int kb = 1;
                 while (b >= tbb.bucket[kb + 1]) ++kb;
                 const int nsb = tbb.bucket[kb + 1] - tbb.bucket[kb], sb = b - tbb.bucket[kb], kk = kb * kb;
-                const float2* B = Bb + (size_t)tbb.b_off[kb] + ((size_t)w * nsb + sb) * kk;
+                const float2* B = Bb + (size_t)tbb.b_off[kb] + ((size_t)w * nsb + sb) * b_stride(kb);
                 const uint8_t* yx = tbb.kx + tbb.cmx_off[kb] + (size_t)sb * kk;
                 for (int e = lane; e < kk; e += 32) {
                     const float2 v = B[e];
@@ -161,7 +161,7 @@ k_pair_y(SpinTables ta, SpinTables tbb, const float2* __restrict__ rfa, const fl
                         const float c = tbb.csr_cf[d];
                         const int nsa = ta.bucket[ka + 1] - ta.bucket[ka], sa = a - ta.bucket[ka];
                         q.kk = ka * ka;
-                        q.aoff = ta.b_off[ka] + ((long long)w * nsa + sa) * q.kk;
+                        q.aoff = ta.b_off[ka] + ((long long)w * nsa + sa) * b_stride(ka);
                         q.xoff = (int)ta.cmx_off[ka] + sa * q.kk;
                         q.yoff = lo * XPP;
                         q.wr = c * wab.x; q.wi = c * wab.y;

@@ -285,7 +285,8 @@ k_strings(SpinTables tb, int nw, const double2* __restrict__ Gact, double2* __re
             for (int j = 0; j < K; ++j) lu[i][j] = T2{(T)a[i][j].x, (T)a[i][j].y};
         }
     }
-    T2* B = reinterpret_cast<T2*>(Bout) + (size_t)tb.b_off[K] + ((size_t)w * ns + sl) * (K * K);
+    T2* B = reinterpret_cast<T2*>(Bout) + (size_t)tb.b_off[K] + ((size_t)w * ns + sl) * b_stride(K);
+    if (K & 1) B[K * K] = T2{0, 0};   // the pad entry
 #pragma unroll
     for (int c = 0; c < K; ++c) {
         T2 x[K];
@@ -472,7 +473,7 @@ void launch_sum_slots(int nw, const double2* part, int nslot, int slot0, int n, 
 // mode, float in mixed mode); the copies are summed in double.
 #define CMAT_COPIES 16
 template <typename T, int GS, int EPL, int U>
-__device__ __forceinline__ void cmat_level(T* __restrict__ a, int g, int ng, int l, int kk, int ns, int s0,
+__device__ __forceinline__ void cmat_level(T* __restrict__ a, int g, int ng, int l, int kk, int kst, int ns, int s0,
                                            const T* __restrict__ B, const uint8_t* __restrict__ xt,
                                            const double2* __restrict__ ww)
 {
@@ -492,8 +493,8 @@ __device__ __forceinline__ void cmat_level(T* __restrict__ a, int g, int ng, int
                 vr[u][q] = 0;
                 vi[u][q] = 0;
                 if (sl < ns && e < kk) {
-                    const size_t o = (size_t)sl * kk + e;
-                    const T br = B[2 * o], bi = B[2 * o + 1];
+                    const size_t o = (size_t)sl * kk + e, ob = (size_t)sl * kst + e;
+                    const T br = B[2 * ob], bi = B[2 * ob + 1];
                     vx[u][q] = xt[o];
                     vr[u][q] = fr * br - fi * bi;
                     vi[u][q] = fr * bi + fi * br;
@@ -526,16 +527,16 @@ __device__ __forceinline__ void cmat_walker(const SpinTables& tb, int w, const d
     for (int k = 1; k <= MSD_KMAX; ++k) {
         const int s0 = tb.bucket[k], ns = tb.bucket[k + 1] - s0, kk = k * k;
         if (ns == 0) continue;
-        const T* B = Bb + 2 * ((size_t)tb.b_off[k] + (size_t)w * ns * kk);
+        const T* B = Bb + 2 * ((size_t)tb.b_off[k] + (size_t)w * ns * b_stride(k));
         const uint8_t* xt = tb.cmx + tb.cmx_off[k];
         if (kk <= 16)
-            cmat_level<T, 16, 1, 3>(acc[threadIdx.x >> 4], threadIdx.x >> 4, 16, threadIdx.x & 15, kk, ns, s0, B, xt,
+            cmat_level<T, 16, 1, 3>(acc[threadIdx.x >> 4], threadIdx.x >> 4, 16, threadIdx.x & 15, kk, b_stride(k), ns, s0, B, xt,
                                     ww);
         else if (kk <= 32)
-            cmat_level<T, 32, 1, 3>(acc[(threadIdx.x >> 5) * 2], threadIdx.x >> 5, 8, threadIdx.x & 31, kk, ns, s0, B,
+            cmat_level<T, 32, 1, 3>(acc[(threadIdx.x >> 5) * 2], threadIdx.x >> 5, 8, threadIdx.x & 31, kk, b_stride(k), ns, s0, B,
                                     xt, ww);
         else
-            cmat_level<T, 32, 2, 3>(acc[(threadIdx.x >> 5) * 2], threadIdx.x >> 5, 8, threadIdx.x & 31, kk, ns, s0, B,
+            cmat_level<T, 32, 2, 3>(acc[(threadIdx.x >> 5) * 2], threadIdx.x >> 5, 8, threadIdx.x & 31, kk, b_stride(k), ns, s0, B,
                                     xt, ww);
     }
     __syncthreads();

@@ -299,7 +299,7 @@ SpinTables tables(const SpinHost& s, int cap)
     for (int k = 0; k <= MSD_KMAX; ++k) {
         t.b_off[k] = off;
         t.cmx_off[k] = xo;
-        off += (long long)cap * k * k * (s.bucket[k + 1] - s.bucket[k]);
+        off += (long long)cap * b_stride(k) * (s.bucket[k + 1] - s.bucket[k]);
         xo += (long long)k * k * (s.bucket[k + 1] - s.bucket[k]);
     }
     t.b_off[MSD_KMAX + 1] = off;
@@ -416,7 +416,7 @@ int build_spin(msd_ctx* ctx, int s, const int32_t* occ, int n_det, std::vector<i
     if (S.bucket[1] != 1 || keys[order[0]].size() != 0)
         return fail(ctx, MSD_ERR_ARG, "spin %d: the reference string is missing", s);
     S.b_per_walker = 0;
-    for (int k = 0; k <= MSD_KMAX; ++k) S.b_per_walker += (long long)k * k * (S.bucket[k + 1] - S.bucket[k]);
+    for (int k = 0; k <= MSD_KMAX; ++k) S.b_per_walker += (long long)b_stride(k) * (S.bucket[k + 1] - S.bucket[k]);
     sid.resize(n_det);
     for (int I = 0; I < n_det; ++I) sid[I] = final_of_tmp[tmp_of_det[I]];
     return MSD_OK;
