@@ -471,13 +471,16 @@ def run_ours(args, rank, world, local):
     if not args.no_e2e:
         ha = torch.from_numpy(wk.phi_a).pin_memory()
         hb = torch.from_numpy(wk.phi_b).pin_memory()
+        # the caller's result buffers, pinned and allocated once like its inputs
+        outs_h = tuple(torch.empty(shape, dtype=torch.complex128).pin_memory()
+                       for shape in ((n_w,), (n_w, s.n_chol), (n_w,)))
         ctx.set_sync(True)
-        ctx.evaluate(ha, hb)
+        ctx.evaluate(ha, hb, out=outs_h)
         barrier()
         t0 = time.perf_counter()
         n_e2e = max(1, min(args.steps, 5))
         for _ in range(n_e2e):
-            o_h, v_h, e_h = ctx.evaluate(ha, hb)      # host in, host out (the library stages)
+            o_h, v_h, e_h = ctx.evaluate(ha, hb, out=outs_h)   # host in, host out (the library stages)
         wall = (time.perf_counter() - t0) * 1e3
         wall_max, u_e2e = aggregate(wall, float(units_per_step * n_e2e))
         phi_bytes = ha.numel() * 16 + hb.numel() * 16

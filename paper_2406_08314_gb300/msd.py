@@ -309,8 +309,8 @@ class Context:
         return out
 
     def set_tensor_gram(self, on: bool):
-        """Mixed precision: Gram matrices on the tensor cores (default) or
-        by FP32 FMAs."""
+        """Mixed precision: Gram matrices on the tensor cores, or by FP32
+        FMAs (the default)."""
         self._check(_lib.msd_set_tensor_gram(self._h, int(bool(on))))
 
     def set_wait_budget(self, ns: int):
