@@ -91,6 +91,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     # library options (alternative implementations of the same step)
+    p.add_argument("--no-overlap", action="store_true",
+                   help="run every kernel of a step on one stream (msd_set_stream_overlap(0))")
     p.add_argument("--tensor-gram", action="store_true",
                    help="Gram matrices on the tensor cores (msd_set_tensor_gram)")
     p.add_argument("--no-fused", action="store_true",
@@ -371,6 +373,7 @@ def run_ours(args, rank, world, local):
     ctx.set_fused(not args.no_fused)
     ctx.set_pair_form(args.pair_form)
     ctx.set_tensor_gram(args.tensor_gram)
+    ctx.set_stream_overlap(not args.no_overlap)
     vb = torch.empty((n_w, s.n_chol), dtype=torch.complex128, device=dev)
     el = torch.empty((n_w,), dtype=torch.complex128, device=dev)
     ov = torch.empty((n_w,), dtype=torch.complex128, device=dev)
@@ -535,7 +538,10 @@ def run_ours(args, rank, world, local):
                        "step": "msd_evaluate: overlap + force bias + local energy",
                        "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"walker replicas x{world}",
-                       "strings": [int(sp["lv"].sum()) for sp in spins]},
+                       "strings": [int(sp["lv"].sum()) for sp in spins],
+                       "streams": ("2: the energy's per-walker sums after the contraction run concurrently "
+                                   "with the strings, weights and force bias" if args.precision == "mixed"
+                                   and not args.no_overlap else "1")},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -543,6 +549,8 @@ def run_ours(args, rank, world, local):
             "clocks": clocks,
             "fp64": fp64,
             "kernels": kernels,
+            "kernels_note": "CUDA-event span of each kernel inside the timed steps; with two streams the "
+                            "spans of the concurrent kernels overlap and sum to more than the step",
             "peaks_source": peak_src,
             "peaks": {k: peaks[k] for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained", "fp64_gflops",
                                             "fp32_gflops", "tf32_gflops", "alu_how") if k in peaks},

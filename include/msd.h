@@ -258,6 +258,19 @@ int msd_set_exact_reference(msd_ctx* ctx, int on);
    scale from 2.9e-6 to 3.4e-6 Ha (maximum over 640 walkers). */
 int msd_set_tensor_gram(msd_ctx* ctx, int on);
 
+/* Mixed precision, msd_evaluate / msd_local_energy only: with on = 1 (the
+   default) the energy's per-walker sums that follow the Cholesky
+   contraction (one-body terms, the exactly split reference sums, the sums of
+   Lambda and Xi, the Gram matrices) run on a second stream of this context,
+   concurrently with the string minors, weights and force bias (bound by FP64
+   arithmetic) on the caller's stream; the per-determinant terms wait for
+   both. The call stays ordered on the caller's stream (the second stream
+   waits for the caller's stream at the fork, and the caller's stream waits for
+   the second stream before the per-determinant terms, also on an error
+   return). The results are identical with on = 0, which runs every kernel on
+   the caller's stream. */
+int msd_set_stream_overlap(msd_ctx* ctx, int on);
+
 /* The form of the opposite-spin exchange term of the local energy (Sec. III,
    the alpha-beta part of the two-body Wick contraction),
      sum_I c_I r_a r_b sum_ij sum_kl Ba[i][j] Bb[k][l] K^ab[(h_j,p_i)][(h_l,p_k)].

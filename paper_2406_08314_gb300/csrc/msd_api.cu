@@ -127,6 +127,12 @@ struct msd_ctx {
     // alpha spin's first kernels run (created on first use)
     cudaStream_t copy_st = nullptr;
     cudaEvent_t ev_in = nullptr, ev_b = nullptr;
+    // mixed evaluation: the energy's remaining per-walker contractions run on
+    // a side stream while the strings, weights and force bias run on the
+    // caller's stream (msd_set_stream_overlap; created on first use)
+    bool overlap = true;
+    cudaStream_t side_st = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     TimerHook hook;
     // TF32 hi/lo splits of the half-rotated Cholesky vectors (mixed path)
     bool mixed_ready = false;
@@ -916,9 +922,8 @@ int chunk_alloc(msd_ctx* ctx, int cap, bool want_b, int nslot, Chunk& c)
     return MSD_OK;
 }
 
-// Reference inverse, string minors and weights for walkers [w0, w0 + nw).
-int run_overlap_part(msd_ctx* ctx, const Staged& in, int w0, int nw, int cap, Chunk& c,
-                     bool want_b, bool fp32_b, cudaStream_t st)
+// Reference inverse of walkers [w0, w0 + nw), both spins.
+int run_refs(msd_ctx* ctx, const Staged& in, int w0, int nw, int cap, Chunk& c, cudaStream_t st)
 {
     const int M = ctx->M;
     const TimerHook& th = ctx->hook;
@@ -931,6 +936,14 @@ int run_overlap_part(msd_ctx* ctx, const Staged& in, int w0, int nw, int cap, Ch
         th.end(st);
         CKLAUNCH();
     }
+    return MSD_OK;
+}
+
+// String minors, ratios and weights of a chunk whose reference inverse is done.
+int run_strings_weights(msd_ctx* ctx, int nw, int cap, Chunk& c, bool want_b, bool fp32_b, cudaStream_t st)
+{
+    const TimerHook& th = ctx->hook;
+    SpinTables T[2] = {tables(ctx->sp[0], cap), tables(ctx->sp[1], cap)};
     for (int s = 0; s < 2; ++s) {
         launch_strings(T[s], nw, c.Gact[s], c.r[s], fp32_b ? c.rf[s] : nullptr, c.B[s], fp32_b, want_b, st, th);
         CKLAUNCH();
@@ -941,6 +954,14 @@ int run_overlap_part(msd_ctx* ctx, const Staged& in, int w0, int nw, int cap, Ch
     th.end(st);
     CKLAUNCH();
     return MSD_OK;
+}
+
+// Reference inverse, string minors and weights for walkers [w0, w0 + nw).
+int run_overlap_part(msd_ctx* ctx, const Staged& in, int w0, int nw, int cap, Chunk& c,
+                     bool want_b, bool fp32_b, cudaStream_t st)
+{
+    int rc = run_refs(ctx, in, w0, nw, cap, c, st);
+    return rc ? rc : run_strings_weights(ctx, nw, cap, c, want_b, fp32_b, st);
 }
 
 int begin_call(msd_ctx* ctx, int n_w, const double* pa, const double* pb, cudaStream_t st)
@@ -1184,13 +1205,13 @@ int en_alloc(msd_ctx* ctx, int cap, bool fp32, EnWork& E)
     return MSD_OK;
 }
 
-int en_chunk(msd_ctx* ctx, Chunk& c, EnWork& E, int w0, int nw, int cap, bool fp32, double2* e_out,
-             double2* ov_out, cudaStream_t st, bool defer_det = false)
+// Energy part, first stage: the Cholesky contractions F_g = G L_g and their
+// epilogue (v0, Lambda, Xi) per spin.
+int en_fepi(msd_ctx* ctx, Chunk& c, EnWork& E, int nw, int cap, bool fp32, cudaStream_t st)
 {
     const int M = ctx->M, G = ctx->n_chol;
     const TimerHook& th = ctx->hook;
     SpinTables T[2] = {tables(ctx->sp[0], cap), tables(ctx->sp[1], cap)};
-    const int X[2] = {T[0].nh * T[0].np, T[1].nh * T[1].np};
     const int NC[2] = {T[0].N + T[0].np, T[1].N + T[1].np};
     // with the exact reference sums the FP32 exchange traces are not needed
     const bool exact = fp32 && exact_ref_on(ctx);
@@ -1239,6 +1260,23 @@ int en_chunk(msd_ctx* ctx, Chunk& c, EnWork& E, int w0, int nw, int cap, bool fp
                         (double2*)E.xx[s], (double2*)E.La[s], (double2*)E.Xi[s], st);
             th.end(st);
         }
+        CKLAUNCH();
+    }
+    return MSD_OK;
+}
+
+// Energy part, second stage (reads only the reference inverse and the first
+// stage's outputs): one-body terms, the exactly split reference sums, the
+// per-walker sums of Lambda and Xi, the Gram matrices.
+int en_rest(msd_ctx* ctx, Chunk& c, EnWork& E, int nw, int cap, bool fp32, cudaStream_t st)
+{
+    const int M = ctx->M, G = ctx->n_chol;
+    const TimerHook& th = ctx->hook;
+    SpinTables T[2] = {tables(ctx->sp[0], cap), tables(ctx->sp[1], cap)};
+    const int X[2] = {T[0].nh * T[0].np, T[1].nh * T[1].np};
+    const bool exact = fp32 && exact_ref_on(ctx);
+    const bool traces = !exact;
+    for (int s = 0; s < 2; ++s) {
         th.begin("k_onebody", st);
         launch_onebody(T[s], nw, M, ctx->d_h1 + (size_t)s * M * M, c.Gr[s], (double2*)E.e1[s],
                        (double2*)E.Lh1[s], st, exact && ctx->d_hJ ? ctx->d_hJ + (size_t)s * M * M : nullptr);
@@ -1301,7 +1339,16 @@ int en_chunk(msd_ctx* ctx, Chunk& c, EnWork& E, int w0, int nw, int cap, bool fp
     }
     th.end(st);
     CKLAUNCH();
-    if (defer_det) return MSD_OK;   // the batched kernel and the final sum follow
+    return MSD_OK;
+}
+
+// Energy part, last stage (after the string weights): the per-determinant
+// terms and the final reduction.
+int en_terms(msd_ctx* ctx, Chunk& c, EnWork& E, int w0, int nw, int cap, bool fp32, double2* e_out,
+             double2* ov_out, cudaStream_t st)
+{
+    const TimerHook& th = ctx->hook;
+    SpinTables T[2] = {tables(ctx->sp[0], cap), tables(ctx->sp[1], cap)};
     int slot = c.nR;
     void* Kss[2] = {E.Kaa, E.Kbb};
     th.begin("k_string_energy", st);
@@ -1331,6 +1378,16 @@ int en_chunk(msd_ctx* ctx, Chunk& c, EnWork& E, int w0, int nw, int cap, bool fp
     th.end(st);
     CKLAUNCH();
     return MSD_OK;
+}
+
+int en_chunk(msd_ctx* ctx, Chunk& c, EnWork& E, int w0, int nw, int cap, bool fp32, double2* e_out,
+             double2* ov_out, cudaStream_t st, bool defer_det = false)
+{
+    int rc;
+    if ((rc = en_fepi(ctx, c, E, nw, cap, fp32, st))) return rc;
+    if ((rc = en_rest(ctx, c, E, nw, cap, fp32, st))) return rc;
+    if (defer_det) return MSD_OK;   // the batched kernel and the final sum follow
+    return en_terms(ctx, c, E, w0, nw, cap, fp32, e_out, ov_out, st);
 }
 
 // Overlap (always), force bias (vbias != NULL) and local energy (e_loc !=
@@ -1380,8 +1437,42 @@ int evaluate_impl(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_
     if (defer && (cap < n_w || !want_e || in.host_any || o_e.host || o_v.host || o_ov.host))
         return fail(ctx, MSD_ERR_SHAPE, "batched evaluation needs device buffers, the energy output and all "
                                         "walkers in one chunk (%d walkers, %d fit)", n_w, cap);
+    // mixed energy: the second energy stage on a side stream, concurrent
+    // with the strings, weights and force bias (FP64-bound) on this stream
+    const bool side = fp32 && want_e && !defer && ctx->overlap;
+    if (side && !ctx->side_st) {
+        if (cudaStreamCreateWithFlags(&ctx->side_st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess)
+            return fail(ctx, MSD_ERR_CUDA, "side stream could not be created");
+    }
+    // every return after a fork first makes this stream wait for the side stream
+    struct Join {
+        cudaStream_t st = nullptr, side = nullptr;
+        cudaEvent_t ev = nullptr;
+        void now() {
+            if (side) { cudaEventRecord(ev, side); cudaStreamWaitEvent(st, ev, 0); side = nullptr; }
+        }
+        ~Join() { now(); }
+    } join;
     for (int w0 = 0; w0 < n_w; w0 += cap) {
         const int nw = std::min(cap, n_w - w0);
+        if (side) {
+            if ((rc = run_refs(ctx, in, w0, nw, cap, c, st))) return rc;
+            if ((rc = en_fepi(ctx, c, E, nw, cap, fp32, st))) return rc;
+            CK(cudaEventRecord(ctx->ev_fork, st));
+            CK(cudaStreamWaitEvent(ctx->side_st, ctx->ev_fork, 0));
+            join.st = st;
+            join.side = ctx->side_st;
+            join.ev = ctx->ev_join;
+            if ((rc = en_rest(ctx, c, E, nw, cap, fp32, ctx->side_st))) return rc;
+            if ((rc = run_strings_weights(ctx, nw, cap, c, true, fp32, st))) return rc;
+            if (want_v && (rc = fb_chunk(ctx, c, f, w0, nw, cap, fp32, o_v.dev, nullptr, st))) return rc;
+            join.now();
+            CKLAUNCH();
+            if ((rc = en_terms(ctx, c, E, w0, nw, cap, fp32, o_e.dev, o_ov.dev, st))) return rc;
+            continue;
+        }
         if ((rc = run_overlap_part(ctx, in, w0, nw, cap, c, true, fp32, st))) return rc;
         if (want_v && (rc = fb_chunk(ctx, c, f, w0, nw, cap, fp32, o_v.dev, want_e ? nullptr : o_ov.dev, st)))
             return rc;
@@ -1718,6 +1809,9 @@ void msd_destroy(msd_ctx* ctx)
     for (auto& p : ctx->pending) { ctx->ev_pool.push_back(p.a); ctx->ev_pool.push_back(p.b); }
     for (auto e : ctx->ev_pool) cudaEventDestroy(e);
     if (ctx->copy_st) cudaStreamDestroy(ctx->copy_st);
+    if (ctx->side_st) cudaStreamDestroy(ctx->side_st);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
     if (ctx->ev_b) cudaEventDestroy(ctx->ev_b);
     delete ctx;
@@ -2172,6 +2266,13 @@ int msd_set_tensor_gram(msd_ctx* ctx, int on)
 {
     if (!ctx) return MSD_ERR_ARG;
     ctx->tc_gram = on != 0;
+    return MSD_OK;
+}
+
+int msd_set_stream_overlap(msd_ctx* ctx, int on)
+{
+    if (!ctx) return MSD_ERR_ARG;
+    ctx->overlap = on != 0;
     return MSD_OK;
 }
 

@@ -22,7 +22,7 @@ _ERRORS = {-1: "MSD_ERR_ARG", -2: "MSD_ERR_SHAPE", -3: "MSD_ERR_CUDA", -4: "MSD_
 EXPORTS = ["msd_create", "msd_destroy", "msd_last_error", "msd_set_hamiltonian", "msd_set_trial",
            "msd_set_precision", "msd_overlap", "msd_det_ratios", "msd_force_bias",
            "msd_local_energy", "msd_evaluate", "msd_det_energies", "msd_rdm1", "msd_info", "msd_set_timing", "msd_reset_stats",
-           "msd_kernel_count", "msd_kernel_stat", "msd_set_workspace_limit", "msd_set_sync", "msd_set_fused", "msd_set_pair_form", "msd_set_exact_reference", "msd_set_tensor_gram", "msd_set_wait_budget", "msd_propagate",
+           "msd_kernel_count", "msd_kernel_stat", "msd_set_workspace_limit", "msd_set_sync", "msd_set_fused", "msd_set_pair_form", "msd_set_exact_reference", "msd_set_tensor_gram", "msd_set_stream_overlap", "msd_set_wait_budget", "msd_propagate",
            "msd_launch_count", "msd_overlap_noalloc", "msd_batch_create", "msd_batch_destroy",
            "msd_batch_last_error", "msd_batch_evaluate", "msd_batch_autotune", "msd_batch_config",
            "msd_batch_set_config", "msd_batch_time_persistent", "msd_batch_graph_ready", "msd_batch_graph_kernels", "msd_features", "msd_features_rows",
@@ -70,6 +70,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.msd_set_pair_form.argtypes = [vp, ci]
     lib.msd_set_exact_reference.argtypes = [vp, ci]
     lib.msd_set_tensor_gram.argtypes = [vp, ci]
+    lib.msd_set_stream_overlap.argtypes = [vp, ci]
     lib.msd_set_wait_budget.argtypes = [vp, ctypes.c_ulonglong]
     lib.msd_det_energies.argtypes = [vp, ci, vp, vp, ci, vp, vp, vp, vp]
     lib.msd_rdm1.argtypes = [vp, ci, vp, vp, vp, vp]
@@ -312,6 +313,12 @@ class Context:
         """Mixed precision: Gram matrices on the tensor cores, or by FP32
         FMAs (the default)."""
         self._check(_lib.msd_set_tensor_gram(self._h, int(bool(on))))
+
+    def set_stream_overlap(self, on: bool):
+        """Mixed energy: the per-walker sums after the Cholesky contraction
+        on a second stream, concurrent with the strings, weights and force
+        bias (default on; identical results either way)."""
+        self._check(_lib.msd_set_stream_overlap(self._h, int(bool(on))))
 
     def set_wait_budget(self, ns: int):
         """Budget (ns) of the tensor-core kernels' device-side waits;

@@ -427,6 +427,31 @@ def test_fe2s2_full_size_fused_matches_unfused(msd, fe2s2):
     assert np.all(np.abs(e1 - e0) <= 0.1 * MIX_E_ABS), np.abs(e1 - e0).max()
 
 
+def test_fe2s2_full_size_stream_overlap_identical(msd, fe2s2):
+    """Full size, bench launch configuration: the energy's second stage on
+    its own stream (the default) against every kernel on the caller's
+    stream. The same kernels compute the same values in the same order, so
+    overlaps, force biases and local energies agree bit for bit: with device
+    buffers, with host buffers, and with walker chunks smaller than the
+    batch (one fork and join per chunk)."""
+    s, w = fe2s2
+    da, db = _cuda(w.phi_a), _cuda(w.phi_b)
+    ctx = msd.Context(s, "mixed")
+    ctx.set_stream_overlap(False)
+    ref = [_np(x) for x in ctx.evaluate(da, db)]
+    ctx.set_stream_overlap(True)
+    for got in ([_np(x) for x in ctx.evaluate(da, db)],
+                [_np(x) for x in ctx.evaluate(w.phi_a, w.phi_b)]):
+        for a, b in zip(ref, got):
+            assert np.array_equal(a, b)
+    ctx.set_workspace_limit(3 << 30)
+    got = [_np(x) for x in ctx.evaluate(da, db)]
+    assert ctx.info("walker_chunk") < 640
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b)
+    ctx.close()
+
+
 def test_fe2s2_full_size_pair_forms_agree(msd, fe2s2):
     """Full size, bench launch configuration: the opposite-spin term over
     runs sharing a string (the default here), per beta string and per
