@@ -1441,7 +1441,11 @@ int evaluate_impl(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_
     // with the strings, weights and force bias (FP64-bound) on this stream
     const bool side = fp32 && want_e && !defer && ctx->overlap;
     if (side && !ctx->side_st) {
-        if (cudaStreamCreateWithFlags(&ctx->side_st, cudaStreamNonBlocking) != cudaSuccess ||
+        // the highest stream priority: the second stage's blocks are placed
+        // first and it finishes early instead of trailing into the weights
+        int least = 0, greatest = 0;
+        cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        if (cudaStreamCreateWithPriority(&ctx->side_st, cudaStreamNonBlocking, greatest) != cudaSuccess ||
             cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess)
             return fail(ctx, MSD_ERR_CUDA, "side stream could not be created");
