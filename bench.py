@@ -539,9 +539,9 @@ def run_ours(args, rank, world, local):
                        "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"walker replicas x{world}",
                        "strings": [int(sp["lv"].sum()) for sp in spins],
-                       "streams": ("2: the energy's per-walker sums after the contraction run concurrently "
-                                   "with the strings, weights and force bias" if args.precision == "mixed"
-                                   and not args.no_overlap else "1")},
+                       "streams": ("2: the energy's per-walker sums after the contraction beside the strings "
+                                   "and weights, then the force bias beside the per-determinant terms"
+                                   if args.precision == "mixed" and not args.no_overlap else "1")},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

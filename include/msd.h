@@ -263,12 +263,15 @@ int msd_set_tensor_gram(msd_ctx* ctx, int on);
    contraction (one-body terms, the exactly split reference sums, the sums of
    Lambda and Xi, the Gram matrices) run on a second stream of this context
    (created on first use at the device's highest stream priority),
-   concurrently with the string minors, weights and force bias (bound by FP64
-   arithmetic) on the caller's stream; the per-determinant terms wait for
-   both. On the iron-sulfur shape: 23.86 against 24.63 ms per step. The call stays ordered on the caller's stream (the second stream
-   waits for the caller's stream at the fork, and the caller's stream waits for
-   the second stream before the per-determinant terms, also on an error
-   return). The results are identical with on = 0, which runs every kernel on
+   concurrently with the string minors and weights (bound by FP64
+   arithmetic) on the caller's stream; then the force bias runs on the
+   second stream, concurrently with the per-determinant terms, which wait for
+   the energy sums. On the iron-sulfur shape: 23.54 against 24.60 ms per
+   step. The call stays ordered on the caller's stream: the second stream
+   waits for the caller's stream at each fork, and the caller's stream waits
+   for the second stream before the per-determinant terms (energy sums) and
+   again at the end of each walker chunk (force bias), also on an error
+   return. The results are identical with on = 0, which runs every kernel on
    the caller's stream. */
 int msd_set_stream_overlap(msd_ctx* ctx, int on);
 

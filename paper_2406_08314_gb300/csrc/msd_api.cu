@@ -132,7 +132,7 @@ struct msd_ctx {
     // caller's stream (msd_set_stream_overlap; created on first use)
     bool overlap = true;
     cudaStream_t side_st = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_rest = nullptr, ev_w = nullptr;
     TimerHook hook;
     // TF32 hi/lo splits of the half-rotated Cholesky vectors (mixed path)
     bool mixed_ready = false;
@@ -1438,7 +1438,8 @@ int evaluate_impl(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_
         return fail(ctx, MSD_ERR_SHAPE, "batched evaluation needs device buffers, the energy output and all "
                                         "walkers in one chunk (%d walkers, %d fit)", n_w, cap);
     // mixed energy: the second energy stage on a side stream, concurrent
-    // with the strings, weights and force bias (FP64-bound) on this stream
+    // with the strings and weights (FP64-bound) on this stream; then the force
+    // bias on the side stream, concurrent with the per-determinant terms
     const bool side = fp32 && want_e && !defer && ctx->overlap;
     if (side && !ctx->side_st) {
         // the highest stream priority: the second stage's blocks are placed
@@ -1447,7 +1448,9 @@ int evaluate_impl(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_
         cudaDeviceGetStreamPriorityRange(&least, &greatest);
         if (cudaStreamCreateWithPriority(&ctx->side_st, cudaStreamNonBlocking, greatest) != cudaSuccess ||
             cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess)
+            cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->ev_rest, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->ev_w, cudaEventDisableTiming) != cudaSuccess)
             return fail(ctx, MSD_ERR_CUDA, "side stream could not be created");
     }
     // every return after a fork first makes this stream wait for the side stream
@@ -1470,11 +1473,19 @@ int evaluate_impl(msd_ctx* ctx, int n_w, const double* phi_a, const double* phi_
             join.side = ctx->side_st;
             join.ev = ctx->ev_join;
             if ((rc = en_rest(ctx, c, E, nw, cap, fp32, ctx->side_st))) return rc;
+            CK(cudaEventRecord(ctx->ev_rest, ctx->side_st));
             if ((rc = run_strings_weights(ctx, nw, cap, c, true, fp32, st))) return rc;
-            if (want_v && (rc = fb_chunk(ctx, c, f, w0, nw, cap, fp32, o_v.dev, nullptr, st))) return rc;
-            join.now();
-            CKLAUNCH();
+            // the force bias (cofactors, G_T, contraction) follows the weights
+            // on the second stream, beside the per-determinant terms here
+            if (want_v) {
+                CK(cudaEventRecord(ctx->ev_w, st));
+                CK(cudaStreamWaitEvent(ctx->side_st, ctx->ev_w, 0));
+                if ((rc = fb_chunk(ctx, c, f, w0, nw, cap, fp32, o_v.dev, nullptr, ctx->side_st))) return rc;
+            }
+            CK(cudaStreamWaitEvent(st, ctx->ev_rest, 0));
             if ((rc = en_terms(ctx, c, E, w0, nw, cap, fp32, o_e.dev, o_ov.dev, st))) return rc;
+            join.now();   // before the next chunk's reference inverse and before the outputs
+            CKLAUNCH();
             continue;
         }
         if ((rc = run_overlap_part(ctx, in, w0, nw, cap, c, true, fp32, st))) return rc;
@@ -1816,6 +1827,8 @@ void msd_destroy(msd_ctx* ctx)
     if (ctx->side_st) cudaStreamDestroy(ctx->side_st);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->ev_rest) cudaEventDestroy(ctx->ev_rest);
+    if (ctx->ev_w) cudaEventDestroy(ctx->ev_w);
     if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
     if (ctx->ev_b) cudaEventDestroy(ctx->ev_b);
     delete ctx;

@@ -315,9 +315,10 @@ class Context:
         self._check(_lib.msd_set_tensor_gram(self._h, int(bool(on))))
 
     def set_stream_overlap(self, on: bool):
-        """Mixed energy: the per-walker sums after the Cholesky contraction
-        on a second stream, concurrent with the strings, weights and force
-        bias (default on; identical results either way)."""
+        """Mixed energy: the per-walker sums after the Cholesky contraction,
+        then the force bias, on a second stream, concurrent with the strings
+        and weights, then with the per-determinant terms (default on;
+        identical results either way)."""
         self._check(_lib.msd_set_stream_overlap(self._h, int(bool(on))))
 
     def set_wait_budget(self, ns: int):
