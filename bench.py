@@ -388,8 +388,6 @@ def run_ours(args, rank, world, local):
     step()                                  # surfaces any device-side error
     ctx.set_sync(False)
     torch.cuda.synchronize(dev)
-    ctx.set_timing(True)
-    ctx.reset_stats()
     sampler = ClockSampler(local)
     sampler.start()
     launches0 = msd.launch_count()
@@ -408,8 +406,20 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize(dev)
     launches = msd.launch_count() - launches0
     clocks = sampler.stop()
+    # per-kernel CUDA-event times: the same steps again with every kernel on
+    # one stream, where each kernel has the GPU to itself (with two streams
+    # the event spans of concurrent kernels overlap and include their waits)
+    ctx.set_stream_overlap(False)
+    ctx.set_timing(True)
+    ctx.reset_stats()
+    torch.cuda.synchronize(dev)
+    for _ in range(args.steps):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize(dev)
     kstats = ctx.kernel_stats()
     ctx.set_timing(False)
+    ctx.set_stream_overlap(not args.no_overlap)
     ms_max, units = aggregate(ms_total, float(units_per_step * args.steps))
     ms_per_step = ms_max / args.steps
     value = units / (ms_max / 1e3)
@@ -549,8 +559,10 @@ def run_ours(args, rank, world, local):
             "clocks": clocks,
             "fp64": fp64,
             "kernels": kernels,
-            "kernels_note": "CUDA-event span of each kernel inside the timed steps; with two streams the "
-                            "spans of the concurrent kernels overlap and sum to more than the step",
+            "kernels_note": "CUDA-event time of each kernel in a second pass of the timed steps with every "
+                            "kernel on one stream (msd_set_stream_overlap(0))"
+                            + ("; the timed steps run two streams" if args.precision == "mixed"
+                               and not args.no_overlap else ""),
             "peaks_source": peak_src,
             "peaks": {k: peaks[k] for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained", "fp64_gflops",
                                             "fp32_gflops", "tf32_gflops", "alu_how") if k in peaks},
