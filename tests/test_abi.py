@@ -46,3 +46,17 @@ def test_create_without_device_fails_cleanly():
     rc = msd.lib().msd_create(ctypes.byref(h), 10, 3, 3, 0, 0)
     assert rc == -3 and h.value is None
     assert b"device" in msd.lib().msd_last_error(None)
+
+
+def test_switches_reject_a_null_context():
+    """Every option setter checks its context on the host before anything
+    else (no device is touched), returning MSD_ERR_ARG (-1)."""
+    from paper_2406_08314_gb300 import build, msd
+    build.build()
+    lib = msd.lib()
+    for name in ("msd_set_precision", "msd_set_timing", "msd_set_sync", "msd_set_fused",
+                 "msd_set_exact_reference", "msd_set_tensor_gram", "msd_set_stream_overlap",
+                 "msd_set_pair_form"):
+        assert getattr(lib, name)(None, 1) == -1, name
+    assert lib.msd_set_workspace_limit(None, ctypes.c_size_t(1 << 20)) == -1
+    assert lib.msd_set_wait_budget(None, ctypes.c_ulonglong(1000)) == -1
